@@ -1,0 +1,228 @@
+"""Oracle: unregularised wavelet alternating minimisation (Algorithm 1) and the
+plain pixel-domain AM it reduces to, in FP64 with explicit sparse matrices.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline leg of the
+benchmark).  Shares no code with the CUDA path.
+
+Each step follows the paper's definitions literally, with scipy.sparse
+products as the only library primitive:
+
+  Phi = H Omega                                       (Sec. II, after Eq. 1.4)
+  b(z) = sum_y d(y) phi(y|z)                           (Eq. 1.6, for all z)
+  per iteration j (Algorithm 1):
+    qhat(y) = I0(y) exp(-sum_{z in Zs} phi(y|z) beta(z))
+    Z0 = max_y sum_{z in Zs} |phi(y|z)|                (Eq. 1.61)
+    bhat+(z) = sum_{y: phi>0} qhat phi,  bhat-(z) = sum_{y: phi<0} qhat phi   (Eq. 1.10)
+    beta(z) <- the zero of Eq. 1.9 in beta(z)          (closed form, see am_root)
+  I-divergence I(d||q) = sum d log(d/q) - d + q        (Sec. II footnote)
+
+Readings where the paper is silent (each also listed in the design notes):
+  * beta^(0) = 0 (mu = 0, qhat = I0).
+  * The active set Zs is a tree: the level-L approximations are always
+    active; the three level-l details of a block are active when that block
+    is "expanded".  Inactive coefficients stay 0.
+  * Expansion (Results section): after the iterations listed in expand_at
+    have completed, the image mu = Omega beta is formed, S = mu (summed over
+    z-slices in the per-slice 3-D mode), and every pixel with S > tau * max S
+    expands its current leaf one level (the leaf is the finest block on the
+    pixel's path from level L whose details are inactive).  tau < 0 expands
+    every leaf.  The comparison is made in FP64 on the given S.
+  * Degenerate roots and the clamp |Z0 delta| <= 30 (see am_root).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import haar
+
+CLAMP = 30.0
+
+
+# ---------------------------------------------------------------------------
+# cost
+# ---------------------------------------------------------------------------
+
+def idiv(d: np.ndarray, I0, p: np.ndarray) -> float:
+    """I(d || q) with q = I0 exp(-p), written with log q = log I0 - p so that
+    an underflowed q never enters a logarithm; 0 log 0 = 0."""
+    d = np.asarray(d, dtype=np.float64).ravel()
+    p = np.asarray(p, dtype=np.float64).ravel()
+    I0 = np.broadcast_to(np.asarray(I0, dtype=np.float64), d.shape)
+    q = I0 * np.exp(-p)
+    pos = d > 0
+    logterm = np.zeros_like(d)
+    logterm[pos] = d[pos] * (np.log(d[pos]) - np.log(I0[pos]) + p[pos])
+    return float(np.sum(logterm - d + q))
+
+
+# ---------------------------------------------------------------------------
+# the closed-form coordinate update
+# ---------------------------------------------------------------------------
+
+def am_root(b, bp, bm, Z0: float, clamp: float = CLAMP) -> np.ndarray:
+    """Delta = beta~ - betahat solving Eq. 1.9 = 0:
+        b - bp exp(-Z0 Delta) - bm exp(Z0 Delta) = 0,  bp >= 0 >= bm.
+    With u = exp(-Z0 Delta) this is bp u^2 - b u + bm = 0, whose positive root
+    is taken in the cancellation-free form for the sign of b.  Cases:
+      bp > 0, b >= 0 : u = (b + sqrt(b^2 - 4 bp bm)) / (2 bp)
+      bp > 0, b <  0 : u = 2 bm / (b - sqrt(b^2 - 4 bp bm))
+      bp = 0, b <  0, bm < 0 : u = bm / b
+      bp = 0, otherwise      : Delta = 0 when bm = 0 (nothing to update);
+                               the minimiser is at -infinity when bm < 0 <= b
+    u = 0 or u = infinity (minimiser at +-infinity) is clamped to
+    |Z0 Delta| <= clamp; any step between 0 and the 1-D minimiser keeps the
+    surrogate's decrease."""
+    b = np.asarray(b, dtype=np.float64)
+    bp = np.asarray(bp, dtype=np.float64)
+    bm = np.asarray(bm, dtype=np.float64)
+    u = np.empty_like(b)
+    zero = np.zeros_like(b, dtype=bool)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        disc = np.sqrt(b * b - 4.0 * bp * bm)
+        c1 = (bp > 0) & (b >= 0)
+        c2 = (bp > 0) & (b < 0)
+        c3 = (bp == 0) & (bm < 0) & (b < 0)
+        c4 = (bp == 0) & (bm < 0) & (b >= 0)
+        c5 = (bp == 0) & (bm == 0)
+        u[c1] = (b[c1] + disc[c1]) / (2.0 * bp[c1])
+        u[c2] = 2.0 * bm[c2] / (b[c2] - disc[c2])
+        u[c3] = bm[c3] / b[c3]
+        u[c4] = np.inf
+        u[c5] = 1.0
+        zero |= c5
+        t = -np.log(u)                     # = Z0 * Delta
+    t = np.clip(t, -clamp, clamp)
+    t[zero] = 0.0
+    return t / Z0
+
+
+# ---------------------------------------------------------------------------
+# the wavelet tree
+# ---------------------------------------------------------------------------
+
+def empty_tree(nx: int, ny: int, L: int) -> List[np.ndarray]:
+    """tree[l-1][by, bx] is True when the level-l block's details are active."""
+    return [np.zeros((ny >> l, nx >> l), dtype=bool) for l in range(1, L + 1)]
+
+
+def active_mask(tree: List[np.ndarray], nx: int, ny: int, L: int) -> np.ndarray:
+    level, typ, bx, by = haar.coefficient_info(nx, ny, L)
+    act = typ == -1
+    for l in range(1, L + 1):
+        sel = (level == l) & (typ >= 0)
+        act[sel] = tree[l - 1][by[sel], bx[sel]]
+    return act
+
+
+def leaf_levels(tree: List[np.ndarray], nx: int, ny: int, L: int) -> np.ndarray:
+    """Level of the leaf block holding each pixel ([ny, nx])."""
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    lev = np.full((ny, nx), L, dtype=np.int64)
+    descending = np.ones((ny, nx), dtype=bool)
+    for l in range(L, 0, -1):
+        exp_l = tree[l - 1][iy >> l, ix >> l]
+        descending &= exp_l
+        lev[descending] = l - 1
+    return lev
+
+
+def expand(tree: List[np.ndarray], S: np.ndarray, tau: float) -> List[np.ndarray]:
+    """One expansion step on the criterion image S ([ny, nx]); the leaf of each
+    selected pixel is read from the tree before the step."""
+    ny, nx = S.shape
+    L = len(tree)
+    S64 = np.asarray(S, dtype=np.float64)
+    if tau < 0:
+        sel = np.ones_like(S64, dtype=bool)
+    else:
+        sel = S64 > float(tau) * float(S64.max())
+    lev = leaf_levels(tree, nx, ny, L)
+    new = [t.copy() for t in tree]
+    iy, ix = np.nonzero(sel & (lev >= 1))
+    for l in range(1, L + 1):
+        m = lev[iy, ix] == l
+        new[l - 1][iy[m] >> l, ix[m] >> l] = True
+    return new
+
+
+# ---------------------------------------------------------------------------
+# the iterations
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class AMResult:
+    beta: np.ndarray
+    mu: np.ndarray
+    cost: np.ndarray                  # I(d||qhat^(j)), j = 0..n_iter
+    z0: np.ndarray                    # Z0 used at each iteration
+    tree: Optional[List[np.ndarray]]
+    trees: list                       # tree after each expansion
+    n_active: np.ndarray
+
+
+def _row_abs_max(Ps: sp.spmatrix) -> float:
+    return float(np.max(np.asarray(abs(Ps).sum(axis=1)).ravel()))
+
+
+def am_step(Ps: sp.csc_matrix, b_s, beta_s, d, I0):
+    """One AM iteration on the active columns Ps of Phi; returns (Delta, cost, Z0)."""
+    p = Ps @ beta_s
+    q = np.broadcast_to(np.asarray(I0, dtype=np.float64), p.shape) * np.exp(-p)
+    cost = idiv(d, I0, p)
+    Z0 = _row_abs_max(Ps)
+    bp = Ps.maximum(0).T @ q
+    bm = Ps.minimum(0).T @ q
+    return am_root(b_s, bp, bm, Z0), cost, Z0
+
+
+def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
+               expand_at: Sequence[int] = (), taus: Sequence[float] = (),
+               tree0: Optional[List[np.ndarray]] = None, nz: int = 1) -> AMResult:
+    """Algorithm 1 with the tree schedule; nz > 1 runs the per-slice 2-D Haar
+    mode (one tree shared by all slices, criterion summed over slices)."""
+    d = np.asarray(d, dtype=np.float64).ravel()
+    Om2 = haar.basis_matrix(nx, ny, L)
+    Omega = sp.block_diag([Om2] * nz, format="csc") if nz > 1 else Om2
+    Phi = (H @ Omega).tocsc()
+    b = Phi.T @ d                                        # Eq. 1.6, all z
+    N = nx * ny
+    beta = np.zeros(N * nz)
+    tree = [t.copy() for t in tree0] if tree0 is not None else empty_tree(nx, ny, L)
+    costs, z0s, trees, nact = [], [], [], []
+    sched = dict(zip(expand_at, taus))
+    for j in range(n_iter):
+        act = np.tile(active_mask(tree, nx, ny, L), nz)
+        Ps = Phi[:, act]
+        delta, cost, Z0 = am_step(Ps, b[act], beta[act], d, I0)
+        costs.append(cost)
+        z0s.append(Z0)
+        nact.append(int(act.sum()))
+        beta[act] += delta
+        if (j + 1) in sched:
+            mu = (Omega @ beta).reshape(nz, ny, nx)
+            tree = expand(tree, mu.sum(axis=0), sched[j + 1])
+            trees.append([t.copy() for t in tree])
+    costs.append(idiv(d, I0, Phi @ beta))
+    mu = (Omega @ beta).reshape(nz, ny, nx) if nz > 1 else (Omega @ beta).reshape(ny, nx)
+    return AMResult(beta, mu, np.array(costs), np.array(z0s), tree, trees, np.array(nact))
+
+
+def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None) -> AMResult:
+    """O'Sullivan-Benac AM: Algorithm 1 with Omega = I and every pixel active."""
+    d = np.asarray(d, dtype=np.float64).ravel()
+    Hc = H.tocsc()
+    b = Hc.T @ d
+    mu = np.zeros(H.shape[1])
+    costs, z0s = [], []
+    for _ in range(n_iter):
+        delta, cost, Z0 = am_step(Hc, b, mu, d, I0)
+        costs.append(cost)
+        z0s.append(Z0)
+        mu += delta
+    costs.append(idiv(d, I0, Hc @ mu))
+    out = mu.reshape(shape) if shape is not None else mu
+    return AMResult(mu, out, np.array(costs), np.array(z0s), None, [], np.array([H.shape[1]] * n_iter))

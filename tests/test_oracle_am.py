@@ -1,0 +1,272 @@
+"""Pins of the oracle's Algorithm 1 (unregularised wavelet AM) and plain AM:
+the closed-form root against bracketing on Eq. 1.9, the surrogate of Eq. 1.8
+majorising the cost, closed-form fixed points, the textbook AM log-ratio,
+monotone decrease (Summary: guaranteed decrease at every iteration), the
+expansion rule of the Results section, and Phi = H Omega against closed-form
+chords through the children of a Haar block."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+import scipy.stats as st
+
+from oracle import am, haar
+from oracle import system_matrix as smx
+from paper_1508_04458_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def eq19(delta, b, bp, bm, Z0):
+    return b - bp * math.exp(-Z0 * delta) - bm * math.exp(Z0 * delta)
+
+
+def test_root_matches_bracketing_on_eq19():
+    rng = np.random.default_rng(0)
+    n = 400
+    b = rng.standard_normal(n) * 10.0 ** rng.uniform(-2, 3, n)
+    bp = rng.uniform(0, 1, n) * 10.0 ** rng.uniform(-2, 3, n)
+    bm = -rng.uniform(0, 1, n) * 10.0 ** rng.uniform(-2, 3, n)
+    bm[::5] = 0.0                       # approximation-like coefficients
+    Z0 = 37.5
+    got = am.am_root(b, bp, bm, Z0)
+    for i in range(n):
+        if bm[i] == 0.0 and b[i] <= 0.0:
+            assert got[i] == pytest.approx(am.CLAMP / Z0)
+            continue
+        ref = so.brentq(eq19, -am.CLAMP / Z0, am.CLAMP / Z0, args=(b[i], bp[i], bm[i], Z0),
+                        xtol=1e-300, rtol=1e-15, maxiter=500) \
+            if np.sign(eq19(-am.CLAMP / Z0, b[i], bp[i], bm[i], Z0)) != \
+            np.sign(eq19(am.CLAMP / Z0, b[i], bp[i], bm[i], Z0)) else None
+        if ref is None:
+            assert abs(got[i]) == pytest.approx(am.CLAMP / Z0)
+        else:
+            assert got[i] == pytest.approx(ref, rel=1e-10, abs=1e-13)
+
+
+def test_root_degenerate_cases():
+    Z0 = 2.0
+    # nothing sees the coefficient
+    assert am.am_root([0.0], [0.0], [0.0], Z0)[0] == 0.0
+    # only negative weights: u = bm / b
+    assert am.am_root([-3.0], [0.0], [-1.5], Z0)[0] == pytest.approx(-math.log(0.5) / Z0)
+    # minimiser at +infinity (b <= 0, no negative part) and -infinity
+    assert am.am_root([-1.0], [2.0], [0.0], Z0)[0] == pytest.approx(am.CLAMP / Z0)
+    assert am.am_root([1.0], [0.0], [-2.0], Z0)[0] == pytest.approx(-am.CLAMP / Z0)
+    # plain AM: bm = 0 gives the log-ratio
+    assert am.am_root([2.0], [5.0], [0.0], Z0)[0] == pytest.approx(math.log(5.0 / 2.0) / Z0)
+
+
+def test_idiv_is_poisson_log_likelihood_ratio():
+    # Sec. II: minimising I(d||q) is maximising the Poisson log-likelihood;
+    # I(d||q) = log P(d | mean d) - log P(d | mean q)
+    rng = np.random.default_rng(1)
+    q = rng.uniform(0.5, 50, 300)
+    d = rng.poisson(q).astype(float)
+    d[:7] = 0.0
+    I0 = 60.0
+    p = np.log(I0 / q)
+    ll = st.poisson.logpmf(d, q).sum()
+    ll_sat = st.poisson.logpmf(d, np.where(d > 0, d, 1e-300)).sum()
+    assert am.idiv(d, I0, p) == pytest.approx(ll_sat - ll, rel=1e-10)
+    assert am.idiv(d[d > 0], I0, np.log(I0 / d[d > 0])) == pytest.approx(0.0, abs=1e-9)
+
+
+def _small(kind=I.FAN2D_FLAT, nx=32, ny=24, V=30, B=41, seed=7):
+    p = I.small_problem(nx, ny, V, B, kind=kind, seed=seed)
+    return p, smx.system_matrix(p.geom)
+
+
+def test_single_pixel_fixed_point():
+    # one 1x1 mm pixel, rays through it with h = 1 (horizontal and vertical
+    # lines through its interior); equal counts d: the ML estimate is
+    # mu* = ln(I0 / d) / h, reached by AM in one step (Z0 = 1)
+    seg = np.array([[-2.0, y, 2.0, y] for y in (-0.3, 0.0, 0.2)] +
+                   [[x, -2.0, x, 2.0] for x in (-0.4, 0.1)])
+    H = smx.siddon_matrix(seg, (1, 1), (1.0, 1.0))
+    np.testing.assert_allclose(H.toarray().ravel(), 1.0)
+    I0, dbar = 1000.0, 250.0
+    r = am.plain_am(H, np.full(5, dbar), I0, 3)
+    assert r.beta[0] == pytest.approx(math.log(I0 / dbar), rel=1e-14)
+    assert r.cost[-1] == pytest.approx(0.0, abs=1e-9)
+
+
+def test_plain_am_first_step_is_textbook_log_ratio():
+    # Omega = I: mu1 = mu0 + (1/Z0) ln(H^T qhat / H^T d) with qhat = I0 at mu0 = 0,
+    # Z0 = max_y sum_x h(y|x) = the longest chord through the image
+    p, H = _small(kind=I.PARALLEL2D)
+    r = am.plain_am(H, p.d, p.I0, 1)
+    ones = np.full(H.shape[0], p.I0)
+    b = H.T @ p.d.ravel()
+    bq = H.T @ ones
+    seen = b > 0
+    Z0 = np.max(np.asarray(H.sum(axis=1)))
+    np.testing.assert_allclose(r.beta[seen], np.log(bq[seen] / b[seen]) / Z0, rtol=1e-12)
+    g = p.geom
+    lo = (-0.5 * g.nx * g.vx, -0.5 * g.ny * g.vy)
+    # the longest chord of any ray through the image rectangle (slab clipping)
+    best = 0.0
+    for s in smx.ray_segments(g):
+        d = s[2:] - s[:2]
+        t0, t1 = 0.0, 1.0
+        for k in range(2):
+            if d[k] != 0:
+                a1, a2 = (lo[k] - s[k]) / d[k], (-lo[k] - s[k]) / d[k]
+                t0, t1 = max(t0, min(a1, a2)), min(t1, max(a1, a2))
+        best = max(best, max(0.0, t1 - t0) * np.linalg.norm(d))
+    assert r.z0[0] == pytest.approx(best, rel=1e-12)
+
+
+def test_wavelet_am_with_no_levels_is_plain_am():
+    p, H = _small()
+    a = am.plain_am(H, p.d, p.I0, 6)
+    w = am.wavelet_am(H, p.d, p.I0, p.geom.nx, p.geom.ny, 0, 6)
+    np.testing.assert_allclose(w.beta, a.beta, rtol=1e-12, atol=1e-15)
+
+
+def _surrogate(Ps, b_s, beta_hat, beta, qhat, Z0):
+    """F^(beta) of Eq. 1.8 up to the constant: sum_z b beta + sum_y qhat *
+    [sum_z r exp(-(phi/r)(beta - beta_hat)) + (1 - sum_z r)], r = |phi|/Z0."""
+    P = Ps.toarray()
+    r = np.abs(P) / Z0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(r > 0, P / np.where(r > 0, r, 1.0), 0.0)
+    ex = r * np.exp(-ratio * (beta - beta_hat)[None, :])
+    return b_s @ beta + qhat @ (ex.sum(axis=1) + 1.0 - r.sum(axis=1))
+
+
+def test_surrogate_majorises_and_update_minimises_it():
+    p, H = _small(nx=16, ny=16, V=20, B=29)
+    nx, ny, L = 16, 16, 2
+    Om = haar.basis_matrix(nx, ny, L)
+    Phi = (H @ Om).tocsc()
+    d = p.d.ravel()
+    b = Phi.T @ d
+    tree = am.empty_tree(nx, ny, L)
+    tree[1][0, 1] = tree[1][1, 1] = True
+    tree[0][0, 2] = True
+    act = am.active_mask(tree, nx, ny, L)
+    Ps = Phi[:, act]
+    rng = np.random.default_rng(2)
+    beta_hat = rng.normal(0.0, 0.05, act.sum())
+    beta_hat[: (nx >> L) * (ny >> L)] = 0.08
+    qhat = p.I0 * np.exp(-(Ps @ beta_hat))
+    Z0 = float(np.max(np.asarray(abs(Ps).sum(axis=1))))
+
+    def F(beta):  # the cost minus its beta-independent constant
+        return b[act] @ beta + np.sum(p.I0 * np.exp(-(Ps @ beta)))
+
+    Fh = _surrogate(Ps, b[act], beta_hat, beta_hat, qhat, Z0)
+    assert Fh == pytest.approx(F(beta_hat), rel=1e-12)
+    for _ in range(20):
+        beta = beta_hat + rng.normal(0, 0.02, beta_hat.size)
+        assert _surrogate(Ps, b[act], beta_hat, beta, qhat, Z0) >= F(beta) - 1e-9 * abs(F(beta))
+    delta, cost, z0 = am.am_step(Ps, b[act], beta_hat, d, p.I0)
+    assert z0 == pytest.approx(Z0)
+    new = beta_hat + delta
+    # the update is the surrogate's minimiser: no coordinate move lowers it
+    s0 = _surrogate(Ps, b[act], beta_hat, new, qhat, Z0)
+    for k in rng.choice(new.size, 25, replace=False):
+        for h in (1e-4, -1e-4):
+            e = new.copy()
+            e[k] += h
+            assert _surrogate(Ps, b[act], beta_hat, e, qhat, Z0) >= s0 - 1e-9 * abs(s0)
+    assert F(new) <= F(beta_hat)
+
+
+@pytest.mark.parametrize("kind", [I.PARALLEL2D, I.FAN2D_FLAT])
+def test_monotone_decrease_with_expansions(kind):
+    p, H = _small(kind=kind, nx=32, ny=32, V=36, B=49, seed=11)
+    r = am.wavelet_am(H, p.d, p.I0, 32, 32, 3, 30, expand_at=(5, 10, 20), taus=(0.1, 0.03, -1.0))
+    assert np.all(np.diff(r.cost) <= 1e-12 * r.cost[:-1])
+    assert r.n_active[0] == 16 and r.n_active[-1] > r.n_active[0]
+    assert len(r.trees) == 3
+    a = am.plain_am(H, p.d, p.I0, 30)
+    assert np.all(np.diff(a.cost) <= 1e-12 * a.cost[:-1])
+
+
+def test_noiseless_block_constant_object_is_recovered():
+    # data consistent with a block-constant mu_true (in the span of the
+    # level-L approximations): coarse AM drives mu towards mu_true and the
+    # surrogate gradient b - bhat+ - bhat- towards 0
+    nx = ny = 16
+    L = 2
+    g = I.Geometry(kind=I.PARALLEL2D, nx=nx, ny=ny, n_views=24, angle0=0.1,
+                   angle_span=math.pi, n_bins=31, bin_pitch=0.8)
+    H = smx.system_matrix(g)
+    rng = np.random.default_rng(4)
+    blocks = rng.uniform(0.01, 0.05, (ny >> L, nx >> L))
+    mu_true = np.kron(blocks, np.ones((1 << L, 1 << L)))
+    I0 = 1e4
+    d = I0 * np.exp(-(H @ mu_true.ravel()))
+    r1 = am.wavelet_am(H, d, I0, nx, ny, L, 20)
+    r2 = am.wavelet_am(H, d, I0, nx, ny, L, 200)
+    e1 = np.linalg.norm(r1.mu - mu_true)
+    e2 = np.linalg.norm(r2.mu - mu_true)
+    assert e2 < 0.5 * e1 and e2 < 0.05 * np.linalg.norm(mu_true)
+    assert r2.cost[-1] < 1e-4 * r2.cost[0]
+
+
+def test_expansion_golden():
+    g = json.load(open(os.path.join(GOLD, "expand_8x8.json")))
+    ny, nx = g["shape"]
+    L = g["L"]
+    S = np.zeros((ny, nx))
+    for y, x, v in g["S_nonzero"]:
+        S[y, x] = v
+    tree = am.empty_tree(nx, ny, L)
+    for step in g["after_step"]:
+        tree = am.expand(tree, S, g["tau"])
+        for lev, key in ((2, "level2"), (1, "level1")):
+            want = np.zeros_like(tree[lev - 1])
+            for by, bx in step[key]:
+                want[by, bx] = True
+            np.testing.assert_array_equal(tree[lev - 1], want)
+
+
+def test_phi_equals_child_chords():
+    # phi(y|z) for a level-l detail = 2^-l sum_k s_k chord(y, child_k): the
+    # children are 2^(l-1)-pixel squares; chords by slab clipping
+    p, H = _small(nx=32, ny=32, V=12, B=45)
+    g = p.geom
+    nx, ny, L = 32, 32, 3
+    Phi = (H @ haar.basis_matrix(nx, ny, L)).tocsc()
+    seg = smx.ray_segments(g)
+    ox, oy = -0.5 * nx, -0.5 * ny
+
+    def chord(s, x0, y0, w):
+        d = s[2:] - s[:2]
+        t0, t1 = 0.0, 1.0
+        for k, (lo, hi) in enumerate(((x0, x0 + w), (y0, y0 + w))):
+            if d[k] == 0:
+                if not lo <= s[k] < hi:
+                    return 0.0
+                continue
+            a1, a2 = (lo - s[k]) / d[k], (hi - s[k]) / d[k]
+            t0, t1 = max(t0, min(a1, a2)), min(t1, max(a1, a2))
+        return max(0.0, t1 - t0) * np.linalg.norm(d)
+
+    level, typ, bx, by = haar.coefficient_info(nx, ny, L)
+    rng = np.random.default_rng(9)
+    for z in rng.choice(nx * ny, 60, replace=False):
+        l, t = int(level[z]), int(typ[z])
+        s = 1 << l
+        h = s // 2
+        x0, y0 = ox + bx[z] * s, oy + by[z] * s
+        col = Phi[:, z].toarray().ravel()
+        for y in range(0, H.shape[0], 7):
+            c = [chord(seg[y], x0 + i * h, y0 + j * h, h) for j in (0, 1) for i in (0, 1)]
+            # c = [ylo-xlo, ylo-xhi, yhi-xlo, yhi-xhi]
+            if t == -1:
+                want = sum(c) / s
+            elif t == 0:
+                want = (c[0] + c[1] - c[2] - c[3]) / s
+            elif t == 1:
+                want = (c[0] - c[1] + c[2] - c[3]) / s
+            else:
+                want = (c[0] - c[1] - c[2] + c[3]) / s
+            assert col[y] == pytest.approx(want, abs=1e-12)

@@ -1,0 +1,154 @@
+"""Pins of the oracle's system matrix H (Sec. II: h(y|x) = length of ray y in
+voxel x) against hand derivations, closed forms and brute force."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import system_matrix as smx
+from paper_1508_04458_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def box_chord(p1, p2, lo, hi):
+    """Closed-form length of segment p1->p2 inside the box [lo, hi] (slab clipping)."""
+    p1, p2 = np.asarray(p1, float), np.asarray(p2, float)
+    d = p2 - p1
+    t0, t1 = 0.0, 1.0
+    for k in range(len(p1)):
+        if d[k] == 0.0:
+            if not (lo[k] <= p1[k] < hi[k]):
+                return 0.0
+            continue
+        a, b = (lo[k] - p1[k]) / d[k], (hi[k] - p1[k]) / d[k]
+        t0, t1 = max(t0, min(a, b)), min(t1, max(a, b))
+    return max(0.0, t1 - t0) * float(np.linalg.norm(d))
+
+
+def test_hand_derived_chords():
+    g = json.load(open(os.path.join(GOLD, "siddon_chords.json")))
+    for ray in g["rays"]:
+        seg = np.array([ray["p1"] + ray["p2"]])
+        H = smx.siddon_matrix(seg, (2, 2), (1.0, 1.0)).toarray()[0]
+        want = np.zeros(4)
+        for k, v in ray["h"].items():
+            want[int(k)] = v
+        np.testing.assert_allclose(H, want, atol=1e-14, err_msg=ray["why"])
+
+
+def test_single_pixel_chords_closed_form():
+    # one 1x1 pixel at the origin; lines through its centre at angle a have
+    # chord 1/max(|cos a|, |sin a|)
+    rng = np.random.default_rng(3)
+    for a in rng.uniform(0, math.pi, 50):
+        dvec = np.array([math.cos(a), math.sin(a)])
+        seg = np.array([np.concatenate([-3 * dvec, 3 * dvec])])
+        h = smx.siddon_matrix(seg, (1, 1), (1.0, 1.0)).toarray()[0, 0]
+        assert abs(h - 1.0 / max(abs(math.cos(a)), abs(math.sin(a)))) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [I.PARALLEL2D, I.FAN2D_FLAT])
+def test_row_sums_equal_box_chord(kind):
+    p = I.small_problem(48, 40, 24, 37, kind=kind)
+    g = p.geom
+    H = smx.system_matrix(g)
+    seg = smx.ray_segments(g)
+    lo = (-0.5 * g.nx * g.vx, -0.5 * g.ny * g.vy)
+    hi = (0.5 * g.nx * g.vx, 0.5 * g.ny * g.vy)
+    rows = np.asarray(H.sum(axis=1)).ravel()
+    want = np.array([box_chord(s[:2], s[2:], lo, hi) for s in seg])
+    np.testing.assert_allclose(rows, want, rtol=0, atol=1e-12)
+    assert (want > 0).mean() > 0.5
+
+
+def test_uniform_disk_line_integrals():
+    # parallel-beam projection of a disk image sampled finely: the chord
+    # 2 mu sqrt(R^2 - s^2) within an O(pixel) band
+    n, pix, R, mu = 128, 0.5, 25.0, 0.02
+    g = I.Geometry(kind=I.PARALLEL2D, nx=n, ny=n, vx=pix, vy=pix, n_views=8,
+                   angle0=0.05, angle_span=math.pi, n_bins=61, bin_pitch=1.0)
+    ss = 8
+    sub = (np.arange(ss) + 0.5) / ss
+    c = -0.5 * n * pix + (np.arange(n)[:, None] + sub[None, :]).ravel() * pix
+    X, Y = np.meshgrid(c, c)
+    img = (X * X + Y * Y < R * R).astype(float).reshape(n, ss, n, ss).mean(axis=(1, 3)) * mu
+    H = smx.system_matrix(g)
+    proj = (H @ img.ravel()).reshape(g.n_views, g.n_bins)
+    s = (np.arange(g.n_bins) - 30.0) * g.bin_pitch
+    exact = 2 * mu * np.sqrt(np.maximum(R * R - s * s, 0.0))
+    # rays crossing the boundary see at most ~2 partly-filled pixels per side
+    band = 4 * mu * pix * math.sqrt(2)
+    assert np.max(np.abs(proj - exact[None, :])) < band
+    # and the total attenuation (integral over s) matches mu * area to O(pixel)
+    area = (proj.sum(axis=1) * g.bin_pitch)
+    assert np.max(np.abs(area - mu * math.pi * R * R)) < 0.01 * mu * math.pi * R * R
+
+
+def test_brute_force_8x8():
+    # fine point sampling along random rays; each pixel's share of samples
+    # times the ray length approaches h(y|x)
+    rng = np.random.default_rng(11)
+    n = 8
+    nsamp = 100000
+    seg = []
+    for _ in range(20):
+        a = rng.uniform(0, 2 * math.pi)
+        p = rng.uniform(-3, 3, 2)
+        dvec = np.array([math.cos(a), math.sin(a)])
+        seg.append(np.concatenate([p - 7 * dvec, p + 7 * dvec]))
+    seg = np.array(seg)
+    H = smx.siddon_matrix(seg, (n, n), (1.0, 1.0)).toarray()
+    for r, s in enumerate(seg):
+        t = (np.arange(nsamp) + 0.5) / nsamp
+        pts = s[:2][None, :] + t[:, None] * (s[2:] - s[:2])[None, :]
+        ix = np.floor(pts[:, 0] + 4).astype(int)
+        iy = np.floor(pts[:, 1] + 4).astype(int)
+        ok = (ix >= 0) & (ix < n) & (iy >= 0) & (iy < n)
+        step = np.linalg.norm(s[2:] - s[:2]) / nsamp
+        est = np.bincount(iy[ok] * n + ix[ok], minlength=n * n) * step
+        assert np.max(np.abs(est - H[r])) < 2.5 * step
+
+
+def test_pixel_orientation():
+    # a single hot pixel at (ix, iy): at view 0 of a parallel scan (rays along
+    # e = (1, 0), detector axis u = (0, 1)) it shadows the bin at u = y_centre;
+    # at the view a quarter turn later (u = (-1, 0)) the bin at u = -x_centre.
+    n = 16
+    g = I.Geometry(kind=I.PARALLEL2D, nx=n, ny=n, n_views=4, angle0=0.0,
+                   angle_span=2 * math.pi, n_bins=16, bin_pitch=1.0)
+    img = np.zeros((n, n))
+    ix, iy = 10, 3
+    img[iy, ix] = 1.0
+    proj = (smx.system_matrix(g) @ img.ravel()).reshape(4, 16)
+    y_c = -8 + iy + 0.5
+    x_c = -8 + ix + 0.5
+    assert np.argmax(proj[0]) == int(round(y_c + 7.5))
+    assert np.argmax(proj[1]) == int(round(-x_c + 7.5))
+    np.testing.assert_allclose(proj[0].sum(), 1.0, atol=1e-12)
+
+
+def test_quarter_turn_symmetry_fan():
+    # rotating the object by +90 deg equals shifting the views by a quarter
+    # of a full turn (fan beam over 360 deg with V divisible by 4)
+    p = I.small_problem(32, 32, 16, 29, kind=I.FAN2D_FLAT)
+    g = p.geom
+    H = smx.system_matrix(g)
+    rng = np.random.default_rng(5)
+    img = rng.random((32, 32))
+    # rot +90 (counter-clockwise): new(x, y) = old(R^-1 (x, y)) = old(y, -x)
+    rot = np.rot90(img, k=1).copy()   # numpy rows are y; verify the mapping below
+    X = np.arange(32) - 15.5
+    # check mapping: rot[iy, ix] should equal img at (x', y') = (y, -x)
+    iy, ix = 5, 20
+    x, y = X[ix], X[iy]
+    jx, jy = int(y + 15.5), int(-x + 15.5)
+    if rot[iy, ix] != img[jy, jx]:
+        rot = np.rot90(img, k=-1).copy()
+        assert rot[iy, ix] == img[jy, jx]
+    a = (H @ img.ravel()).reshape(g.n_views, g.n_bins)
+    b = (H @ rot.ravel()).reshape(g.n_views, g.n_bins)
+    q = g.n_views // 4
+    np.testing.assert_allclose(b[q:], a[:-q], rtol=1e-10, atol=1e-10)
