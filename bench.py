@@ -1,0 +1,379 @@
+"""Benchmark: multiresolution (wavelet-tree) AM on the 2-D fan-beam baggage
+workload (512x512 at 1 mm, 720 views over 360 deg, 1024 bins x 1.2 mm, I0 1e5,
+4-level Haar tree with the adaptive threshold schedule, 100 iterations).
+
+One step = one complete reconstruction through the C-ABI (precompute of
+b = Phi^T d, then per iteration: tree-masked synthesis, ray-driven projection
+with Beer's law and the FP64 I-divergence, split back-projection, AM update;
+tree expansions with Z0 recomputation after iterations 8, 16, 32, 64).
+value = AM iterations per second over all ranks (weak scaling: every rank
+reconstructs its own seeded bag; no collective on the data path).
+
+Also reported: the same rate end to end from host buffers (e2e), plain
+full-image AM's rate, time to reach plain AM's final I-divergence, the
+dominant kernel's roofline, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wam|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-target I-divergence and AM iters/s, multires vs full AM; projector GB/s"
+WORKLOAD = "fan512: 2-D fan beam 512x512 @1 mm, 720 views x 1024 bins, I0 1e5, L=4 Haar tree, 100 AM iterations"
+L_LEVELS = 4
+N_ITERS = 100
+EXPAND_AT = (8, 16, 32, 64)
+TAU = (0.1, 0.03, 0.01, -1.0)       # adaptive threshold: last expansion takes every leaf
+TTT_MAX_ITERS = 300                 # multires iterations allowed to reach the target
+K_MIN = 10                          # FP32 instructions per ray-rectangle intersection (floor)
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(problem, view_stride: int, n_iters: int):
+    """Time the FP64 oracle's Algorithm 1 on every view_stride-th view of the
+    workload (full image; the schedule scaled to n_iters, i.e. expansions
+    after n_iters * (8, 16, 32, 64) / 100 iterations, so the tree spends the
+    same share of iterations at each size).  Its cost per iteration is linear
+    in the number of rays, so the rate is scaled by view_stride to the full
+    workload."""
+    from oracle import am
+    from oracle import system_matrix as smx
+    from paper_1508_04458_gb300 import inputs as I
+
+    g = problem.geom
+    sub = I.Geometry(**{**g.__dict__, "n_views": g.n_views // view_stride,
+                        "angle_span": g.angle_span * ((g.n_views // view_stride) * view_stride) / g.n_views})
+    d = problem.d[::view_stride][: sub.n_views]
+    t0 = time.perf_counter()
+    H = smx.system_matrix(sub)
+    exp_at = tuple(sorted(set(max(1, round(n_iters * e / N_ITERS)) for e in EXPAND_AT)))
+    r = am.wavelet_am(H, d, problem.I0, g.nx, g.ny, L_LEVELS, n_iters,
+                      expand_at=exp_at, taus=TAU[: len(exp_at)])
+    dt = time.perf_counter() - t0
+    rate = n_iters / dt / view_stride
+    return rate, dt, r
+
+
+def run_reference(args, problem, world):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    stride, iters = 30, 25
+    for _ in range(args.warmup):
+        oracle_sample(problem, stride, iters)
+    times = []
+    for _ in range(args.steps):
+        rate, dt, _ = oracle_sample(problem, stride, iters)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * iters / total / stride
+    cores = os.cpu_count()
+    sample = ("every %dth view (%d of %d), full 512x512 image, %d iterations, expansions at the same "
+              "fractions of the run; rate scaled by %d" % (stride, problem.geom.n_views // stride,
+                                                          problem.geom.n_views, iters, stride))
+    line = {"metric": METRIC, "value": value, "unit": "AM iters/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "AM iters/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "AM iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_wam(args, problem, world, rank, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1508_04458_gb300 import wam
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    g = problem.geom
+    N, M = g.nx * g.ny, g.n_views * g.n_bins
+    ctx = wam.Context(g)
+    d_dev = torch.from_numpy(problem.d.astype(np.float32).ravel()).to(dev)
+    ctx.set_data(d_dev, problem.I0)
+
+    def step(n_iters=N_ITERS, levels=L_LEVELS, full=False):
+        return ctx.reconstruct(levels, n_iters, () if full else EXPAND_AT, () if full else TAU,
+                               precision=32, full_am=full, device_out=True)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K complete reconstructions, L2 flushed between them
+    ctx.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = wam.kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            mu, hist, masks, st = step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    launches = wam.kernel_launches() - launches0
+    stats = ctx.stats()
+    ctx.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_ms = float(sum(step_ms))
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t_max.item())
+    value = world * args.steps * N_ITERS / (dev_ms_max / 1e3)
+    hist_mr = hist.cpu().numpy()
+
+    # ---- plain full-image AM and time to target (outside the timed region)
+    def timed(fn):
+        torch.cuda.synchronize()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    step(full=True, levels=0)
+    (mu_f, hist_f, _, _), full_ms = timed(lambda: step(full=True, levels=0))
+    hist_f = hist_f.cpu().numpy()
+    target = float(hist_f[-1]) * (1.0 + 1e-3)
+    (_, hist_long, _, _), long_ms = timed(lambda: step(n_iters=TTT_MAX_ITERS))
+    hist_long = hist_long.cpu().numpy()
+    hit = np.nonzero(hist_long <= target)[0]
+    ttt_mr = None
+    j_hit = None
+    if hit.size:
+        j_hit = int(hit[0])
+        _, ttt_mr = timed(lambda: step(n_iters=j_hit))
+    # plain AM's own time to its final value is its full run
+    (_, _, _, _), full_ms2 = timed(lambda: step(full=True, levels=0))
+
+    # ---- e2e through the C-ABI from host buffers
+    d_host = np.ascontiguousarray(problem.d.astype(np.float32).ravel())
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_data(d_host, problem.I0)
+        mu_h, hist_h, masks_h, _ = ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    e2e = {"value": args.steps * N_ITERS / e2e_s, "unit": "AM iters/s",
+           "h2d_bytes_per_step": int(d_host.nbytes + 4),
+           "d2h_bytes_per_step": int(mu_h.nbytes + hist_h.nbytes + masks_h.nbytes)}
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * args.steps * N_ITERS / float(t.item())
+
+    # ---- roofline of the dominant kernel (ALU bound: ray-rectangle intersections)
+    dom = max(("forward", "backproject"), key=lambda k: stats[k]["ms"])
+    sd = stats[dom]
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * 128 * clk_mhz * 1e6 / K_MIN / 1e9            # G intersections / s
+    per_launch_work = sd["work"] / max(1, sd["launches"])
+    per_launch_ms = sd["ms"] / max(1, sd["launches"])
+    achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            traffic = tj.get(dom, {}).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+                "unit": "G ray-rectangle intersections/s", "frac": achieved / peak if peak else None,
+                "traffic": traffic,
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS sm_max_mhz) / %d "
+                              "instructions per intersection" % (sms, clk_mhz, K_MIN),
+                "work_per_launch": per_launch_work, "ms_per_launch": per_launch_ms}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        stride, iters = 15, 25
+        rate, dt, _ = oracle_sample(problem, stride, iters)
+        cpu = {"value": rate, "unit": "AM iters/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "every %dth view (%d of %d), full 512x512 image, %d iterations, expansions at the "
+                         "same fractions of the run, %.1f s; rate scaled by %d" % (stride, g.n_views // stride,
+                                                                                 g.n_views, iters, dt, stride)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "AM iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": L_LEVELS, "iterations": N_ITERS,
+                       "expand_after": list(EXPAND_AT), "tau": list(TAU),
+                       "l2": "flushed between steps (256 MiB write)",
+                       "cost_precision": "f64", "seed": 1509},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "roofline": roofline, "cpu_baseline": cpu,
+            "multires": {"final_idiv": float(hist_mr[-1]), "ms_per_iter": dev_ms_max / args.steps / N_ITERS,
+                         "time_to_target_ms": ttt_mr, "iters_to_target": j_hit,
+                         "idiv_after_%d" % TTT_MAX_ITERS: float(hist_long[-1]),
+                         "ms_%d_iters" % TTT_MAX_ITERS: long_ms},
+            "full_am": {"iters_per_s": N_ITERS / (full_ms2 / 1e3), "final_idiv": float(hist_f[-1]),
+                        "ms_per_iter": full_ms2 / N_ITERS, "time_to_target_ms": full_ms2},
+            "target_idiv": target,
+            "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "work": v["work"]}
+                        for k, v in stats.items()},
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def profile_case():
+    """A small case of the same kernels: 256x256 bag, 360 views x 512 bins."""
+    import torch
+    from paper_1508_04458_gb300 import inputs as I
+    from paper_1508_04458_gb300 import wam
+    p = I.problem_fan(256, 360, 512, 1e5, seed=I.SEED_BASE + 3)
+    ctx = wam.Context(p.geom)
+    ctx.set_data(p.d.astype(np.float32), p.I0)
+    for _ in range(2):
+        ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32, device_out=True)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run two reconstructions of a 256x256 fan-beam bag (360 views x 512 bins) "
+                         "for kernel profiling, print nothing")
+    args = ap.parse_args()
+    if args.profile_case:
+        profile_case()
+        return
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    from paper_1508_04458_gb300 import inputs as I
+    problem = I.problem_fan512(seed=I.SEED_BASE + 1 + rank)
+
+    if args.impl == "reference":
+        run_reference(args, problem, world)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_wam(args, problem, world, rank, local_rank)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

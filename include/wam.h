@@ -1,0 +1,244 @@
+/*
+ * libwam: multiresolution (wavelet-tree) alternating minimisation for
+ * transmission CT on one GPU (sm_103a).
+ *
+ * Method: Degirmenci, O'Sullivan, Politte, "Multiresolution approach to
+ * acceleration of iterative image reconstruction for X-ray imaging for
+ * security applications" (arXiv 1508.04458).  Sec. II poses the problem:
+ * counts d(y) with mean q(mu)(y) = I0(y) exp(-sum_x h(y|x) mu(x)), h(y|x)
+ * the length of ray y inside voxel x, mu = Omega beta (Eq. 1.2) with Omega an
+ * orthonormal Haar synthesis, minimised in I-divergence by Algorithm 1 over a
+ * tree of active coefficients that grows as in the Results section.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Image: nx * ny pixels of vx * vy mm centred at the origin, row-major,
+ *    x fastest: pixel (ix, iy) is mu[iy * nx + ix] and covers
+ *    [-nx vx/2 + ix vx, ... + vx) x [-ny vy/2 + iy vy, ... + vy).
+ *  - Scan: view k at theta_k = angle0 + k * angle_span / n_views,
+ *    e = (cos, sin), u = (-sin, cos); bin b at
+ *    u_b = (b - (n_bins - 1) / 2) * bin_pitch along u.  Parallel beam: ray =
+ *    line through u_b u with direction e.  Flat-detector fan beam: ray = segment
+ *    from the source SOD e to the detector point -(SDD - SOD) e + u_b u.
+ *    Sinograms are [n_views][n_bins], ray index y = k * n_bins + b.
+ *  - Haar coefficients (orthonormal, levels 1..L, block of a level-l
+ *    coefficient = 2^l x 2^l pixels, basis value +-2^-l): vector of length
+ *    nx*ny holding the level-L approximations ((ny>>L) x (nx>>L), row-major),
+ *    then for l = L, L-1, ..., 1 the detail planes h_l, v_l, d_l (each
+ *    (ny>>l) x (nx>>l)).  h is + on the lower-y half of its block, v is + on
+ *    the lower-x half, d is their product.
+ *  - Tree masks ("masks"): bytes, one per block and level, for l = L, L-1,
+ *    ..., 1 in turn, each level (ny>>l) x (nx>>l) row-major; nonzero = the
+ *    block is expanded, i.e. its three level-l details are active.  The
+ *    level-L approximations are always active.  Total size wam_mask_bytes().
+ *  - Pointers named on_device / documented as device pointers are
+ *    caller-owned CUDA device memory used on `stream` (a cudaStream_t, NULL =
+ *    the legacy default stream); the library never retains them after the
+ *    call returns.  Host pointers are read or written before the call returns.
+ *  - Errors: every call returns a wam_status; no C++ exception crosses this
+ *    boundary.  On error the context keeps a message (wam_last_error) and
+ *    stays usable unless the status is WAM_ERR_CUDA from a sticky CUDA error.
+ */
+#ifndef WAM_H
+#define WAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WAM_MAX_LEVELS 8
+
+typedef enum {
+    WAM_OK = 0,
+    WAM_ERR_ARG = -1,      /* invalid argument; nothing was launched */
+    WAM_ERR_OOM = -2,      /* device allocation failed */
+    WAM_ERR_CUDA = -3,     /* a CUDA call failed */
+    WAM_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    WAM_ERR_STATE = -5,    /* call order violated (e.g. no data set) */
+    WAM_WARN_NONMONOTONE = 1 /* reconstruction finished, but the cost rose
+                                by more than the rounding band at least once */
+} wam_status;
+
+enum { WAM_PARALLEL2D = 0, WAM_FAN2D_FLAT = 1, WAM_CONE3D_FLAT_CIRCULAR = 2 };
+
+/* Scan geometry (Sec. II names H only abstractly; the scan is ours). */
+typedef struct {
+    int kind;                 /* WAM_PARALLEL2D or WAM_FAN2D_FLAT */
+    int nx, ny, nz;           /* voxels; nz = 1 for 2-D */
+    double vx, vy, vz;        /* voxel size, mm */
+    int n_views;
+    double angle0, angle_span;/* rad */
+    int n_bins, n_rows;       /* n_rows = 1 for 2-D */
+    double bin_pitch, row_pitch; /* mm on the detector */
+    double sod, sdd;          /* fan beam: source-origin, source-detector, mm */
+} wam_geometry;
+
+/* Reconstruction schedule (Algorithm 1 + the Results section's tree growth). */
+typedef struct {
+    int levels;               /* Haar levels L, 0..WAM_MAX_LEVELS (ignored if full_am) */
+    int dims;                 /* 2 */
+    int n_iters;              /* J */
+    int n_expand;             /* number of tree expansions */
+    const int* expand_at;     /* host [n_expand]: expand after this many iterations */
+    const double* tau;        /* host [n_expand]: threshold factor; < 0 = every leaf */
+    int zsum_criterion;       /* reserved for the per-slice 3-D mode (0) */
+    int precision;            /* 32 (FP32 bulk) or 64 (FP64 everywhere) */
+    int full_am;              /* 1: plain AM, Omega = I, every pixel active */
+    double dmax_clamp;        /* clamp on |Z0 * delta|; <= 0 means 30 */
+} wam_schedule;
+
+typedef struct wam_ctx wam_ctx;
+
+/* ---- life cycle --------------------------------------------------------- */
+
+/* Create a context for one geometry on the current CUDA device.  The context
+ * owns its device buffers (allocated here and on first use by a schedule).
+ * Errors: WAM_ERR_ARG for a bad geometry (non-positive sizes, fan beam with
+ * SOD <= image circumradius or SDD <= SOD), WAM_ERR_OOM, WAM_ERR_CUDA. */
+wam_status wam_create(const wam_geometry* g, wam_ctx** out);
+
+/* Free every device buffer and the context.  NULL is ignored. */
+void wam_destroy(wam_ctx* ctx);
+
+/* Message of the last error on this context ("" if none).  Owned by ctx. */
+const char* wam_last_error(const wam_ctx* ctx);
+
+/* Bytes of a tree mask for L levels (sum over l = 1..L of (ny>>l)(nx>>l)). */
+size_t wam_mask_bytes(const wam_ctx* ctx, int levels);
+
+/* ---- data --------------------------------------------------------------- */
+
+/* Set the counts d [n_views][n_bins] (>= 0, finite) and the incident counts
+ * I0 (> 0): one value if I0_is_scalar, else one per ray.  With on_device = 0
+ * both are host arrays, copied in; with on_device = 1 they are device
+ * arrays.  Precomputes d log(d / I0) - d per ray (the cost's constant part,
+ * Sec. II footnote).  Errors: WAM_ERR_ARG for negative or non-finite d,
+ * I0 <= 0. */
+wam_status wam_set_data(wam_ctx* ctx, const float* d, const float* I0, int I0_is_scalar,
+                        int on_device, void* stream);
+
+/* ---- the whole method ---------------------------------------------------- */
+
+/* Algorithm 1 (or plain AM when sched->full_am): starting from beta = 0,
+ * run sched->n_iters iterations, expanding the tree after the listed
+ * iterations.  Outputs (any may be NULL):
+ *   mu_out    [nx*ny] final image mu = Omega beta; float* when precision 32,
+ *             double* when 64; host or device per on_device
+ *   idiv_hist [n_iters + 1] I(d || qhat^(j)), j = 0..n_iters, FP64, host or
+ *             device per on_device (entry j is the cost before update j; the
+ *             last one is the cost of the final image)
+ *   mask_out  [wam_mask_bytes(L)] final tree, host or device per on_device
+ * Returns WAM_WARN_NONMONOTONE when some cost exceeded its predecessor by
+ * more than 1e-6 relative (FP32) or 1e-11 (FP64).  Errors: WAM_ERR_STATE if
+ * no data were set; WAM_ERR_ARG for a bad schedule (nx, ny not divisible by
+ * 2^L, expand_at not increasing, precision not 32/64). */
+wam_status wam_reconstruct(wam_ctx* ctx, const wam_schedule* sched, void* mu_out,
+                           double* idiv_hist, unsigned char* mask_out, int on_device,
+                           void* stream);
+
+/* ---- the steps of one iteration (device pointers) ------------------------ */
+
+/* H: p(y) = sum_x h(y|x) mu(x) by exact ray traversal (Sec. II).
+ * mu [nx*ny], p [n_views*n_bins].  _f64 takes double arrays. */
+wam_status wam_project(wam_ctx* ctx, const float* mu, float* p, void* stream);
+wam_status wam_project_f64(wam_ctx* ctx, const double* mu, double* p, void* stream);
+
+/* H^T: g(x) = sum_y h(y|x) s(y), voxel-driven with the same exact h.
+ * s [n_views*n_bins], g [nx*ny].  Deterministic (no atomics). */
+wam_status wam_backproject(wam_ctx* ctx, const float* s, float* g, void* stream);
+wam_status wam_backproject_f64(wam_ctx* ctx, const double* s, double* g, void* stream);
+
+/* Full orthonormal Haar transform with L levels: analysis (inverse = 0,
+ * image -> coefficients, Omega^T) or synthesis (inverse = 1, Omega).
+ * in, out [nx*ny] FP64, distinct. */
+wam_status wam_haar(wam_ctx* ctx, int levels, const double* in, double* out, int inverse,
+                    void* stream);
+
+/* a1, Eq. 1.2: mu = Omega beta over the tree: only active coefficients are
+ * read (inactive ones are taken as 0).  beta [nx*ny] FP64, masks as above,
+ * mu [nx*ny]. */
+wam_status wam_synthesize(wam_ctx* ctx, int levels, const unsigned char* masks,
+                          const double* beta, float* mu, void* stream);
+
+/* a2+a3, Algorithm 1 first line and Sec. II footnote: for an image mu that is
+ * constant on the leaves of the tree (as wam_synthesize produces),
+ * qhat(y) = I0(y) exp(-sum_x h(y|x) mu(x)) and the FP64 cost
+ * I(d || qhat).  The projection visits one leaf block at a time.  masks = NULL
+ * treats every pixel as a leaf.  qhat [n_views*n_bins]; cost: one double in
+ * device memory.  Needs wam_set_data. */
+wam_status wam_forward(wam_ctx* ctx, int levels, const unsigned char* masks, const float* mu,
+                       float* qhat, double* cost, void* stream);
+wam_status wam_forward_f64(wam_ctx* ctx, int levels, const unsigned char* masks,
+                           const double* mu, double* qhat, double* cost, void* stream);
+
+/* a4, Eq. 1.10: bhat+(z) = sum over rays with phi(y|z) > 0 of qhat(y) phi(y|z)
+ * and bhat-(z) over phi < 0, for every active z, phi = H Omega computed per
+ * (ray, block) from exact chords through the block's four children.
+ * Inactive entries are set to 0.  bplus, bminus [nx*ny] FP64 in coefficient
+ * layout.  levels = 0 gives H^T qhat in bplus (pixel basis). */
+wam_status wam_split_backproject(wam_ctx* ctx, int levels, const unsigned char* masks,
+                                 const float* qhat, double* bplus, double* bminus, void* stream);
+
+/* a5, Eq. 1.61: Z0 = max_y sum_{z active} |phi(y|z)|; one double written to
+ * device memory. */
+wam_status wam_z0(wam_ctx* ctx, int levels, const unsigned char* masks, double* z0,
+                  void* stream);
+
+/* a6, Eq. 1.9 / Algorithm 1 inner loop: for every active z, beta(z) +=
+ * Delta, Delta the zero of b - bhat+ e^{-Z0 Delta} - bhat- e^{Z0 Delta}
+ * (stable quadratic root; |Z0 Delta| clamped to `clamp`, <= 0 means 30).
+ * b, bplus, bminus, beta [nx*ny] FP64 coefficient layout; z0 a device
+ * double.  Inactive entries of beta are untouched. */
+wam_status wam_update(wam_ctx* ctx, int levels, const unsigned char* masks, const double* b,
+                      const double* bplus, const double* bminus, const double* z0, double clamp,
+                      double* beta, void* stream);
+
+/* a7, Results section: one tree expansion.  Every pixel with S > tau * max S
+ * (compared in FP64; tau < 0 selects every pixel) expands its current leaf
+ * (read from mask_in) by one level.  S [nx*ny]; mask_in, mask_out distinct
+ * device arrays of wam_mask_bytes(levels). */
+wam_status wam_expand(wam_ctx* ctx, int levels, const float* S, double tau,
+                      const unsigned char* mask_in, unsigned char* mask_out, void* stream);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Kernel classes timed by wam_profile. */
+enum {
+    WAM_K_FORWARD = 0,     /* ray-driven projection + Beer's law + cost terms */
+    WAM_K_BACKPROJECT = 1, /* voxel-driven (split) back-projection */
+    WAM_K_UPDATE = 2,      /* partial-sum reduction + AM update */
+    WAM_K_Z0 = 3,          /* Z0 row sums */
+    WAM_K_SYNTH = 4,       /* tree-masked synthesis */
+    WAM_K_TREE = 5,        /* expansion criterion, leaf map, block lists, Haar */
+    WAM_NKERNEL = 6
+};
+
+typedef struct {
+    double ms[WAM_NKERNEL];                /* summed device time (CUDA events), ms */
+    unsigned long long launches[WAM_NKERNEL];
+    /* algorithmic work: FORWARD = leaf blocks visited by rays (ray-rectangle
+     * intersections), BACKPROJECT = ray-rectangle chords evaluated (4 per
+     * (block, ray) pair for a block with active details, 1 otherwise), Z0 =
+     * leaf blocks visited; other classes 0 */
+    unsigned long long work[WAM_NKERNEL];
+} wam_stats;
+
+/* enable = 1: reset the statistics and, from now on, bracket every kernel
+ * launch of wam_reconstruct with CUDA events on its stream and count its
+ * work; enable = 0 stops.  Adds two event records per launch. */
+wam_status wam_profile(wam_ctx* ctx, int enable);
+
+/* Statistics gathered since wam_profile(ctx, 1); synchronises the stream
+ * of the last profiled call.  out must not be NULL. */
+wam_status wam_get_stats(wam_ctx* ctx, wam_stats* out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long wam_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAM_H */

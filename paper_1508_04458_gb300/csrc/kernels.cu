@@ -1,0 +1,834 @@
+// CUDA kernels of libwam (sm_103a).  Each kernel is one step of the
+// multiresolution AM iteration (Algorithm 1 and the Results section's tree
+// growth).  All reductions run in a fixed order: results are deterministic.
+#include "wam_internal.cuh"
+#include "wam_kernels.h"
+
+#include <math.h>
+
+#include <atomic>
+
+namespace wam {
+
+// ---------------------------------------------------------------------------
+// deterministic block reductions
+// ---------------------------------------------------------------------------
+
+template <typename V, typename Op>
+__device__ __forceinline__ V warp_reduce(V x, Op op)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = op(x, __shfl_down_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Reduce over the CTA; the result is valid in thread 0.  Fixed tree order.
+template <typename V, typename Op>
+__device__ __forceinline__ V block_reduce(V x, Op op, V identity)
+{
+    __shared__ V sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    x = warp_reduce(x, op);
+    if (lane == 0) sh[wid] = x;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    x = (threadIdx.x < nw) ? sh[threadIdx.x] : identity;
+    if (wid == 0) x = warp_reduce(x, op);
+    __syncthreads();
+    return x;
+}
+
+// Warp-aggregated add of a per-thread count into a 64-bit device counter.
+__device__ __forceinline__ void add_work(unsigned long long* work, unsigned cnt)
+{
+    if (!work) return;
+    const unsigned m = __activemask();
+    const unsigned tot = __reduce_add_sync(m, cnt);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicAdd(work, (unsigned long long)tot);
+}
+
+struct OpSum {
+    template <typename V> __device__ V operator()(V a, V b) const { return a + b; }
+};
+struct OpMax {
+    template <typename V> __device__ V operator()(V a, V b) const { return a > b ? a : b; }
+};
+
+// ---------------------------------------------------------------------------
+// a2 + a3: ray-driven forward projection over the tree's leaves, fused with
+// Beer's law and the I-divergence terms (Sec. II and its footnote).
+// One thread per ray; CTA = (bin tile, view).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFwdTPB)
+k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
+          const float* __restrict__ d, const double* __restrict__ dterm,
+          const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
+          double* __restrict__ cost_part, unsigned long long* __restrict__ work)
+{
+    const int v = blockIdx.y;
+    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    double term = 0.0;
+    unsigned steps = 0;
+    if (b < g.B) {
+        Ray<T> r;
+        T acc = T(0);
+        if (make_ray(g, v, b, r)) {
+            traverse(g, leaf, r, [&](int ix, int iy, int, int, int, T c) {
+                acc += c * __ldg(mu + iy * g.nx + ix);
+                ++steps;
+            });
+        }
+        const size_t y = (size_t)v * g.B + b;
+        if (p_out) p_out[y] = acc;
+        if (qhat) {
+            const T q = T(I0[y]) * exp(-acc);
+            qhat[y] = q;
+            // d log(d/q) - d + q = [d (log d - log I0) - d] + d p + q
+            term = dterm[y] + (double)d[y] * (double)acc + (double)q;
+        }
+    }
+    add_work(work, steps);
+    if (cost_part) {
+        term = block_reduce(term, OpSum(), 0.0);
+        if (threadIdx.x == 0) cost_part[blockIdx.y * gridDim.x + blockIdx.x] = term;
+    }
+}
+
+// Sum n partials in a fixed order (one CTA of 256 threads).
+__global__ void k_sum_final(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_reduce(s, OpSum(), 0.0);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_max_final(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    double s = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, part[i]);
+    s = block_reduce<double>(s, OpMax(), -INFINITY);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------------------
+// a5, Eq. 1.61: per ray sum over active z of |phi(y|z)|, then max over rays.
+// The ray walks the leaves; each leaf's chord is added to the accumulator of
+// the child (quadrant) it lies in, for every expanded ancestor block.  A
+// convex block is crossed in one contiguous run of leaves, so an ancestor's
+// |phi| terms are final when the next ancestor of that level appears.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFwdTPB)
+k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict__ part)
+{
+    const int v = blockIdx.y;
+    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    double rowsum = 0.0;
+    if (b < g.B) {
+        Ray<T> r;
+        if (make_ray(g, v, b, r)) {
+            T acc[kMaxLevels][4];
+            int cur[kMaxLevels];
+#pragma unroll
+            for (int l = 0; l < kMaxLevels; ++l) {
+                cur[l] = -1;
+                acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = T(0);
+            }
+            T total = T(0), rs = T(0);
+            const int L = lay.L;
+            auto flush = [&](int li) {
+                if (cur[li] >= 0) {
+                    const T* a = acc[li];
+                    const T s = T(1) / T(1 << (li + 1));
+                    rs += s * (fabs(a[0] + a[1] - a[2] - a[3]) + fabs(a[0] - a[1] + a[2] - a[3]) +
+                               fabs(a[0] - a[1] - a[2] + a[3]));
+                }
+                acc[li][0] = acc[li][1] = acc[li][2] = acc[li][3] = T(0);
+            };
+            traverse(g, leaf, r, [&](int ix, int iy, int lam, int bx0, int by0, T c) {
+                total += c;
+#pragma unroll
+                for (int li = 0; li < kMaxLevels; ++li) {
+                    const int l = li + 1;
+                    if (l > lam && l <= L) {
+                        const int id = ((iy >> l) << 16) | (ix >> l);
+                        if (id != cur[li]) { flush(li); cur[li] = id; }
+                        const int q = (((by0 >> li) & 1) << 1) | ((bx0 >> li) & 1);
+                        acc[li][0] += q == 0 ? c : T(0);
+                        acc[li][1] += q == 1 ? c : T(0);
+                        acc[li][2] += q == 2 ? c : T(0);
+                        acc[li][3] += q == 3 ? c : T(0);
+                    }
+                }
+            });
+#pragma unroll
+            for (int li = 0; li < kMaxLevels; ++li) flush(li);
+            rowsum = (double)rs + (double)total / (double)(1 << L);
+        }
+    }
+    rowsum = block_reduce(rowsum, OpMax(), 0.0);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = rowsum;
+}
+
+// ---------------------------------------------------------------------------
+// a4 (Eq. 1.10) and H^T: voxel-driven split back-projection.  One thread per
+// (block, view range).  For each view the block's shadow on the detector is
+// found from its corners; for each ray in it the chords through the four
+// children give phi for the approximation (all +) and the three details (Haar
+// signs), and qhat*phi is added to the + or - accumulator by the sign of phi.
+// Partials are written per view range and summed later in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBackTPB)
+k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino, T* __restrict__ part,
+              unsigned long long* __restrict__ work)
+{
+    const int cta = blockIdx.x;
+    int si = 0;
+    while (si + 1 < tab.n && cta >= tab.s[si + 1].cta_begin) ++si;
+    const Segment& S = tab.s[si];
+    const int local = cta - S.cta_begin;
+    const int chunk = local / S.tiles, tile = local - chunk * S.tiles;
+    const int item = tile * kBackTPB + threadIdx.x;
+    if (item >= S.n_items) return;
+    int bx, by;
+    if (S.items) {
+        const uint32_t w = S.items[item];
+        bx = (int)(w & 0xffffu);
+        by = (int)(w >> 16);
+    } else {
+        bx = item % S.gw;
+        by = item / S.gw;
+    }
+    const int bsz = 1 << S.level;
+    const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
+    const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
+    const T scale = T(1) / T(bsz);
+    const int v0 = chunk * S.vpc;
+    const int v1 = min(g.V, v0 + S.vpc);
+    const bool fan = g.kind != 0;
+    const bool det = S.has_details != 0;
+    T aA = 0, hP = 0, hM = 0, vP = 0, vM = 0, dP = 0, dM = 0;
+    unsigned evals = 0;
+    for (int v = v0; v < v1; ++v) {
+        const T c = g.cs[2 * v], s = g.cs[2 * v + 1];
+        const T ac = cx * c + cy * s;        // block centre along e
+        const T wc = -cx * s + cy * c;       // ... along u
+        // shadow of the block: detector coordinates of its corners
+        T umin = T(1e30), umax = T(-1e30);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T x = cx + ((k & 1) ? hx : -hx), y = cy + ((k & 2) ? hy : -hy);
+            const T wu = -x * s + y * c;
+            const T uu = fan ? g.sdd * wu / (g.sod - (x * c + y * s)) : wu;
+            umin = fmin(umin, uu);
+            umax = fmax(umax, uu);
+        }
+        const int blo = max(0, (int)floor(umin / g.pitch + g.ucen));
+        const int bhi = min(g.B - 1, (int)ceil(umax / g.pitch + g.ucen));
+        const T kappa = fan ? (g.sod - ac) / g.sdd : T(1);
+        const T* row = sino + (size_t)v * g.B;
+        evals += (unsigned)max(0, bhi - blo + 1);
+        for (int bb = blo; bb <= bhi; ++bb) {
+            const T ub = (T(bb) - g.ucen) * g.pitch;
+            const T delta = ub * kappa - wc;         // ray offset from the centre along u
+            const T qx = -delta * s, qy = delta * c;
+            T dx, dy;
+            if (fan) {
+                const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
+                dx = (-g.sdd * c - ub * s) * rn;
+                dy = (-g.sdd * s + ub * c) * rn;
+            } else {
+                dx = c;
+                dy = s;
+            }
+            const T idx = safe_rcp(dx), idy = safe_rcp(dy);
+            const T q = __ldg(row + bb);
+            if (det) {
+                T c00, c01, c10, c11;
+                child_chords(qx, qy, idx, idy, hx, hy, c00, c01, c10, c11);
+                const T qs = q * scale;
+                aA += qs * (c00 + c01 + c10 + c11);
+                const T ph = qs * (c00 + c01 - c10 - c11);
+                const T pv = qs * (c00 - c01 + c10 - c11);
+                const T pd = qs * (c00 - c01 - c10 + c11);
+                if (ph > T(0)) hP += ph; else hM += ph;
+                if (pv > T(0)) vP += pv; else vM += pv;
+                if (pd > T(0)) dP += pd; else dM += pd;
+            } else {
+                aA += q * scale * block_chord(qx, qy, idx, idy, hx, hy);
+            }
+        }
+    }
+    add_work(work, det ? 4u * evals : evals);
+    T* out = part + S.part_off + (size_t)chunk * S.n_slots * S.n_items + item;
+    const size_t st = (size_t)S.n_items;
+    int k = 0;
+    if (S.has_approx) out[st * k++] = aA;
+    if (det) {
+        out[st * k++] = hP; out[st * k++] = hM;
+        out[st * k++] = vP; out[st * k++] = vM;
+        out[st * k++] = dP; out[st * k++] = dM;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// helpers over segment items
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int find_item_segment(const SegTable& tab, int gid)
+{
+    int si = 0;
+    while (si + 1 < tab.n && gid >= tab.s[si + 1].item_begin) ++si;
+    return si;
+}
+
+__device__ __forceinline__ void item_block(const Segment& S, int item, int& bx, int& by)
+{
+    if (S.items) {
+        const uint32_t w = S.items[item];
+        bx = (int)(w & 0xffffu);
+        by = (int)(w >> 16);
+    } else {
+        bx = item % S.gw;
+        by = item / S.gw;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double sum_slot(const Segment& S, const T* __restrict__ part, int item, int slot)
+{
+    double s = 0.0;
+    const T* p = part + S.part_off + (size_t)slot * S.n_items + item;
+    const size_t stride = (size_t)S.n_slots * S.n_items;
+    for (int c = 0; c < S.n_chunks; ++c) s += (double)p[c * stride];
+    return s;
+}
+
+__device__ __forceinline__ long long approx_index(const Layout& lay, int level, int bx, int by)
+{
+    return level == 0 ? (long long)by * lay.nx + bx : (long long)by * lay.gw[lay.L] + bx;
+}
+
+__device__ __forceinline__ long long detail_index(const Layout& lay, int level, int t, int bx, int by)
+{
+    return lay.coff[level] + (long long)t * lay.gw[level] * lay.gh[level] + (long long)by * lay.gw[level] + bx;
+}
+
+// Eq. 1.9 = 0 solved for Delta = beta~ - betahat.  With u = exp(-Z0 Delta):
+// bp u^2 - b u + bm = 0, bp >= 0 >= bm, whose positive root is taken in the
+// form free of cancellation for the sign of b.  No ray weight (bp = bm = 0):
+// Delta = 0.  A minimiser at +-infinity is clamped to |Z0 Delta| = clamp.
+__device__ __forceinline__ double am_delta(double b, double bp, double bm, double z0, double clamp)
+{
+    double t;   // = Z0 * Delta = -ln u
+    if (bp > 0.0) {
+        const double disc = sqrt(b * b - 4.0 * bp * bm);
+        const double u = (b >= 0.0) ? (b + disc) / (2.0 * bp) : 2.0 * bm / (b - disc);
+        t = (u > 0.0) ? -log(u) : clamp;
+    } else if (bm < 0.0) {
+        t = (b < 0.0) ? -log(bm / b) : -clamp;
+    } else {
+        t = 0.0;
+    }
+    t = fmin(fmax(t, -clamp), clamp);
+    return t / z0;
+}
+
+// a6: reduce the partials of each item and apply the AM update to beta.
+template <typename T>
+__global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
+                         const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= tab.total_items) return;
+    const Segment& S = tab.s[find_item_segment(tab, gid)];
+    const int item = gid - S.item_begin;
+    int bx, by;
+    item_block(S, item, bx, by);
+    const double z0 = *z0p;
+    int slot = 0;
+    if (S.has_approx) {
+        const long long z = approx_index(lay, S.level, bx, by);
+        beta[z] += am_delta(bvec[z], sum_slot(S, part, item, 0), 0.0, z0, clamp);
+        slot = 1;
+    }
+    if (S.has_details) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const long long z = detail_index(lay, S.level, t, bx, by);
+            const double bp = sum_slot(S, part, item, slot + 2 * t);
+            const double bm = sum_slot(S, part, item, slot + 2 * t + 1);
+            beta[z] += am_delta(bvec[z], bp, bm, z0, clamp);
+        }
+    }
+}
+
+// Scatter the reduced bhat+ / bhat- of each item into coefficient layout.
+template <typename T>
+__global__ void k_split_out(SegTable tab, Layout lay, const T* __restrict__ part, double* __restrict__ bplus,
+                            double* __restrict__ bminus)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= tab.total_items) return;
+    const Segment& S = tab.s[find_item_segment(tab, gid)];
+    const int item = gid - S.item_begin;
+    int bx, by;
+    item_block(S, item, bx, by);
+    int slot = 0;
+    if (S.has_approx) {
+        const long long z = approx_index(lay, S.level, bx, by);
+        bplus[z] = sum_slot(S, part, item, 0);
+        if (bminus) bminus[z] = 0.0;
+        slot = 1;
+    }
+    if (S.has_details) {
+        for (int t = 0; t < 3; ++t) {
+            const long long z = detail_index(lay, S.level, t, bx, by);
+            bplus[z] = sum_slot(S, part, item, slot + 2 * t);
+            if (bminus) bminus[z] = sum_slot(S, part, item, slot + 2 * t + 1);
+        }
+    }
+}
+
+// Pixel-basis back-projection result (level-0 segment) into an image.
+template <typename T, typename O>
+__global__ void k_reduce_pixels(SegTable tab, const T* __restrict__ part, O* __restrict__ out)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= tab.total_items) return;
+    const Segment& S = tab.s[0];
+    out[gid] = (O)sum_slot(S, part, gid, 0);
+}
+
+// ---------------------------------------------------------------------------
+// a1, Eq. 1.2: mu = Omega beta over the tree.  Per pixel, only the levels
+// above its leaf carry active details; below they are inactive (zero).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
+                        T* __restrict__ mu)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= lay.nx * lay.ny) return;
+    const int ix = p % lay.nx, iy = p / lay.nx;
+    const int L = lay.L;
+    if (L == 0) {
+        mu[p] = (T)beta[p];
+        return;
+    }
+    const int lam = leaf ? (int)leaf[p] : 0;
+    double v = beta[(long long)(iy >> L) * lay.gw[L] + (ix >> L)] / (double)(1 << L);
+    for (int l = L; l > lam; --l) {
+        const int bx = ix >> l, by = iy >> l;
+        const double sh = ((iy >> (l - 1)) & 1) ? -1.0 : 1.0;
+        const double sv = ((ix >> (l - 1)) & 1) ? -1.0 : 1.0;
+        const long long n = (long long)lay.gw[l] * lay.gh[l];
+        const long long z = lay.coff[l] + (long long)by * lay.gw[l] + bx;
+        v += (sh * beta[z] + sv * beta[z + n] + sh * sv * beta[z + 2 * n]) / (double)(1 << l);
+    }
+    mu[p] = (T)v;
+}
+
+// Leaf level of every pixel from the masks.
+__global__ void k_leafmap(Layout lay, const uint8_t* __restrict__ mask, uint8_t* __restrict__ leaf)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= lay.nx * lay.ny) return;
+    const int ix = p % lay.nx, iy = p / lay.nx;
+    int lam = lay.L;
+    for (int l = lay.L; l >= 1; --l) {
+        if (mask[lay.moff[l] + (long long)(iy >> l) * lay.gw[l] + (ix >> l)]) lam = l - 1;
+        else break;
+    }
+    leaf[p] = (uint8_t)lam;
+}
+
+// ---------------------------------------------------------------------------
+// a7: the tree-growth criterion (Results section)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_max_partial(const T* __restrict__ S, int n, double* __restrict__ part)
+{
+    double m = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = fmax(m, (double)S[i]);
+    m = block_reduce<double>(m, OpMax(), -INFINITY);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+// thr = tau * max S, in FP64
+__global__ void k_threshold(const double* __restrict__ part, int n, double tau, double* __restrict__ thr)
+{
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, part[i]);
+    m = block_reduce<double>(m, OpMax(), -INFINITY);
+    if (threadIdx.x == 0) *thr = tau * m;
+}
+
+// Every selected pixel marks its leaf block (leaf read from the tree before
+// the step) as expanded in the new mask.  Stores of 1 are idempotent.
+template <typename T>
+__global__ void k_expand_mark(Layout lay, const T* __restrict__ S, const double* __restrict__ thr, int all,
+                              const uint8_t* __restrict__ leaf_old, uint8_t* __restrict__ mask_new)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= lay.nx * lay.ny) return;
+    const int lam = leaf_old[p];
+    if (lam < 1) return;
+    if (!all && !((double)S[p] > *thr)) return;
+    const int ix = p % lay.nx, iy = p / lay.nx;
+    mask_new[lay.moff[lam] + (long long)(iy >> lam) * lay.gw[lam] + (ix >> lam)] = 1;
+}
+
+// Compacted block lists, one CTA per list, blocks in Morton (Z) order so
+// that neighbouring threads of the back-projector hold neighbouring blocks.
+// List 0: level-L blocks not expanded; list 1: level-L blocks expanded;
+// list 1 + k (k = 1..L-1): expanded blocks of level L - k.
+__device__ __forceinline__ uint32_t compact_bits(uint32_t x)
+{
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    x = (x | (x >> 8)) & 0x0000ffffu;
+    return x;
+}
+
+__global__ void __launch_bounds__(1024) k_compact(Layout lay, const uint8_t* __restrict__ mask,
+                                                  uint32_t* __restrict__ lists, long long list_stride,
+                                                  int* __restrict__ counts)
+{
+    const int list = blockIdx.x;
+    const int level = list <= 1 ? lay.L : lay.L - (list - 1);
+    const int want = list == 0 ? 0 : 1;
+    const int gw = lay.gw[level], gh = lay.gh[level];
+    int side = 1;
+    while (side < gw || side < gh) side <<= 1;
+    const long long ncode = (long long)side * side;
+    uint32_t* out = lists + list_stride * list;
+    __shared__ int warp_cnt[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long m0 = 0; m0 < ncode; m0 += blockDim.x) {
+        const long long m = m0 + threadIdx.x;
+        bool keep = false;
+        int bx = 0, by = 0;
+        if (m < ncode) {
+            bx = (int)compact_bits((uint32_t)m);
+            by = (int)compact_bits((uint32_t)(m >> 1));
+            if (bx < gw && by < gh) {
+                const int e = mask[lay.moff[level] + (long long)by * gw + bx] ? 1 : 0;
+                keep = (e == want);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) warp_cnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < wid; ++w) off += warp_cnt[w];
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_cnt[w];
+        if (keep) out[base + off + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)by << 16) | (uint32_t)bx;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[list] = base;
+}
+
+// ---------------------------------------------------------------------------
+// full orthonormal Haar transform, one level per launch (FP64)
+// ---------------------------------------------------------------------------
+// analysis of level l: `a` is the level l-1 approximation image (w x h,
+// w = nx >> (l-1)); writes the level-l approximation into a_next and the
+// three detail planes into coef.
+__global__ void k_haar_analysis(Layout lay, int l, const double* __restrict__ a, double* __restrict__ a_next,
+                                double* __restrict__ coef)
+{
+    const int gw = lay.gw[l], gh = lay.gh[l];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gw * gh) return;
+    const int bx = i % gw, by = i / gw;
+    const int w = 2 * gw;
+    const double ll = a[(2 * by) * w + 2 * bx], lh = a[(2 * by) * w + 2 * bx + 1];
+    const double hl = a[(2 * by + 1) * w + 2 * bx], hh = a[(2 * by + 1) * w + 2 * bx + 1];
+    a_next[i] = 0.5 * (ll + lh + hl + hh);
+    const long long n = (long long)gw * gh;
+    double* c = coef + lay.coff[l];
+    c[i] = 0.5 * (ll + lh - hl - hh);
+    c[n + i] = 0.5 * (ll - lh + hl - hh);
+    c[2 * n + i] = 0.5 * (ll - lh - hl + hh);
+}
+
+__global__ void k_haar_synthesis(Layout lay, int l, const double* __restrict__ a, const double* __restrict__ coef,
+                                 double* __restrict__ a_prev)
+{
+    const int gw = lay.gw[l], gh = lay.gh[l];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gw * gh) return;
+    const int bx = i % gw, by = i / gw;
+    const int w = 2 * gw;
+    const long long n = (long long)gw * gh;
+    const double* c = coef + lay.coff[l];
+    const double A = a[i], h = c[i], v = c[n + i], d = c[2 * n + i];
+    a_prev[(2 * by) * w + 2 * bx] = 0.5 * (A + h + v + d);
+    a_prev[(2 * by) * w + 2 * bx + 1] = 0.5 * (A + h - v - d);
+    a_prev[(2 * by + 1) * w + 2 * bx] = 0.5 * (A - h + v - d);
+    a_prev[(2 * by + 1) * w + 2 * bx + 1] = 0.5 * (A - h - v + d);
+}
+
+// per-ray constant of the cost: d (log d - log I0) - d, 0 log 0 = 0
+__global__ void k_dterm(const float* __restrict__ d, const float* __restrict__ I0, long long n,
+                        double* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dd = d[i];
+    out[i] = dd > 0.0 ? dd * (log(dd) - log((double)I0[i])) - dd : 0.0;
+}
+
+__global__ void k_fill_f32(float* __restrict__ x, long long n, float v)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (B)x[i];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long kernel_launches() { return g_launches.load(); }
+#define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
+
+template <typename T>
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d,
+                           const double* dterm, const float* I0, T* qhat, T* p_out, double* cost_part,
+                           unsigned long long* work, cudaStream_t st)
+{
+    dim3 grid(nblk(g.B, kFwdTPB), g.V);
+    COUNT_LAUNCH();
+    k_forward<T><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
+    return cudaGetLastError();
+}
+
+int forward_parts(int V, int B) { return (int)nblk(B, kFwdTPB) * V; }
+
+cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_sum_final<<<1, 256, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_max_final<<<1, 256, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, double* part, cudaStream_t st)
+{
+    dim3 grid(nblk(g.B, kFwdTPB), g.V);
+    COUNT_LAUNCH();
+    k_z0<T><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, T* part,
+                               unsigned long long* work, cudaStream_t st)
+{
+    if (tab.total_ctas == 0) return cudaSuccess;
+    COUNT_LAUNCH();
+    k_backproject<T><<<tab.total_ctas, kBackTPB, 0, st>>>(g, tab, sino, part, work);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b,
+                          const double* z0, double clamp, double* beta, cudaStream_t st)
+{
+    if (tab.total_items == 0) return cudaSuccess;
+    COUNT_LAUNCH();
+    k_update<T><<<nblk(tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
+                             cudaStream_t st)
+{
+    if (tab.total_items == 0) return cudaSuccess;
+    COUNT_LAUNCH();
+    k_split_out<T><<<nblk(tab.total_items, 256), 256, 0, st>>>(tab, lay, part, bp, bm);
+    return cudaGetLastError();
+}
+
+template <typename T, typename O>
+cudaError_t launch_reduce_pixels(const SegTable& tab, const T* part, O* out, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_reduce_pixels<T, O><<<nblk(tab.total_items, 256), 256, 0, st>>>(tab, part, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_synth(const Layout& lay, const uint8_t* leaf, const double* beta, T* mu, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_synth<T><<<nblk((long long)lay.nx * lay.ny, 256), 256, 0, st>>>(lay, leaf, beta, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leafmap(const Layout& lay, const uint8_t* mask, uint8_t* leaf, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_leafmap<<<nblk((long long)lay.nx * lay.ny, 256), 256, 0, st>>>(lay, mask, leaf);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_expand(const Layout& lay, const T* S, double tau, const uint8_t* leaf_old,
+                          uint8_t* mask_new, double* scratch /* >= 257 doubles */, cudaStream_t st)
+{
+    const int n = lay.nx * lay.ny;
+    const int nb = 256;
+    COUNT_LAUNCH();
+    k_max_partial<T><<<nb, 256, 0, st>>>(S, n, scratch);
+    COUNT_LAUNCH();
+    k_threshold<<<1, 256, 0, st>>>(scratch, nb, tau, scratch + nb);
+    COUNT_LAUNCH();
+    k_expand_mark<T><<<nblk(n, 256), 256, 0, st>>>(lay, S, scratch + nb, tau < 0.0 ? 1 : 0, leaf_old, mask_new);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lists, long long list_stride,
+                           int* counts, cudaStream_t st)
+{
+    const int nlists = lay.L + 1;
+    COUNT_LAUNCH();
+    k_compact<<<nlists, 1024, 0, st>>>(lay, mask, lists, list_stride, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_haar(const Layout& lay, const double* in, double* out, int inverse, double* tmp_a,
+                        double* tmp_b, cudaStream_t st)
+{
+    const long long N = (long long)lay.nx * lay.ny;
+    if (lay.L == 0) return cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (!inverse) {
+        const double* a = in;
+        double* bufs[2] = {tmp_a, tmp_b};
+        for (int l = 1; l <= lay.L; ++l) {
+            double* an = (l == lay.L) ? out : bufs[l & 1];   // level-L approximations go first in `out`
+            COUNT_LAUNCH();
+            k_haar_analysis<<<nblk((long long)lay.gw[l] * lay.gh[l], 256), 256, 0, st>>>(lay, l, a, an, out);
+            a = an;
+        }
+    } else {
+        // start from the level-L approximations stored at the front of `in`
+        const double* a = in;
+        double* bufs[2] = {tmp_a, tmp_b};
+        for (int l = lay.L; l >= 1; --l) {
+            double* ap = (l == 1) ? out : bufs[l & 1];
+            COUNT_LAUNCH();
+            k_haar_synthesis<<<nblk((long long)lay.gw[l] * lay.gh[l], 256), 256, 0, st>>>(lay, l, a, in, ap);
+            a = ap;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_dterm<<<nblk(n, 256), 256, 0, st>>>(d, I0, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float* x, long long n, float v, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_fill_f32<<<nblk(n, 256), 256, 0, st>>>(x, n, v);
+    return cudaGetLastError();
+}
+
+template <typename A, typename B>
+cudaError_t launch_convert(const A* x, B* y, long long n, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_convert<A, B><<<nblk(n, 256), 256, 0, st>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+// a6 on dense coefficient arrays (the step-level entry point): every active
+// coefficient gets its AM step from given b, bhat+, bhat-.
+__global__ void k_update_dense(Layout lay, const uint8_t* __restrict__ mask, const double* __restrict__ bvec,
+                               const double* __restrict__ bp, const double* __restrict__ bm,
+                               const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
+{
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = (long long)lay.nx * lay.ny;
+    if (z >= N) return;
+    const int L = lay.L;
+    const long long nA = (long long)lay.gw[L] * lay.gh[L];
+    if (L > 0 && z >= nA) {
+        int l = L;
+        while (l > 1 && z >= lay.coff[l - 1]) --l;
+        const long long n = (long long)lay.gw[l] * lay.gh[l];
+        const long long r = (z - lay.coff[l]) % n;
+        const int bx = (int)(r % lay.gw[l]), by = (int)(r / lay.gw[l]);
+        if (!mask[lay.moff[l] + (long long)by * lay.gw[l] + bx]) return;
+    }
+    beta[z] += am_delta(bvec[z], bp[z], bm ? bm[z] : 0.0, *z0p, clamp);
+}
+
+cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const double* b, const double* bp,
+                                const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st)
+{
+    const long long N = (long long)lay.nx * lay.ny;
+    COUNT_LAUNCH();
+    k_update_dense<<<nblk(N, 256), 256, 0, st>>>(lay, mask, b, bp, bm, z0, clamp, beta);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+#define WAM_INST(T)                                                                                              \
+    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, const uint8_t*, const float*, const double*, \
+                                           const float*, T*, T*, double*, unsigned long long*, cudaStream_t);    \
+    template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
+    template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, T*,                    \
+                                               unsigned long long*, cudaStream_t);                              \
+    template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
+                                          double, double*, cudaStream_t);                                        \
+    template cudaError_t launch_split_out<T>(const SegTable&, const Layout&, const T*, double*, double*,         \
+                                             cudaStream_t);                                                      \
+    template cudaError_t launch_synth<T>(const Layout&, const uint8_t*, const double*, T*, cudaStream_t);        \
+    template cudaError_t launch_expand<T>(const Layout&, const T*, double, const uint8_t*, uint8_t*, double*,    \
+                                          cudaStream_t);
+WAM_INST(float)
+WAM_INST(double)
+#undef WAM_INST
+template cudaError_t launch_reduce_pixels<float, float>(const SegTable&, const float*, float*, cudaStream_t);
+template cudaError_t launch_reduce_pixels<float, double>(const SegTable&, const float*, double*, cudaStream_t);
+template cudaError_t launch_reduce_pixels<double, double>(const SegTable&, const double*, double*, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+
+}  // namespace wam

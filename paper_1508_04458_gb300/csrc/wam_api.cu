@@ -1,0 +1,859 @@
+// C-ABI of libwam: context, data, the reconstruction driver (Algorithm 1 with
+// the Results section's tree growth, or plain AM) and the step-level calls.
+// No exception crosses the boundary; every call returns a wam_status.
+#include "../../include/wam.h"
+#include "wam_internal.cuh"
+#include "wam_kernels.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace wam;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+enum BufId {
+    B_CS32, B_CS64, B_D, B_I0, B_DTERM,
+    B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
+    B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
+    B_NBUF
+};
+
+}  // namespace
+
+struct ProfPending {
+    int k;
+    cudaEvent_t a, b;
+};
+
+struct wam_ctx {
+    wam_geometry g{};
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<ProfPending> pend;
+    wam_stats stats{};
+    unsigned long long* dwork = nullptr;   // device [WAM_NKERNEL]
+    cudaStream_t prof_stream = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    std::string err;
+    bool has_data = false;
+    long long M = 0, N = 0;
+    Buf buf[B_NBUF];
+};
+
+namespace {
+
+wam_status fail(wam_ctx* c, wam_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define WCK(ctx, call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(ctx, WAM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+#define WST(call)                       \
+    do {                                \
+        wam_status s_ = (call);         \
+        if (s_ != WAM_OK) return s_;    \
+    } while (0)
+
+// Grow-only device buffer.
+wam_status ensure(wam_ctx* c, BufId id, size_t bytes, void** out)
+{
+    Buf& b = c->buf[id];
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(c, WAM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+        b.bytes = bytes;
+    }
+    *out = b.p;
+    return WAM_OK;
+}
+
+template <typename P>
+wam_status ensure_t(wam_ctx* c, BufId id, size_t count, P** out)
+{
+    void* p = nullptr;
+    WST(ensure(c, id, count * sizeof(P), &p));
+    *out = static_cast<P*>(p);
+    return WAM_OK;
+}
+
+// --- profiling ---------------------------------------------------------------
+cudaEvent_t take_event(wam_ctx* c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+struct ProfScope {
+    wam_ctx* c;
+    int k;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(wam_ctx* c_, int k_, cudaStream_t st_) : c(c_), k(k_), st(st_)
+    {
+        if (c->prof) {
+            a = take_event(c);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope()
+    {
+        if (!c->prof || !a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) {
+            c->ev_pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, st);
+        c->pend.push_back({k, a, b});
+        c->stats.launches[k] += 1;
+        c->prof_stream = st;
+    }
+};
+
+unsigned long long* work_ptr(wam_ctx* c, int k) { return c->prof && c->dwork ? c->dwork + k : nullptr; }
+
+wam_status prof_resolve(wam_ctx* c)
+{
+    if (c->pend.empty() && !c->dwork) return WAM_OK;
+    WCK(c, cudaStreamSynchronize(c->prof_stream));
+    for (auto& p : c->pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->stats.ms[p.k] += ms;
+        else cudaGetLastError();
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pend.clear();
+    if (c->dwork) {
+        unsigned long long h[WAM_NKERNEL];
+        WCK(c, cudaMemcpy(h, c->dwork, sizeof(h), cudaMemcpyDeviceToHost));
+        WCK(c, cudaMemset(c->dwork, 0, sizeof(h)));
+        for (int k = 0; k < WAM_NKERNEL; ++k) c->stats.work[k] += h[k];
+    }
+    return WAM_OK;
+}
+
+#define PROF(K) ProfScope prof_scope_##K(c, K, st)
+
+template <typename T>
+wam_status make_geom(wam_ctx* c, Geom<T>* g)
+{
+    const wam_geometry& w = c->g;
+    g->kind = w.kind;
+    g->nx = w.nx;
+    g->ny = w.ny;
+    g->V = w.n_views;
+    g->B = w.n_bins;
+    g->vx = (T)w.vx;
+    g->vy = (T)w.vy;
+    g->X0 = (T)(-0.5 * w.nx * w.vx);
+    g->Y0 = (T)(-0.5 * w.ny * w.vy);
+    g->ivx = (T)(1.0 / w.vx);
+    g->ivy = (T)(1.0 / w.vy);
+    g->pitch = (T)w.bin_pitch;
+    g->ucen = (T)(0.5 * (w.n_bins - 1));
+    g->sod = (T)w.sod;
+    g->sdd = (T)w.sdd;
+    T* cs = nullptr;
+    WST(ensure_t(c, sizeof(T) == 4 ? B_CS32 : B_CS64, 2 * (size_t)w.n_views, &cs));
+    g->cs = cs;
+    return WAM_OK;
+}
+
+wam_status upload_views(wam_ctx* c)
+{
+    const wam_geometry& w = c->g;
+    std::vector<double> cs64(2 * (size_t)w.n_views);
+    std::vector<float> cs32(cs64.size());
+    for (int k = 0; k < w.n_views; ++k) {
+        const double th = w.angle0 + k * (w.angle_span / w.n_views);
+        cs64[2 * k] = std::cos(th);
+        cs64[2 * k + 1] = std::sin(th);
+        cs32[2 * k] = (float)cs64[2 * k];
+        cs32[2 * k + 1] = (float)cs64[2 * k + 1];
+    }
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    WST(ensure_t(c, B_CS64, cs64.size(), &d64));
+    WST(ensure_t(c, B_CS32, cs32.size(), &d32));
+    WCK(c, cudaMemcpy(d64, cs64.data(), cs64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    WCK(c, cudaMemcpy(d32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return WAM_OK;
+}
+
+wam_status make_layout(wam_ctx* c, int L, Layout* lay)
+{
+    const wam_geometry& w = c->g;
+    if (L < 0 || L > WAM_MAX_LEVELS) return fail(c, WAM_ERR_ARG, "levels must be in 0..8");
+    if (w.nx % (1 << L) || w.ny % (1 << L))
+        return fail(c, WAM_ERR_ARG, "nx and ny must be divisible by 2^levels");
+    if ((w.nx >> 1) > 65535 || (w.ny >> 1) > 65535) return fail(c, WAM_ERR_ARG, "image too large");
+    std::memset(lay, 0, sizeof(*lay));
+    lay->L = L;
+    lay->nx = w.nx;
+    lay->ny = w.ny;
+    for (int l = 0; l <= L; ++l) {
+        lay->gw[l] = w.nx >> l;
+        lay->gh[l] = w.ny >> l;
+    }
+    long long off = (long long)lay->gw[L] * lay->gh[L];
+    long long moff = 0;
+    for (int l = L; l >= 1; --l) {
+        lay->coff[l] = off;
+        off += 3LL * lay->gw[l] * lay->gh[l];
+        lay->moff[l] = moff;
+        moff += (long long)lay->gw[l] * lay->gh[l];
+    }
+    lay->mask_bytes = moff;
+    return WAM_OK;
+}
+
+// --- back-projection work plan ------------------------------------------------
+
+struct ListInfo {
+    int level, has_approx, has_details, n;
+    const uint32_t* items;
+    int gw;
+};
+
+// Split every list into view ranges so that the whole grid holds about
+// 1024 threads per SM and each thread a similar number of chord evaluations.
+template <typename T>
+wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTable* tab, T** part_out)
+{
+    const wam_geometry& w = c->g;
+    std::memset(tab, 0, sizeof(*tab));
+    const double mag = (w.kind == WAM_FAN2D_FLAT) ? 1.2 * w.sdd / w.sod : 1.0;
+    const double diag = std::sqrt(w.vx * w.vx + w.vy * w.vy);
+    std::vector<double> cost(lists.size());
+    double total = 0.0;
+    for (size_t i = 0; i < lists.size(); ++i) {
+        const double shadow = (double)(1 << lists[i].level) * diag * mag / w.bin_pitch + 1.0;
+        cost[i] = shadow * (lists[i].has_details ? 3.0 : 1.0);
+        total += (double)lists[i].n * w.n_views * cost[i];
+    }
+    const double target_threads = (double)c->num_sms * 1024.0;
+    const double per_thread = std::max(total / target_threads, 256.0);
+    int cta = 0, items = 0;
+    long long part = 0;
+    for (size_t i = 0; i < lists.size(); ++i) {
+        const ListInfo& li = lists[i];
+        if (li.n == 0) continue;
+        if (tab->n >= kMaxSegs) return fail(c, WAM_ERR_ARG, "too many segments");
+        Segment& s = tab->s[tab->n++];
+        s.level = li.level;
+        s.has_approx = li.has_approx;
+        s.has_details = li.has_details;
+        s.n_items = li.n;
+        s.items = li.items;
+        s.gw = li.gw;
+        int vpc = (int)std::lround(per_thread / cost[i]);
+        vpc = std::max(1, std::min(vpc, w.n_views));
+        s.n_chunks = (w.n_views + vpc - 1) / vpc;
+        s.vpc = (w.n_views + s.n_chunks - 1) / s.n_chunks;
+        s.tiles = (li.n + kBackTPB - 1) / kBackTPB;
+        s.cta_begin = cta;
+        s.item_begin = items;
+        s.n_slots = li.has_approx + 6 * li.has_details;
+        s.part_off = part;
+        cta += s.tiles * s.n_chunks;
+        items += li.n;
+        part += (long long)s.n_slots * s.n_chunks * li.n;
+    }
+    tab->total_ctas = cta;
+    tab->total_items = items;
+    return ensure_t(c, B_PART, (size_t)std::max<long long>(part, 1), part_out);
+}
+
+template <typename T>
+wam_status plan_pixels(wam_ctx* c, SegTable* tab, T** part)
+{
+    std::vector<ListInfo> lists = {{0, 1, 0, (int)c->N, nullptr, c->g.nx}};
+    return plan_segments<T>(c, lists, tab, part);
+}
+
+// Rebuild leaf map, block lists and work plan from the mask (device); reads
+// the list lengths back (one small synchronous copy).
+template <typename T>
+wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t* leaf, SegTable* tab, T** part,
+                     cudaStream_t st)
+{
+    PROF(WAM_K_TREE);
+    WCK(c, launch_leafmap(lay, mask, leaf, st));
+    const int L = lay.L;
+    const long long stride = (long long)lay.gw[1] * lay.gh[1];
+    uint32_t* lists = nullptr;
+    int* counts = nullptr;
+    WST(ensure_t(c, B_LISTS, (size_t)stride * (L + 1), &lists));
+    WST(ensure_t(c, B_COUNTS, (size_t)(L + 1), &counts));
+    WCK(c, launch_compact(lay, mask, lists, stride, counts, st));
+    std::vector<int> h(L + 1);
+    WCK(c, cudaMemcpyAsync(h.data(), counts, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
+    WCK(c, cudaStreamSynchronize(st));
+    std::vector<ListInfo> li;
+    li.push_back({L, 1, 0, h[0], lists, lay.gw[L]});
+    li.push_back({L, 1, 1, h[1], lists + stride, lay.gw[L]});
+    for (int k = 1; k < L; ++k) li.push_back({L - k, 0, 1, h[k + 1], lists + stride * (k + 1), lay.gw[L - k]});
+    return plan_segments<T>(c, li, tab, part);
+}
+
+template <typename T>
+wam_status compute_z0(wam_ctx* c, const Geom<T>& g, const Layout& lay, const uint8_t* leaf, double* z0,
+                      cudaStream_t st)
+{
+    const int np = forward_parts(g.V, g.B);
+    double* part = nullptr;
+    WST(ensure_t(c, B_COSTPART, (size_t)np, &part));
+    WCK(c, launch_z0(g, lay, leaf, part, st));
+    WCK(c, launch_max_final(part, np, z0, st));
+    return WAM_OK;
+}
+
+wam_status check_geometry(const wam_geometry* g, std::string* why)
+{
+    if (!g) { *why = "geometry is NULL"; return WAM_ERR_ARG; }
+    if (g->kind != WAM_PARALLEL2D && g->kind != WAM_FAN2D_FLAT) { *why = "unsupported geometry kind"; return WAM_ERR_ARG; }
+    if (g->nx <= 0 || g->ny <= 0 || g->n_views <= 0 || g->n_bins <= 0) { *why = "sizes must be positive"; return WAM_ERR_ARG; }
+    if (g->nz > 1 || g->n_rows > 1) { *why = "2-D geometry expected (nz = n_rows = 1)"; return WAM_ERR_ARG; }
+    if (!(g->vx > 0) || !(g->vy > 0) || !(g->bin_pitch > 0)) { *why = "voxel size and bin pitch must be > 0"; return WAM_ERR_ARG; }
+    if (!std::isfinite(g->angle0) || !std::isfinite(g->angle_span)) { *why = "angles must be finite"; return WAM_ERR_ARG; }
+    if ((long long)g->nx * g->ny > (1LL << 31) - 1 || (long long)g->n_views * g->n_bins > (1LL << 31) - 1) {
+        *why = "problem too large for 32-bit indices"; return WAM_ERR_ARG;
+    }
+    if (g->nx > 65536 || g->ny > 65536) { *why = "image side above 65536"; return WAM_ERR_ARG; }
+    if (g->kind == WAM_FAN2D_FLAT) {
+        const double r = 0.5 * std::hypot(g->nx * g->vx, g->ny * g->vy);
+        if (!(g->sod > r)) { *why = "fan beam: SOD must exceed the image circumradius"; return WAM_ERR_ARG; }
+        if (!(g->sdd > g->sod)) { *why = "fan beam: SDD must exceed SOD"; return WAM_ERR_ARG; }
+    }
+    return WAM_OK;
+}
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+
+
+// ---------------------------------------------------------------------------
+// the reconstruction driver
+// ---------------------------------------------------------------------------
+template <typename T>
+wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
+                            int on_device, cudaStream_t st)
+{
+    const int L = sc->full_am ? 0 : sc->levels;
+    Layout lay;
+    WST(make_layout(c, L, &lay));
+    Geom<T> g;
+    WST(make_geom<T>(c, &g));
+    const long long N = c->N, M = c->M;
+    const int J = sc->n_iters;
+    const double clamp = sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0;
+
+    T *q = nullptr, *mu = nullptr, *sino = nullptr;
+    double *beta = nullptr, *bvec = nullptr, *costs = nullptr, *z0 = nullptr, *scratch = nullptr;
+    double *tmpa = nullptr, *tmpb = nullptr, *gimg = nullptr, *cpart = nullptr;
+    uint8_t *mask = nullptr, *mask2 = nullptr, *leaf = nullptr;
+    WST(ensure_t(c, B_Q, (size_t)M, &q));
+    WST(ensure_t(c, B_MU, (size_t)N, &mu));
+    WST(ensure_t(c, B_BETA, (size_t)N, &beta));
+    WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
+    WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
+    WST(ensure_t(c, B_Z0, 1, &z0));
+    WST(ensure_t(c, B_SCRATCH, 1024, &scratch));
+    WST(ensure_t(c, B_TMPA, (size_t)N, &tmpa));
+    WST(ensure_t(c, B_TMPB, (size_t)N, &tmpb));
+    WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
+    const int np = forward_parts(g.V, g.B);
+    WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+    if (L > 0) {
+        WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
+        WST(ensure_t(c, B_MASK_B, (size_t)lay.mask_bytes, &mask2));
+        WST(ensure_t(c, B_LEAF, (size_t)N, &leaf));
+    }
+    const float* dsino = static_cast<const float*>(c->buf[B_D].p);
+    const float* I0 = static_cast<const float*>(c->buf[B_I0].p);
+    const double* dterm = static_cast<const double*>(c->buf[B_DTERM].p);
+
+    // a0, Eq. 1.6: b = Phi^T d = Omega^T (H^T d) for every coefficient
+    SegTable pix;
+    T* part = nullptr;
+    WST(plan_pixels<T>(c, &pix, &part));
+    const T* dT;
+    if (sizeof(T) == sizeof(float)) {
+        dT = reinterpret_cast<const T*>(dsino);
+    } else {
+        WST(ensure_t(c, B_SINO, (size_t)M, &sino));
+        WCK(c, (launch_convert<float, double>(dsino, reinterpret_cast<double*>(sino), M, st)));
+        dT = sino;
+    }
+    {
+        PROF(WAM_K_BACKPROJECT);
+        WCK(c, launch_backproject(g, pix, dT, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+    }
+    {
+        PROF(WAM_K_TREE);
+        WCK(c, (launch_reduce_pixels<T, double>(pix, part, gimg, st)));
+        WCK(c, launch_haar(lay, gimg, bvec, 0, tmpa, tmpb, st));
+    }
+
+    // beta^(0) = 0; the tree holds the approximations only
+    WCK(c, cudaMemsetAsync(beta, 0, N * sizeof(double), st));
+    SegTable tab;
+    if (L > 0) {
+        WCK(c, cudaMemsetAsync(mask, 0, lay.mask_bytes, st));
+        WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+    } else {
+        tab = pix;
+    }
+    {
+        PROF(WAM_K_Z0);
+        WST(compute_z0<T>(c, g, lay, leaf, z0, st));
+    }
+
+    std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
+                            sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
+    size_t next_exp = 0;
+    for (int j = 0; j < J; ++j) {
+        {
+            PROF(WAM_K_SYNTH);
+            WCK(c, launch_synth(lay, leaf, beta, mu, st));                                  // a1
+        }
+        {
+            PROF(WAM_K_FORWARD);                                                            // a2, a3
+            WCK(c, launch_forward(g, mu, leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+                                  work_ptr(c, WAM_K_FORWARD), st));
+            WCK(c, launch_sum_final(cpart, np, costs + j, st));
+        }
+        {
+            PROF(WAM_K_BACKPROJECT);                                                        // a4
+            WCK(c, launch_backproject(g, tab, q, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+        }
+        {
+            PROF(WAM_K_UPDATE);                                                             // a6
+            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, st));
+        }
+        if (L > 0 && next_exp < exp_at.size() && exp_at[next_exp] == j + 1) {              // a7
+            const double tau = sc->tau[next_exp];
+            ++next_exp;
+            {
+                PROF(WAM_K_TREE);
+                WCK(c, launch_synth(lay, leaf, beta, mu, st));
+                WCK(c, cudaMemcpyAsync(mask2, mask, lay.mask_bytes, cudaMemcpyDeviceToDevice, st));
+                WCK(c, launch_expand<T>(lay, mu, tau, leaf, mask2, scratch, st));
+            }
+            std::swap(mask, mask2);
+            std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
+            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+            {
+                PROF(WAM_K_Z0);
+                WST(compute_z0<T>(c, g, lay, leaf, z0, st));                              // a5
+            }
+        }
+    }
+    {
+        PROF(WAM_K_SYNTH);
+        WCK(c, launch_synth(lay, leaf, beta, mu, st));
+    }
+    {
+        PROF(WAM_K_FORWARD);
+        WCK(c, launch_forward(g, mu, leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+                              work_ptr(c, WAM_K_FORWARD), st));
+        WCK(c, launch_sum_final(cpart, np, costs + J, st));
+    }
+
+    const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (mu_out) WCK(c, cudaMemcpyAsync(mu_out, mu, N * sizeof(T), k2, st));
+    if (mask_out && L > 0) WCK(c, cudaMemcpyAsync(mask_out, mask, lay.mask_bytes, k2, st));
+    std::vector<double> h(J + 1);
+    WCK(c, cudaMemcpyAsync(h.data(), costs, (J + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
+    WCK(c, cudaStreamSynchronize(st));
+    if (c->prof) WST(prof_resolve(c));
+    const double band = sizeof(T) == sizeof(float) ? 1e-6 : 1e-11;
+    for (int j = 0; j < J; ++j)
+        if (h[j + 1] > h[j] + band * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
+    return WAM_OK;
+}
+
+template <typename T>
+wam_status project_impl(wam_ctx* c, const T* mu, T* p, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
+    Geom<T> g;
+    WST(make_geom<T>(c, &g));
+    WCK(c, launch_forward<T>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+                             as_stream(stream)));
+    return WAM_OK;
+}
+
+template <typename T>
+wam_status backproject_impl(wam_ctx* c, const T* s, T* out, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!s || !out) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Geom<T> g;
+        WST(make_geom<T>(c, &g));
+        SegTable tab;
+        T* part = nullptr;
+        WST(plan_pixels<T>(c, &tab, &part));
+        cudaStream_t st = as_stream(stream);
+        WCK(c, launch_backproject(g, tab, s, part, nullptr, st));
+        WCK(c, (launch_reduce_pixels<T, T>(tab, part, out, st)));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status leaf_from_masks(wam_ctx* c, const Layout& lay, const unsigned char* masks, uint8_t** leaf,
+                                  cudaStream_t st)
+{
+    *leaf = nullptr;
+    if (lay.L == 0 || !masks) return WAM_OK;
+    WST(ensure_t(c, B_LEAF, (size_t)c->N, leaf));
+    WCK(c, launch_leafmap(lay, masks, *leaf, st));
+    return WAM_OK;
+}
+
+template <typename T>
+wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, const T* mu, T* qhat,
+                               double* cost, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    if (!mu || !qhat || !cost) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    Geom<T> g;
+    WST(make_geom<T>(c, &g));
+    cudaStream_t st = as_stream(stream);
+    uint8_t* leaf = nullptr;
+    WST(leaf_from_masks(c, lay, masks, &leaf, st));
+    const int np = forward_parts(g.V, g.B);
+    double* cpart = nullptr;
+    WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+    WCK(c, launch_forward<T>(g, mu, leaf, static_cast<const float*>(c->buf[B_D].p),
+                             static_cast<const double*>(c->buf[B_DTERM].p),
+                             static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, cpart, nullptr, st));
+    WCK(c, launch_sum_final(cpart, np, cost, st));
+    return WAM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+wam_status wam_create(const wam_geometry* g, wam_ctx** out)
+{
+    if (!out) return WAM_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (check_geometry(g, &why) != WAM_OK) return WAM_ERR_ARG;
+    try {
+        wam_ctx* c = new wam_ctx();
+        c->g = *g;
+        c->N = (long long)g->nx * g->ny;
+        c->M = (long long)g->n_views * g->n_bins;
+        if (cudaGetDevice(&c->device) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return WAM_ERR_CUDA;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
+            c->num_sms = sms;
+        wam_status s = upload_views(c);
+        if (s != WAM_OK) {
+            wam_destroy(c);
+            return s;
+        }
+        *out = c;
+        return WAM_OK;
+    } catch (...) {
+        return WAM_ERR_OOM;
+    }
+}
+
+void wam_destroy(wam_ctx* c)
+{
+    if (!c) return;
+    for (auto& b : c->buf)
+        if (b.p) cudaFree(b.p);
+    for (auto& p : c->pend) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->dwork) cudaFree(c->dwork);
+    delete c;
+}
+
+const char* wam_last_error(const wam_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t wam_mask_bytes(const wam_ctx* c, int levels)
+{
+    if (!c || levels < 0 || levels > WAM_MAX_LEVELS) return 0;
+    size_t s = 0;
+    for (int l = 1; l <= levels; ++l) s += (size_t)(c->g.nx >> l) * (size_t)(c->g.ny >> l);
+    return s;
+}
+
+wam_status wam_set_data(wam_ctx* c, const float* d, const float* I0, int I0_is_scalar, int on_device, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!d || !I0) return fail(c, WAM_ERR_ARG, "d and I0 must not be NULL");
+    try {
+        cudaStream_t st = as_stream(stream);
+        const long long M = c->M;
+        float *dd = nullptr, *ii = nullptr;
+        double* dt = nullptr;
+        WST(ensure_t(c, B_D, (size_t)M, &dd));
+        WST(ensure_t(c, B_I0, (size_t)M, &ii));
+        WST(ensure_t(c, B_DTERM, (size_t)M, &dt));
+        // validate on the host (device data are copied back once)
+        std::vector<float> hd((size_t)M), hi(I0_is_scalar ? 1 : (size_t)M);
+        const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        WCK(c, cudaMemcpyAsync(hd.data(), d, M * sizeof(float), kin, st));
+        WCK(c, cudaMemcpyAsync(hi.data(), I0, hi.size() * sizeof(float), kin, st));
+        WCK(c, cudaStreamSynchronize(st));
+        for (float x : hd)
+            if (!(x >= 0.0f) || !std::isfinite(x)) return fail(c, WAM_ERR_ARG, "d must be finite and >= 0");
+        for (float x : hi)
+            if (!(x > 0.0f) || !std::isfinite(x)) return fail(c, WAM_ERR_ARG, "I0 must be finite and > 0");
+        WCK(c, cudaMemcpyAsync(dd, hd.data(), M * sizeof(float), cudaMemcpyHostToDevice, st));
+        if (I0_is_scalar) {
+            WCK(c, launch_fill_f32(ii, M, hi[0], st));
+        } else {
+            WCK(c, cudaMemcpyAsync(ii, hi.data(), M * sizeof(float), cudaMemcpyHostToDevice, st));
+        }
+        WCK(c, launch_dterm(dd, ii, M, dt, st));
+        WCK(c, cudaStreamSynchronize(st));
+        c->has_data = true;
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
+                           int on_device, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!sc) return fail(c, WAM_ERR_ARG, "schedule is NULL");
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    if (sc->n_iters < 0) return fail(c, WAM_ERR_ARG, "n_iters must be >= 0");
+    if (sc->precision != 32 && sc->precision != 64) return fail(c, WAM_ERR_ARG, "precision must be 32 or 64");
+    if (sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
+        return fail(c, WAM_ERR_ARG, "expand_at/tau missing");
+    for (int k = 0; k < sc->n_expand; ++k) {
+        if (sc->expand_at[k] < 1 || (k > 0 && sc->expand_at[k] <= sc->expand_at[k - 1]))
+            return fail(c, WAM_ERR_ARG, "expand_at must be increasing and >= 1");
+        if (!std::isfinite(sc->tau[k])) return fail(c, WAM_ERR_ARG, "tau must be finite");
+    }
+    try {
+        cudaStream_t st = as_stream(stream);
+        if (sc->precision == 32) return reconstruct_impl<float>(c, sc, mu_out, hist, mask_out, on_device, st);
+        return reconstruct_impl<double>(c, sc, mu_out, hist, mask_out, on_device, st);
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+// ---- steps ------------------------------------------------------------------
+
+wam_status wam_project(wam_ctx* c, const float* mu, float* p, void* s) { return project_impl<float>(c, mu, p, s); }
+wam_status wam_project_f64(wam_ctx* c, const double* mu, double* p, void* s) { return project_impl<double>(c, mu, p, s); }
+
+wam_status wam_backproject(wam_ctx* c, const float* s, float* g, void* st) { return backproject_impl<float>(c, s, g, st); }
+wam_status wam_backproject_f64(wam_ctx* c, const double* s, double* g, void* st)
+{
+    return backproject_impl<double>(c, s, g, st);
+}
+
+wam_status wam_haar(wam_ctx* c, int levels, const double* in, double* out, int inverse, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!in || !out || in == out) return fail(c, WAM_ERR_ARG, "in and out must be distinct non-null arrays");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    double *ta = nullptr, *tb = nullptr;
+    WST(ensure_t(c, B_TMPA, (size_t)c->N, &ta));
+    WST(ensure_t(c, B_TMPB, (size_t)c->N, &tb));
+    WCK(c, launch_haar(lay, in, out, inverse, ta, tb, as_stream(stream)));
+    return WAM_OK;
+}
+
+wam_status wam_synthesize(wam_ctx* c, int levels, const unsigned char* masks, const double* beta, float* mu,
+                          void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!beta || !mu || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    cudaStream_t st = as_stream(stream);
+    uint8_t* leaf = nullptr;
+    WST(leaf_from_masks(c, lay, masks, &leaf, st));
+    WCK(c, launch_synth<float>(lay, leaf, beta, mu, st));
+    return WAM_OK;
+}
+
+wam_status wam_forward(wam_ctx* c, int levels, const unsigned char* masks, const float* mu, float* qhat,
+                       double* cost, void* st)
+{
+    return forward_impl<float>(c, levels, masks, mu, qhat, cost, st);
+}
+
+wam_status wam_forward_f64(wam_ctx* c, int levels, const unsigned char* masks, const double* mu, double* qhat,
+                           double* cost, void* st)
+{
+    return forward_impl<double>(c, levels, masks, mu, qhat, cost, st);
+}
+
+wam_status wam_split_backproject(wam_ctx* c, int levels, const unsigned char* masks, const float* qhat,
+                                 double* bplus, double* bminus, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!qhat || !bplus || !bminus || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        Geom<float> g;
+        WST(make_geom<float>(c, &g));
+        cudaStream_t st = as_stream(stream);
+        SegTable tab;
+        float* part = nullptr;
+        if (levels == 0) {
+            WST(plan_pixels<float>(c, &tab, &part));
+        } else {
+            uint8_t* leaf = nullptr;
+            WST(ensure_t(c, B_LEAF, (size_t)c->N, &leaf));
+            WST(plan_tree<float>(c, lay, masks, leaf, &tab, &part, st));
+        }
+        WCK(c, cudaMemsetAsync(bplus, 0, c->N * sizeof(double), st));
+        WCK(c, cudaMemsetAsync(bminus, 0, c->N * sizeof(double), st));
+        WCK(c, launch_backproject(g, tab, qhat, part, nullptr, st));
+        WCK(c, launch_split_out(tab, lay, part, bplus, bminus, st));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_z0(wam_ctx* c, int levels, const unsigned char* masks, double* z0, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!z0 || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    Geom<float> g;
+    WST(make_geom<float>(c, &g));
+    cudaStream_t st = as_stream(stream);
+    uint8_t* leaf = nullptr;
+    WST(leaf_from_masks(c, lay, masks, &leaf, st));
+    return compute_z0<float>(c, g, lay, leaf, z0, st);
+}
+
+wam_status wam_update(wam_ctx* c, int levels, const unsigned char* masks, const double* b, const double* bplus,
+                      const double* bminus, const double* z0, double clamp, double* beta, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!b || !bplus || !bminus || !z0 || !beta || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    WCK(c, launch_update_dense(lay, masks, b, bplus, bminus, z0, clamp > 0 ? clamp : 30.0, beta, as_stream(stream)));
+    return WAM_OK;
+}
+
+wam_status wam_expand(wam_ctx* c, int levels, const float* S, double tau, const unsigned char* mask_in,
+                      unsigned char* mask_out, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (levels < 1) return fail(c, WAM_ERR_ARG, "levels must be >= 1");
+    if (!S || !mask_in || !mask_out || mask_in == mask_out) return fail(c, WAM_ERR_ARG, "bad pointers");
+    if (!std::isfinite(tau)) return fail(c, WAM_ERR_ARG, "tau must be finite");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    cudaStream_t st = as_stream(stream);
+    uint8_t* leaf = nullptr;
+    double* scratch = nullptr;
+    WST(leaf_from_masks(c, lay, mask_in, &leaf, st));
+    WST(ensure_t(c, B_SCRATCH, 1024, &scratch));
+    WCK(c, cudaMemcpyAsync(mask_out, mask_in, lay.mask_bytes, cudaMemcpyDeviceToDevice, st));
+    WCK(c, launch_expand<float>(lay, S, tau, leaf, mask_out, scratch, st));
+    return WAM_OK;
+}
+
+wam_status wam_profile(wam_ctx* c, int enable)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (enable) {
+        if (!c->dwork) {
+            if (cudaMalloc(&c->dwork, sizeof(unsigned long long) * WAM_NKERNEL) != cudaSuccess) {
+                cudaGetLastError();
+                c->dwork = nullptr;
+                return fail(c, WAM_ERR_OOM, "profiling counters");
+            }
+        }
+        WCK(c, cudaDeviceSynchronize());
+        for (auto& p : c->pend) {
+            c->ev_pool.push_back(p.a);
+            c->ev_pool.push_back(p.b);
+        }
+        c->pend.clear();
+        WCK(c, cudaMemset(c->dwork, 0, sizeof(unsigned long long) * WAM_NKERNEL));
+        std::memset(&c->stats, 0, sizeof(c->stats));
+    }
+    c->prof = enable != 0;
+    return WAM_OK;
+}
+
+wam_status wam_get_stats(wam_ctx* c, wam_stats* out)
+{
+    if (!c || !out) return WAM_ERR_ARG;
+    WST(prof_resolve(c));
+    *out = c->stats;
+    return WAM_OK;
+}
+
+unsigned long long wam_kernel_launches(void) { return wam::kernel_launches(); }
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal device/host declarations of libwam (not part of the C-ABI).
+//
+// Geometry, tree layout and the two exact-intersection primitives shared by
+// the kernels:
+//   * ray traversal over the leaf blocks of the wavelet tree (ray-driven
+//     projector and Z0), and
+//   * closed-form chords of one ray through a block and its four children
+//     (voxel-driven back-projectors).
+// Both evaluate h(y|x) = length of ray y inside voxel x (Sec. II) and its
+// block sums, which by Eq. 1.2 give phi(y|z) = sum_x h(y|x) omega(x|z).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wam {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxSegs = 2 * kMaxLevels + 4;
+constexpr int kBackTPB = 128;     // threads per CTA of the back-projectors
+constexpr int kFwdTPB = 128;      // threads per CTA of the ray-driven kernels
+
+// Scan geometry in the kernel's precision T.  X0, Y0: lower-left image corner.
+template <typename T>
+struct Geom {
+    int kind, nx, ny, V, B;
+    T vx, vy, X0, Y0, ivx, ivy;
+    T pitch, ucen, sod, sdd;
+    const T* cs;                  // device [V][2]: cos, sin of each view angle
+};
+
+// Tree / coefficient layout for L levels (see wam.h).
+struct Layout {
+    int L, nx, ny;
+    int gw[kMaxLevels + 1], gh[kMaxLevels + 1];     // block grid per level
+    long long coff[kMaxLevels + 1];                 // first detail plane of level l
+    long long moff[kMaxLevels + 1];                 // mask offset of level l
+    long long mask_bytes;
+};
+
+// One homogeneous group of back-projection items (blocks of one level and
+// one kind), split into `n_chunks` view ranges of `vpc` views each.
+struct Segment {
+    int level;          // 0: pixel basis (Omega = I); 1..L: Haar level
+    int has_approx;     // accumulates the (unsigned) approximation slot
+    int has_details;    // accumulates h+, h-, v+, v-, d+, d-
+    int n_items;
+    const uint32_t* items;   // packed (by << 16) | bx, or null: implicit row-major
+    int gw;             // block-grid width for implicit items
+    int n_chunks, vpc;
+    int tiles;
+    int cta_begin;      // first CTA of this segment in the back-projection grid
+    int item_begin;     // first thread of this segment in the update grid
+    int n_slots;
+    long long part_off; // first partial of this segment
+};
+
+struct SegTable {
+    int n;
+    int total_ctas;
+    int total_items;
+    Segment s[kMaxSegs];
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <typename T> __device__ __forceinline__ T tiny_dir();
+template <> __device__ __forceinline__ float tiny_dir<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double tiny_dir<double>() { return 1e-200; }
+
+// Finite reciprocal of a direction component: |d| is clamped to a tiny value
+// (sign kept, +0 for a zero) so that plane-crossing parameters stay finite.
+template <typename T>
+__device__ __forceinline__ T safe_rcp(T d)
+{
+    T a = fabs(d);
+    a = a < tiny_dir<T>() ? tiny_dir<T>() : a;
+    T r = T(1) / a;
+    return signbit(d) ? -r : r;
+}
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// ---------------------------------------------------------------------------
+// one ray in parametric form P(t) = P0 + t * dir, |dir| = 1, P0 the point of
+// the ray closest to the origin; [tin, tout] is its part inside the image.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Ray {
+    T px, py, dx, dy, idx, idy, tin, tout;
+};
+
+template <typename T>
+__device__ __forceinline__ bool make_ray(const Geom<T>& g, int v, int b, Ray<T>& r)
+{
+    const T c = g.cs[2 * v], s = g.cs[2 * v + 1];
+    const T ub = (T(b) - g.ucen) * g.pitch;
+    T tlo, thi;
+    if (g.kind == 0) {
+        // line through ub*u, u = (-s, c), direction e = (c, s)
+        r.dx = c; r.dy = s;
+        r.px = -ub * s; r.py = ub * c;
+        tlo = T(-1e30); thi = T(1e30);
+    } else {
+        // source SOD e, detector point -(SDD-SOD) e + ub u
+        const T n2 = g.sdd * g.sdd + ub * ub;
+        const T rn = rsqrt_t<T>(n2);
+        r.dx = (-g.sdd * c - ub * s) * rn;
+        r.dy = (-g.sdd * s + ub * c) * rn;
+        const T k = g.sod * ub / n2;               // P0 = k (ub e + SDD u)
+        r.px = k * (ub * c - g.sdd * s);
+        r.py = k * (ub * s + g.sdd * c);
+        tlo = -g.sod * g.sdd * rn;                 // the source
+        thi = tlo + n2 * rn;                       // the detector
+    }
+    r.idx = safe_rcp(r.dx);
+    r.idy = safe_rcp(r.dy);
+    const T X1 = g.X0 + T(g.nx) * g.vx, Y1 = g.Y0 + T(g.ny) * g.vy;
+    T a0 = (g.X0 - r.px) * r.idx, a1 = (X1 - r.px) * r.idx;
+    T b0 = (g.Y0 - r.py) * r.idy, b1 = (Y1 - r.py) * r.idy;
+    r.tin = fmax(tlo, fmax(fmin(a0, a1), fmin(b0, b1)));
+    r.tout = fmin(thi, fmin(fmax(a0, a1), fmax(b0, b1)));
+    return r.tout > r.tin;
+}
+
+// Visit the leaf blocks crossed by the ray, in order.  leaf[iy*nx+ix] is the
+// level of the leaf holding pixel (ix, iy) (null: every pixel is a leaf).
+// visit(ix, iy, lam, bx0, by0, chord): (ix, iy) the pixel where the ray
+// enters the leaf, (bx0, by0) the leaf's first pixel, chord its length (mm).
+// Every step crosses one grid line in the travel direction, so nx + ny + 4
+// steps bound the walk.
+template <typename T, typename F>
+__device__ __forceinline__ void traverse(const Geom<T>& g, const uint8_t* __restrict__ leaf,
+                                         const Ray<T>& r, F&& visit)
+{
+    T t = r.tin;
+    int ix = clampi((int)floor((r.px + t * r.dx - g.X0) * g.ivx), 0, g.nx - 1);
+    int iy = clampi((int)floor((r.py + t * r.dy - g.Y0) * g.ivy), 0, g.ny - 1);
+    const bool xpos = r.idx > T(0), ypos = r.idy > T(0);
+    const int max_steps = g.nx + g.ny + 4;
+    for (int step = 0; step < max_steps; ++step) {
+        const int lam = leaf ? (int)leaf[iy * g.nx + ix] : 0;
+        const int bs = 1 << lam;
+        const int bx0 = (ix >> lam) << lam, by0 = (iy >> lam) << lam;
+        const int xe = xpos ? bx0 + bs : bx0;
+        const int ye = ypos ? by0 + bs : by0;
+        const T tx = (g.X0 + T(xe) * g.vx - r.px) * r.idx;
+        const T ty = (g.Y0 + T(ye) * g.vy - r.py) * r.idy;
+        T te = fmin(fmin(tx, ty), r.tout);
+        te = fmax(te, t);
+        visit(ix, iy, lam, bx0, by0, te - t);
+        t = te;
+        if (te >= r.tout) break;
+        if (tx <= ty) {
+            ix = xpos ? bx0 + bs : bx0 - 1;
+            iy = clampi((int)floor((r.py + te * r.dy - g.Y0) * g.ivy), by0, by0 + bs - 1);
+        } else {
+            iy = ypos ? by0 + bs : by0 - 1;
+            ix = clampi((int)floor((r.px + te * r.dx - g.X0) * g.ivx), bx0, bx0 + bs - 1);
+        }
+        if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// closed-form chords through an axis-aligned block, in block-local
+// coordinates: (qx, qy) a point of the ray relative to the block centre,
+// (idx, idy) the reciprocal unit direction, (hx, hy) the half sizes.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T block_chord(T qx, T qy, T idx, T idy, T hx, T hy)
+{
+    const T x0 = (-hx - qx) * idx, x1 = (hx - qx) * idx;
+    const T y0 = (-hy - qy) * idy, y1 = (hy - qy) * idy;
+    const T lo = fmax(fmin(x0, x1), fmin(y0, y1));
+    const T hi = fmin(fmax(x0, x1), fmax(y0, y1));
+    return fmax(hi - lo, T(0));
+}
+
+// Chords through the four children: c00 (y lo, x lo), c01 (y lo, x hi),
+// c10 (y hi, x lo), c11 (y hi, x hi).
+template <typename T>
+__device__ __forceinline__ void child_chords(T qx, T qy, T idx, T idy, T hx, T hy,
+                                             T& c00, T& c01, T& c10, T& c11)
+{
+    const T tx0 = (-hx - qx) * idx, tx1 = -qx * idx, tx2 = (hx - qx) * idx;
+    const T ty0 = (-hy - qy) * idy, ty1 = -qy * idy, ty2 = (hy - qy) * idy;
+    const T xl0 = fmin(tx0, tx1), xl1 = fmax(tx0, tx1);   // x-lo slab
+    const T xh0 = fmin(tx1, tx2), xh1 = fmax(tx1, tx2);   // x-hi slab
+    const T yl0 = fmin(ty0, ty1), yl1 = fmax(ty0, ty1);
+    const T yh0 = fmin(ty1, ty2), yh1 = fmax(ty1, ty2);
+    c00 = fmax(fmin(xl1, yl1) - fmax(xl0, yl0), T(0));
+    c01 = fmax(fmin(xh1, yl1) - fmax(xh0, yl0), T(0));
+    c10 = fmax(fmin(xl1, yh1) - fmax(xl0, yh0), T(0));
+    c11 = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
+}
+
+}  // namespace wam

@@ -1,0 +1,47 @@
+// Host-side launchers of the libwam kernels (internal).
+#pragma once
+
+#include "wam_internal.cuh"
+
+namespace wam {
+
+template <typename T>
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d, const double* dterm,
+                           const float* I0, T* qhat, T* p_out, double* cost_part, unsigned long long* work,
+                           cudaStream_t st);
+int forward_parts(int V, int B);
+cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st);
+cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, double* part, cudaStream_t st);
+template <typename T>
+cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, T* part,
+                               unsigned long long* work, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b, const double* z0,
+                          double clamp, double* beta, cudaStream_t st);
+template <typename T>
+cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
+                             cudaStream_t st);
+template <typename T, typename O>
+cudaError_t launch_reduce_pixels(const SegTable& tab, const T* part, O* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_synth(const Layout& lay, const uint8_t* leaf, const double* beta, T* mu, cudaStream_t st);
+cudaError_t launch_leafmap(const Layout& lay, const uint8_t* mask, uint8_t* leaf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_expand(const Layout& lay, const T* S, double tau, const uint8_t* leaf_old, uint8_t* mask_new,
+                          double* scratch, cudaStream_t st);
+cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lists, long long list_stride,
+                           int* counts, cudaStream_t st);
+cudaError_t launch_haar(const Layout& lay, const double* in, double* out, int inverse, double* tmp_a,
+                        double* tmp_b, cudaStream_t st);
+cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, cudaStream_t st);
+cudaError_t launch_fill_f32(float* x, long long n, float v, cudaStream_t st);
+template <typename A, typename B>
+cudaError_t launch_convert(const A* x, B* y, long long n, cudaStream_t st);
+cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const double* b, const double* bp,
+                                const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st);
+
+unsigned long long kernel_launches();
+
+}  // namespace wam
