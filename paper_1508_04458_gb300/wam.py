@@ -86,6 +86,7 @@ _PROTOS = {
     "wam_z0": (_S, [_P, _I, _P, _P, _P]),
     "wam_update": (_S, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "wam_expand": (_S, [_P, _I, _P, _D, _P, _P, _P]),
+    "wam_backproject_static": (_S, [ctypes.POINTER(wam_geometry), _P, _P, _P]),
     "wam_profile": (_S, [_P, _I]),
     "wam_get_stats": (_S, [_P, _P]),
     "wam_kernel_launches": (ctypes.c_ulonglong, []),
