@@ -325,7 +325,7 @@ def run_wam(args, problem, world, rank, local_rank):
     ctx.close()
 
 
-def profile_case():
+def profile_case(full: bool):
     """A small case of the same kernels: 256x256 bag, 360 views x 512 bins."""
     import torch
     from paper_1508_04458_gb300 import inputs as I
@@ -334,7 +334,10 @@ def profile_case():
     ctx = wam.Context(p.geom)
     ctx.set_data(p.d.astype(np.float32), p.I0)
     for _ in range(2):
-        ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32, device_out=True)
+        if full:
+            ctx.reconstruct(0, N_ITERS, precision=32, full_am=True, device_out=True)
+        else:
+            ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32, device_out=True)
     torch.cuda.synchronize()
     ctx.close()
 
@@ -346,12 +349,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run two reconstructions of a 256x256 fan-beam bag (360 views x 512 bins) "
-                         "for kernel profiling, print nothing")
+    ap.add_argument("--profile-case", choices=("multires", "full"), default=None,
+                    help="run two reconstructions (multires or plain AM) of a 256x256 fan-beam bag "
+                         "(360 views x 512 bins) for kernel profiling, print nothing")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case()
+        profile_case(args.profile_case == "full")
         return
 
     world = _env_int("WORLD_SIZE", 1)

@@ -59,7 +59,7 @@ struct OpMax {
 // Beer's law and the I-divergence terms (Sec. II and its footnote).
 // One thread per ray; CTA = (bin tile, view).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool PIX>
 __global__ void __launch_bounds__(kFwdTPB)
 k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
           const float* __restrict__ d, const double* __restrict__ dterm,
@@ -74,10 +74,17 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
         Ray<T> r;
         T acc = T(0);
         if (make_ray(g, v, b, r)) {
-            traverse(g, leaf, r, [&](int ix, int iy, int, int, int, T c) {
-                acc += c * __ldg(mu + iy * g.nx + ix);
-                ++steps;
-            });
+            if (PIX) {
+                traverse_pixels(g, r, [&](int ix, int iy, T c) {
+                    acc += c * __ldg(mu + iy * g.nx + ix);
+                    ++steps;
+                });
+            } else {
+                traverse(g, leaf, r, [&](int ix, int iy, int, int, int, T c) {
+                    acc += c * __ldg(mu + iy * g.nx + ix);
+                    ++steps;
+                });
+            }
         }
         const size_t y = (size_t)v * g.B + b;
         if (p_out) p_out[y] = acc;
@@ -173,104 +180,139 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// a4 (Eq. 1.10) and H^T: voxel-driven split back-projection.  One thread per
-// (block, view range).  For each view the block's shadow on the detector is
-// found from its corners; for each ray in it the chords through the four
-// children give phi for the approximation (all +) and the three details (Haar
-// signs), and qhat*phi is added to the + or - accumulator by the sign of phi.
-// Partials are written per view range and summed later in a fixed order.
+// a4 (Eq. 1.10) and H^T: voxel-driven split back-projection.
+// CTA = 32 consecutive items (blocks of one level, Morton order) x 8 warps;
+// lane i of every warp holds item i, warp w takes views v0 + w, v0 + w + 8,
+// ... of the CTA's view range.  For each view the block's shadow on the
+// detector is found from its corners; for each ray in it the chords through
+// the four children give phi for the approximation (all +) and the three
+// details (Haar signs), and qhat*phi goes to the + or - accumulator by the
+// sign of phi.  The 8 warps' sums are added in a fixed order in shared memory
+// and one partial per (item, view range) is written; partials are summed in a
+// fixed order by the consumer.  dirtab (optional) holds the reciprocal unit
+// direction (1/dx, 1/dy) of every ray.
 // ---------------------------------------------------------------------------
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
 template <typename T>
 __global__ void __launch_bounds__(kBackTPB)
-k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino, T* __restrict__ part,
+k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
+              const typename Vec2<T>::type* __restrict__ dirtab, T* __restrict__ part,
               unsigned long long* __restrict__ work)
 {
+    __shared__ T red[kViewLanes][7][kItemsPerCta];
     const int cta = blockIdx.x;
     int si = 0;
     while (si + 1 < tab.n && cta >= tab.s[si + 1].cta_begin) ++si;
     const Segment& S = tab.s[si];
     const int local = cta - S.cta_begin;
     const int chunk = local / S.tiles, tile = local - chunk * S.tiles;
-    const int item = tile * kBackTPB + threadIdx.x;
-    if (item >= S.n_items) return;
-    int bx, by;
-    if (S.items) {
-        const uint32_t w = S.items[item];
-        bx = (int)(w & 0xffffu);
-        by = (int)(w >> 16);
-    } else {
-        bx = item % S.gw;
-        by = item / S.gw;
-    }
-    const int bsz = 1 << S.level;
-    const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
-    const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
-    const T scale = T(1) / T(bsz);
-    const int v0 = chunk * S.vpc;
-    const int v1 = min(g.V, v0 + S.vpc);
-    const bool fan = g.kind != 0;
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int item = tile * kItemsPerCta + lane;
+    const bool valid = item < S.n_items;
     const bool det = S.has_details != 0;
     T aA = 0, hP = 0, hM = 0, vP = 0, vM = 0, dP = 0, dM = 0;
     unsigned evals = 0;
-    for (int v = v0; v < v1; ++v) {
-        const T c = g.cs[2 * v], s = g.cs[2 * v + 1];
-        const T ac = cx * c + cy * s;        // block centre along e
-        const T wc = -cx * s + cy * c;       // ... along u
-        // shadow of the block: detector coordinates of its corners
-        T umin = T(1e30), umax = T(-1e30);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T x = cx + ((k & 1) ? hx : -hx), y = cy + ((k & 2) ? hy : -hy);
-            const T wu = -x * s + y * c;
-            const T uu = fan ? g.sdd * wu / (g.sod - (x * c + y * s)) : wu;
-            umin = fmin(umin, uu);
-            umax = fmax(umax, uu);
+    if (valid) {
+        int bx, by;
+        if (S.items) {
+            const uint32_t w = S.items[item];
+            bx = (int)(w & 0xffffu);
+            by = (int)(w >> 16);
+        } else {
+            bx = item % S.gw;
+            by = item / S.gw;
         }
-        const int blo = max(0, (int)floor(umin / g.pitch + g.ucen));
-        const int bhi = min(g.B - 1, (int)ceil(umax / g.pitch + g.ucen));
-        const T kappa = fan ? (g.sod - ac) / g.sdd : T(1);
-        const T* row = sino + (size_t)v * g.B;
-        evals += (unsigned)max(0, bhi - blo + 1);
-        for (int bb = blo; bb <= bhi; ++bb) {
-            const T ub = (T(bb) - g.ucen) * g.pitch;
-            const T delta = ub * kappa - wc;         // ray offset from the centre along u
-            const T qx = -delta * s, qy = delta * c;
-            T dx, dy;
-            if (fan) {
-                const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
-                dx = (-g.sdd * c - ub * s) * rn;
-                dy = (-g.sdd * s + ub * c) * rn;
-            } else {
-                dx = c;
-                dy = s;
+        const int bsz = 1 << S.level;
+        const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
+        const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
+        const T scale = T(1) / T(bsz);
+        const int v0 = chunk * S.vpc;
+        const int v1 = min(g.V, v0 + S.vpc);
+        const bool fan = g.kind != 0;
+        const T isdd = T(1) / g.sdd, ipitch = T(1) / g.pitch;
+        const T u0 = -g.ucen * g.pitch;
+        for (int v = v0 + wv; v < v1; v += kViewLanes) {
+            const T c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
+            const T ac = cx * c + cy * s;        // block centre along e
+            const T wc = -cx * s + cy * c;       // ... along u
+            // shadow of the block: detector coordinates of its four corners
+            T umin = T(1e30), umax = T(-1e30);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy;
+                const T wu = wc - ox * s + oy * c;
+                const T uu = fan ? fast_div(g.sdd * wu, g.sod - (ac + ox * c + oy * s)) : wu;
+                umin = fmin(umin, uu);
+                umax = fmax(umax, uu);
             }
-            const T idx = safe_rcp(dx), idy = safe_rcp(dy);
-            const T q = __ldg(row + bb);
-            if (det) {
-                T c00, c01, c10, c11;
-                child_chords(qx, qy, idx, idy, hx, hy, c00, c01, c10, c11);
-                const T qs = q * scale;
-                aA += qs * (c00 + c01 + c10 + c11);
-                const T ph = qs * (c00 + c01 - c10 - c11);
-                const T pv = qs * (c00 - c01 + c10 - c11);
-                const T pd = qs * (c00 - c01 - c10 + c11);
-                if (ph > T(0)) hP += ph; else hM += ph;
-                if (pv > T(0)) vP += pv; else vM += pv;
-                if (pd > T(0)) dP += pd; else dM += pd;
-            } else {
-                aA += q * scale * block_chord(qx, qy, idx, idy, hx, hy);
+            // a margin of 1e-4 bin covers the fast division's rounding
+            const int blo = max(0, (int)floor(umin * ipitch + g.ucen - T(1e-4)));
+            const int bhi = min(g.B - 1, (int)ceil(umax * ipitch + g.ucen + T(1e-4)));
+            const T kappa = fan ? (g.sod - ac) * isdd : T(1);
+            const T* row = sino + (size_t)v * g.B;
+            const typename Vec2<T>::type* drow = dirtab ? dirtab + (size_t)v * g.B : nullptr;
+            evals += (unsigned)max(0, bhi - blo + 1);
+            for (int bb = blo; bb <= bhi; ++bb) {
+                const T ub = T(bb) * g.pitch + u0;
+                const T delta = ub * kappa - wc;     // ray offset from the centre along u
+                const T qx = -delta * s, qy = delta * c;
+                T idx, idy;
+                if (drow) {
+                    const typename Vec2<T>::type dd = __ldg(drow + bb);
+                    idx = dd.x;
+                    idy = dd.y;
+                } else if (fan) {
+                    const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
+                    idx = safe_rcp((-g.sdd * c - ub * s) * rn);
+                    idy = safe_rcp((-g.sdd * s + ub * c) * rn);
+                } else {
+                    idx = safe_rcp(c);
+                    idy = safe_rcp(s);
+                }
+                const T q = __ldg(row + bb);
+                if (det) {
+                    T c00, c01, c10, c11;
+                    child_chords(qx, qy, idx, idy, hx, hy, c00, c01, c10, c11);
+                    const T qs = q * scale;
+                    aA += qs * (c00 + c01 + c10 + c11);
+                    const T ph = qs * (c00 + c01 - c10 - c11);
+                    const T pv = qs * (c00 - c01 + c10 - c11);
+                    const T pd = qs * (c00 - c01 - c10 + c11);
+                    if (ph > T(0)) hP += ph; else hM += ph;
+                    if (pv > T(0)) vP += pv; else vM += pv;
+                    if (pd > T(0)) dP += pd; else dM += pd;
+                } else {
+                    aA += q * scale * block_chord(qx, qy, idx, idy, hx, hy);
+                }
             }
         }
     }
     add_work(work, det ? 4u * evals : evals);
-    T* out = part + S.part_off + (size_t)chunk * S.n_slots * S.n_items + item;
-    const size_t st = (size_t)S.n_items;
-    int k = 0;
-    if (S.has_approx) out[st * k++] = aA;
-    if (det) {
-        out[st * k++] = hP; out[st * k++] = hM;
-        out[st * k++] = vP; out[st * k++] = vM;
-        out[st * k++] = dP; out[st * k++] = dM;
+    // fixed-order sum of the 8 view lanes, one partial per (item, view range)
+    red[wv][0][lane] = aA;
+    red[wv][1][lane] = hP; red[wv][2][lane] = hM;
+    red[wv][3][lane] = vP; red[wv][4][lane] = vM;
+    red[wv][5][lane] = dP; red[wv][6][lane] = dM;
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < 7 * kItemsPerCta) {
+        const int k = t / kItemsPerCta, l = t - k * kItemsPerCta;
+        const int it = tile * kItemsPerCta + l;
+        // slot k of the segment: 0 = approximation when present, then h+ .. d-
+        const int slot = S.has_approx ? k : k - 1;
+        const bool used = (k == 0) ? S.has_approx != 0 : det;
+        if (used && it < S.n_items) {
+            T sum = red[0][k][l];
+#pragma unroll
+            for (int w = 1; w < kViewLanes; ++w) sum += red[w][k][l];
+            part[S.part_off + ((size_t)chunk * S.n_slots + slot) * S.n_items + it] = sum;
+        }
     }
 }
 
@@ -297,13 +339,15 @@ __device__ __forceinline__ void item_block(const Segment& S, int item, int& bx, 
     }
 }
 
+// Sum of one slot of an item over its view ranges, in a fixed order, in the
+// kernel precision T.
 template <typename T>
-__device__ __forceinline__ double sum_slot(const Segment& S, const T* __restrict__ part, int item, int slot)
+__device__ __forceinline__ T sum_slot(const Segment& S, const T* __restrict__ part, int item, int slot)
 {
-    double s = 0.0;
+    T s = T(0);
     const T* p = part + S.part_off + (size_t)slot * S.n_items + item;
     const size_t stride = (size_t)S.n_slots * S.n_items;
-    for (int c = 0; c < S.n_chunks; ++c) s += (double)p[c * stride];
+    for (int c = 0; c < S.n_chunks; ++c) s += p[c * stride];
     return s;
 }
 
@@ -337,6 +381,37 @@ __device__ __forceinline__ double am_delta(double b, double bp, double bm, doubl
     return t / z0;
 }
 
+// The same root in FP32.  Where the counts are near zero (the data weight b
+// is below 1e-3 of the model weight bp - bm, e.g. rays behind metal) the log
+// ratio is taken in FP64 instead.
+__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, double clamp)
+{
+    const float bf = (float)b;
+    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta(b, (double)bp, (double)bm, z0, clamp);
+    float t;
+    if (bp > 0.0f) {
+        const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
+        const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
+        t = (u > 0.0f) ? -logf(u) : (float)clamp;
+    } else if (bm < 0.0f) {
+        t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
+    } else {
+        t = 0.0f;
+    }
+    t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
+    return (double)t / z0;
+}
+
+__device__ __forceinline__ double am_step(double b, float bp, float bm, double z0, double clamp)
+{
+    return am_delta_f32(b, bp, bm, z0, clamp);
+}
+
+__device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, double clamp)
+{
+    return am_delta(b, bp, bm, z0, clamp);
+}
+
 // a6: reduce the partials of each item and apply the AM update to beta.
 template <typename T>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
@@ -352,16 +427,16 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     int slot = 0;
     if (S.has_approx) {
         const long long z = approx_index(lay, S.level, bx, by);
-        beta[z] += am_delta(bvec[z], sum_slot(S, part, item, 0), 0.0, z0, clamp);
+        beta[z] += am_step(bvec[z], sum_slot(S, part, item, 0), T(0), z0, clamp);
         slot = 1;
     }
     if (S.has_details) {
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const long long z = detail_index(lay, S.level, t, bx, by);
-            const double bp = sum_slot(S, part, item, slot + 2 * t);
-            const double bm = sum_slot(S, part, item, slot + 2 * t + 1);
-            beta[z] += am_delta(bvec[z], bp, bm, z0, clamp);
+            const T bp = sum_slot(S, part, item, slot + 2 * t);
+            const T bm = sum_slot(S, part, item, slot + 2 * t + 1);
+            beta[z] += am_step(bvec[z], bp, bm, z0, clamp);
         }
     }
 }
@@ -380,15 +455,15 @@ __global__ void k_split_out(SegTable tab, Layout lay, const T* __restrict__ part
     int slot = 0;
     if (S.has_approx) {
         const long long z = approx_index(lay, S.level, bx, by);
-        bplus[z] = sum_slot(S, part, item, 0);
+        bplus[z] = (double)sum_slot(S, part, item, 0);
         if (bminus) bminus[z] = 0.0;
         slot = 1;
     }
     if (S.has_details) {
         for (int t = 0; t < 3; ++t) {
             const long long z = detail_index(lay, S.level, t, bx, by);
-            bplus[z] = sum_slot(S, part, item, slot + 2 * t);
-            if (bminus) bminus[z] = sum_slot(S, part, item, slot + 2 * t + 1);
+            bplus[z] = (double)sum_slot(S, part, item, slot + 2 * t);
+            if (bminus) bminus[z] = (double)sum_slot(S, part, item, slot + 2 * t + 1);
         }
     }
 }
@@ -621,7 +696,10 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, c
 {
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
     COUNT_LAUNCH();
-    k_forward<T><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
+    if (leaf)
+        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
+    else
+        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
     return cudaGetLastError();
 }
 
@@ -651,12 +729,13 @@ cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, 
 }
 
 template <typename T>
-cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, T* part,
+cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, const void* dirtab, T* part,
                                unsigned long long* work, cudaStream_t st)
 {
     if (tab.total_ctas == 0) return cudaSuccess;
     COUNT_LAUNCH();
-    k_backproject<T><<<tab.total_ctas, kBackTPB, 0, st>>>(g, tab, sino, part, work);
+    k_backproject<T><<<tab.total_ctas, kBackTPB, 0, st>>>(
+        g, tab, sino, static_cast<const typename Vec2<T>::type*>(dirtab), part, work);
     return cudaGetLastError();
 }
 
@@ -813,7 +892,7 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
     template cudaError_t launch_forward<T>(const Geom<T>&, const T*, const uint8_t*, const float*, const double*, \
                                            const float*, T*, T*, double*, unsigned long long*, cudaStream_t);    \
     template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
-    template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, T*,                    \
+    template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \
     template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
                                           double, double*, cudaStream_t);                                        \

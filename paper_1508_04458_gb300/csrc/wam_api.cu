@@ -24,6 +24,7 @@ enum BufId {
     B_CS32, B_CS64, B_D, B_I0, B_DTERM,
     B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
+    B_DIR32, B_DIR64,
     B_NBUF
 };
 
@@ -42,6 +43,7 @@ struct wam_ctx {
     std::vector<ProfPending> pend;
     wam_stats stats{};
     unsigned long long* dwork = nullptr;   // device [WAM_NKERNEL]
+    long long last_leaves = 0;             // leaves of the tree last planned
     cudaStream_t prof_stream = nullptr;
     int device = 0;
     int num_sms = 148;
@@ -250,8 +252,8 @@ struct ListInfo {
     int gw;
 };
 
-// Split every list into view ranges so that the whole grid holds about
-// 1024 threads per SM and each thread a similar number of chord evaluations.
+// Split every list into view ranges so that the grid is about one full wave
+// of 256-thread CTAs (8 per SM) with similar work (chord evaluations) each.
 template <typename T>
 wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTable* tab, T** part_out)
 {
@@ -266,8 +268,9 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         cost[i] = shadow * (lists[i].has_details ? 3.0 : 1.0);
         total += (double)lists[i].n * w.n_views * cost[i];
     }
-    const double target_threads = (double)c->num_sms * 1024.0;
-    const double per_thread = std::max(total / target_threads, 256.0);
+    const double target_ctas = (double)c->num_sms * 8.0;
+    const double per_cta = std::max(total / target_ctas, 1.0);
+    const int max_chunks = std::max(1, w.n_views / kViewLanes);
     int cta = 0, items = 0;
     long long part = 0;
     for (size_t i = 0; i < lists.size(); ++i) {
@@ -281,11 +284,12 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         s.n_items = li.n;
         s.items = li.items;
         s.gw = li.gw;
-        int vpc = (int)std::lround(per_thread / cost[i]);
-        vpc = std::max(1, std::min(vpc, w.n_views));
-        s.n_chunks = (w.n_views + vpc - 1) / vpc;
-        s.vpc = (w.n_views + s.n_chunks - 1) / s.n_chunks;
-        s.tiles = (li.n + kBackTPB - 1) / kBackTPB;
+        const double full = (double)kItemsPerCta * w.n_views * cost[i];
+        int chunks = (int)std::ceil(full / per_cta);
+        chunks = std::max(1, std::min(chunks, max_chunks));
+        s.vpc = (w.n_views + chunks - 1) / chunks;
+        s.n_chunks = (w.n_views + s.vpc - 1) / s.vpc;
+        s.tiles = (li.n + kItemsPerCta - 1) / kItemsPerCta;
         s.cta_begin = cta;
         s.item_begin = items;
         s.n_slots = li.has_approx + 6 * li.has_details;
@@ -297,6 +301,47 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
     tab->total_ctas = cta;
     tab->total_items = items;
     return ensure_t(c, B_PART, (size_t)std::max<long long>(part, 1), part_out);
+}
+
+// Reciprocal unit direction (1/dx, 1/dy) of every ray, computed in FP64 on
+// the host once per context and precision.
+template <typename T>
+wam_status dir_table(wam_ctx* c, const void** out)
+{
+    const BufId id = sizeof(T) == 4 ? B_DIR32 : B_DIR64;
+    const wam_geometry& w = c->g;
+    const size_t n = (size_t)w.n_views * w.n_bins;
+    if (c->buf[id].p && c->buf[id].bytes >= n * 2 * sizeof(T)) {
+        *out = c->buf[id].p;
+        return WAM_OK;
+    }
+    std::vector<T> h(2 * n);
+    const double tiny = sizeof(T) == 4 ? 1e-30 : 1e-200;
+    auto rcp = [tiny](double d) {
+        double a = std::fabs(d);
+        a = a < tiny ? tiny : a;
+        return std::signbit(d) ? -1.0 / a : 1.0 / a;
+    };
+    for (int k = 0; k < w.n_views; ++k) {
+        const double th = w.angle0 + k * (w.angle_span / w.n_views);
+        const double cs = std::cos(th), sn = std::sin(th);
+        for (int b = 0; b < w.n_bins; ++b) {
+            double dx = cs, dy = sn;
+            if (w.kind == WAM_FAN2D_FLAT) {
+                const double ub = (b - 0.5 * (w.n_bins - 1)) * w.bin_pitch;
+                const double rn = 1.0 / std::sqrt(w.sdd * w.sdd + ub * ub);
+                dx = (-w.sdd * cs - ub * sn) * rn;
+                dy = (-w.sdd * sn + ub * cs) * rn;
+            }
+            h[2 * ((size_t)k * w.n_bins + b)] = (T)rcp(dx);
+            h[2 * ((size_t)k * w.n_bins + b) + 1] = (T)rcp(dy);
+        }
+    }
+    T* d = nullptr;
+    WST(ensure_t(c, id, 2 * n, &d));
+    WCK(c, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *out = d;
+    return WAM_OK;
 }
 
 template <typename T>
@@ -324,6 +369,10 @@ wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t
     std::vector<int> h(L + 1);
     WCK(c, cudaMemcpyAsync(h.data(), counts, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
     WCK(c, cudaStreamSynchronize(st));
+    // leaves: each expanded block turns one leaf into four
+    long long leaves = (long long)lay.gw[L] * lay.gh[L];
+    for (int k = 1; k <= L; ++k) leaves += 3LL * h[k];
+    c->last_leaves = leaves;
     std::vector<ListInfo> li;
     li.push_back({L, 1, 0, h[0], lists, lay.gw[L]});
     li.push_back({L, 1, 1, h[1], lists + stride, lay.gw[L]});
@@ -408,6 +457,9 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     const float* I0 = static_cast<const float*>(c->buf[B_I0].p);
     const double* dterm = static_cast<const double*>(c->buf[B_DTERM].p);
 
+    const void* dirt = nullptr;
+    WST(dir_table<T>(c, &dirt));
+
     // a0, Eq. 1.6: b = Phi^T d = Omega^T (H^T d) for every coefficient
     SegTable pix;
     T* part = nullptr;
@@ -422,7 +474,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     }
     {
         PROF(WAM_K_BACKPROJECT);
-        WCK(c, launch_backproject(g, pix, dT, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+        WCK(c, launch_backproject(g, pix, dT, dirt, part, work_ptr(c, WAM_K_BACKPROJECT), st));
     }
     {
         PROF(WAM_K_TREE);
@@ -444,6 +496,14 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
         WST(compute_z0<T>(c, g, lay, leaf, z0, st));
     }
 
+    // The leaf walk pays per leaf what the pixel walk pays per pixel, about
+    // 2.5 times over; once leaves average fewer than 4 pixels the image mu
+    // (constant on leaves) is projected pixel by pixel instead.
+    auto pick_leaf = [&]() -> const uint8_t* {
+        return (L > 0 && 4 * c->last_leaves < N) ? leaf : nullptr;
+    };
+    const uint8_t* fwd_leaf = pick_leaf();
+
     std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
                             sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
     size_t next_exp = 0;
@@ -454,13 +514,13 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
         }
         {
             PROF(WAM_K_FORWARD);                                                            // a2, a3
-            WCK(c, launch_forward(g, mu, leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
             WCK(c, launch_sum_final(cpart, np, costs + j, st));
         }
         {
             PROF(WAM_K_BACKPROJECT);                                                        // a4
-            WCK(c, launch_backproject(g, tab, q, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+            WCK(c, launch_backproject(g, tab, q, dirt, part, work_ptr(c, WAM_K_BACKPROJECT), st));
         }
         {
             PROF(WAM_K_UPDATE);                                                             // a6
@@ -478,6 +538,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
             std::swap(mask, mask2);
             std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
             WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+            fwd_leaf = pick_leaf();
             {
                 PROF(WAM_K_Z0);
                 WST(compute_z0<T>(c, g, lay, leaf, z0, st));                              // a5
@@ -490,7 +551,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     }
     {
         PROF(WAM_K_FORWARD);
-        WCK(c, launch_forward(g, mu, leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+        WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
                               work_ptr(c, WAM_K_FORWARD), st));
         WCK(c, launch_sum_final(cpart, np, costs + J, st));
     }
@@ -533,7 +594,9 @@ wam_status backproject_impl(wam_ctx* c, const T* s, T* out, void* stream)
         T* part = nullptr;
         WST(plan_pixels<T>(c, &tab, &part));
         cudaStream_t st = as_stream(stream);
-        WCK(c, launch_backproject(g, tab, s, part, nullptr, st));
+        const void* dirt = nullptr;
+        WST(dir_table<T>(c, &dirt));
+        WCK(c, launch_backproject(g, tab, s, dirt, part, nullptr, st));
         WCK(c, (launch_reduce_pixels<T, T>(tab, part, out, st)));
         return WAM_OK;
     } catch (...) {
@@ -770,7 +833,9 @@ wam_status wam_split_backproject(wam_ctx* c, int levels, const unsigned char* ma
         }
         WCK(c, cudaMemsetAsync(bplus, 0, c->N * sizeof(double), st));
         WCK(c, cudaMemsetAsync(bminus, 0, c->N * sizeof(double), st));
-        WCK(c, launch_backproject(g, tab, qhat, part, nullptr, st));
+        const void* dirt = nullptr;
+        WST(dir_table<float>(c, &dirt));
+        WCK(c, launch_backproject(g, tab, qhat, dirt, part, nullptr, st));
         WCK(c, launch_split_out(tab, lay, part, bplus, bminus, st));
         return WAM_OK;
     } catch (...) {

@@ -17,7 +17,9 @@ namespace wam {
 
 constexpr int kMaxLevels = 8;
 constexpr int kMaxSegs = 2 * kMaxLevels + 4;
-constexpr int kBackTPB = 128;     // threads per CTA of the back-projectors
+constexpr int kItemsPerCta = 32;  // back-projector: items (blocks) per CTA, one per lane
+constexpr int kViewLanes = 8;     // back-projector: warps per CTA, each on its own views
+constexpr int kBackTPB = kItemsPerCta * kViewLanes;
 constexpr int kFwdTPB = 128;      // threads per CTA of the ray-driven kernels
 
 // Scan geometry in the kernel's precision T.  X0, Y0: lower-left image corner.
@@ -163,6 +165,43 @@ __device__ __forceinline__ void traverse(const Geom<T>& g, const uint8_t* __rest
         } else {
             iy = ypos ? by0 + bs : by0 - 1;
             ix = clampi((int)floor((r.px + te * r.dx - g.X0) * g.ivx), bx0, bx0 + bs - 1);
+        }
+        if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny) break;
+    }
+}
+
+// Incremental Siddon walk over single pixels (every pixel a leaf).  The next
+// crossing of each axis is recomputed from the first one and an integer count
+// (t = t_first + k * t_per_pixel), so rounding does not accumulate along the
+// ray.  visit(ix, iy, chord).
+template <typename T, typename F>
+__device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& r, F&& visit)
+{
+    T t = r.tin;
+    int ix = clampi((int)floor((r.px + t * r.dx - g.X0) * g.ivx), 0, g.nx - 1);
+    int iy = clampi((int)floor((r.py + t * r.dy - g.Y0) * g.ivy), 0, g.ny - 1);
+    const bool xpos = r.idx > T(0), ypos = r.idy > T(0);
+    const int sx = xpos ? 1 : -1, sy = ypos ? 1 : -1;
+    const T ax = fabs(r.idx) * g.vx, ay = fabs(r.idy) * g.vy;
+    const T tx0 = (g.X0 + T(ix + (xpos ? 1 : 0)) * g.vx - r.px) * r.idx;
+    const T ty0 = (g.Y0 + T(iy + (ypos ? 1 : 0)) * g.vy - r.py) * r.idy;
+    T tx = tx0, ty = ty0;
+    int kx = 0, ky = 0;
+    const int max_steps = g.nx + g.ny + 4;
+    for (int step = 0; step < max_steps; ++step) {
+        T te = fmin(fmin(tx, ty), r.tout);
+        te = fmax(te, t);
+        visit(ix, iy, te - t);
+        t = te;
+        if (te >= r.tout) break;
+        if (tx <= ty) {
+            ix += sx;
+            ++kx;
+            tx = tx0 + T(kx) * ax;
+        } else {
+            iy += sy;
+            ++ky;
+            ty = ty0 + T(ky) * ay;
         }
         if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny) break;
     }

@@ -15,7 +15,7 @@ cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_
 template <typename T>
 cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, double* part, cudaStream_t st);
 template <typename T>
-cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, T* part,
+cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, const void* dirtab, T* part,
                                unsigned long long* work, cudaStream_t st);
 template <typename T>
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b, const double* z0,

@@ -81,7 +81,7 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
     sg.gw = w->nx;
     sg.n_chunks = (V + vpc - 1) / vpc;
     sg.vpc = (V + sg.n_chunks - 1) / sg.n_chunks;
-    sg.tiles = (int)((N + kBackTPB - 1) / kBackTPB);
+    sg.tiles = (int)((N + kItemsPerCta - 1) / kItemsPerCta);
     sg.cta_begin = 0;
     sg.item_begin = 0;
     sg.n_slots = 1;
@@ -132,7 +132,7 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
     g.cs = cs;
     // every partial of every (pixel, view range) is written before it is read:
     // nothing in the scratch needs clearing
-    if (launch_backproject<float>(g, tab, s, part, nullptr, cst) != cudaSuccess) return WAM_ERR_CUDA;
+    if (launch_backproject<float>(g, tab, s, nullptr, part, nullptr, cst) != cudaSuccess) return WAM_ERR_CUDA;
     if (launch_reduce_pixels<float, float>(tab, part, out, cst) != cudaSuccess) return WAM_ERR_CUDA;
     return WAM_OK;
 }
