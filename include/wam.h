@@ -96,8 +96,9 @@ typedef struct wam_ctx wam_ctx;
 
 /* Create a context for one geometry on the current CUDA device.  The context
  * owns its device buffers (allocated here and on first use by a schedule).
- * Errors: WAM_ERR_ARG for a bad geometry (non-positive sizes, fan beam with
- * SOD <= image circumradius or SDD <= SOD), WAM_ERR_OOM, WAM_ERR_CUDA. */
+ * Errors: WAM_ERR_ARG for a bad geometry (non-positive sizes; fan beam with
+ * the source or the detector line within the image's circumradius of the
+ * origin, i.e. SOD <= r or SDD - SOD <= r), WAM_ERR_OOM, WAM_ERR_CUDA. */
 wam_status wam_create(const wam_geometry* g, wam_ctx** out);
 
 /* Free every device buffer and the context.  NULL is ignored. */

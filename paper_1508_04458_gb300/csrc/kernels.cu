@@ -97,8 +97,10 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
     }
     add_work(work, steps);
     if (cost_part) {
-        term = block_reduce(term, OpSum(), 0.0);
-        if (threadIdx.x == 0) cost_part[blockIdx.y * gridDim.x + blockIdx.x] = term;
+        // one partial per warp: no CTA barrier behind the longest ray
+        term = warp_reduce(term, OpSum());
+        if ((threadIdx.x & 31) == 0)
+            cost_part[(blockIdx.y * gridDim.x + blockIdx.x) * (kFwdTPB / 32) + (threadIdx.x >> 5)] = term;
     }
 }
 
@@ -175,8 +177,9 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
             rowsum = (double)rs + (double)total / (double)(1 << L);
         }
     }
-    rowsum = block_reduce(rowsum, OpMax(), 0.0);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = rowsum;
+    rowsum = warp_reduce(rowsum, OpMax());
+    if ((threadIdx.x & 31) == 0)
+        part[(blockIdx.y * gridDim.x + blockIdx.x) * (kFwdTPB / 32) + (threadIdx.x >> 5)] = rowsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -192,17 +195,43 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
 // fixed order by the consumer.  dirtab (optional) holds the reciprocal unit
 // direction (1/dx, 1/dy) of every ray.
 // ---------------------------------------------------------------------------
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+__device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ double4 ld4(const double4* p)
+{
+    const double2 lo = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 hi = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return make_double4(lo.x, lo.y, hi.x, hi.y);
+}
 
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
+// x with the sign flipped where `sgn` is negative (one logic op in FP32).
+__device__ __forceinline__ float flip(float x, float sgn)
+{
+    return __int_as_float(__float_as_int(x) ^ (__float_as_int(sgn) & 0x80000000));
+}
+__device__ __forceinline__ double flip(double x, double sgn) { return signbit(sgn) ? -x : x; }
+__device__ __forceinline__ float flip2(float x, float s1, float s2)
+{
+    return __int_as_float(__float_as_int(x) ^ ((__float_as_int(s1) ^ __float_as_int(s2)) & 0x80000000));
+}
+__device__ __forceinline__ double flip2(double x, double s1, double s2)
+{
+    return (signbit(s1) != signbit(s2)) ? -x : x;
+}
+
+// dirtab[v][b] = (s/dx, -c/dy, 1/dx, 1/dy) of ray (v, b), c, s = cos, sin of
+// the view: with delta the ray's offset from a block centre along u, the
+// centre-line crossings are a = delta s/dx and b = -delta c/dy.
 template <typename T>
 __global__ void __launch_bounds__(kBackTPB)
 k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
-              const typename Vec2<T>::type* __restrict__ dirtab, T* __restrict__ part,
+              const typename Vec4<T>::type* __restrict__ dirtab, T* __restrict__ part,
               unsigned long long* __restrict__ work)
 {
     __shared__ T red[kViewLanes][7][kItemsPerCta];
@@ -216,6 +245,10 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
     const int item = tile * kItemsPerCta + lane;
     const bool valid = item < S.n_items;
     const bool det = S.has_details != 0;
+    const bool quad = S.quad != 0;
+    const bool four = det || quad;       // chords through the four children
+    // accumulators: Haar split (A, h+, h-, v+, v-, d+, d-); a pixel quad keeps
+    // the Hadamard sums (A, h, v, d) of its four pixels in (A, h+, v+, d+)
     T aA = 0, hP = 0, hM = 0, vP = 0, vM = 0, dP = 0, dM = 0;
     unsigned evals = 0;
     if (valid) {
@@ -231,7 +264,7 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
         const int bsz = 1 << S.level;
         const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
         const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
-        const T scale = T(1) / T(bsz);
+        const T scale = quad ? T(1) : T(1) / T(bsz);
         const int v0 = chunk * S.vpc;
         const int v1 = min(g.V, v0 + S.vpc);
         const bool fan = g.kind != 0;
@@ -256,44 +289,58 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
             const int bhi = min(g.B - 1, (int)ceil(umax * ipitch + g.ucen + T(1e-4)));
             const T kappa = fan ? (g.sod - ac) * isdd : T(1);
             const T* row = sino + (size_t)v * g.B;
-            const typename Vec2<T>::type* drow = dirtab ? dirtab + (size_t)v * g.B : nullptr;
+            const typename Vec4<T>::type* drow = dirtab ? dirtab + (size_t)v * g.B : nullptr;
             evals += (unsigned)max(0, bhi - blo + 1);
-            for (int bb = blo; bb <= bhi; ++bb) {
-                const T ub = T(bb) * g.pitch + u0;
+            T fb = T(blo);
+            for (int bb = blo; bb <= bhi; ++bb, fb += T(1)) {
+                const T ub = fb * g.pitch + u0;
                 const T delta = ub * kappa - wc;     // ray offset from the centre along u
-                const T qx = -delta * s, qy = delta * c;
-                T idx, idy;
+                typename Vec4<T>::type dd;
                 if (drow) {
-                    const typename Vec2<T>::type dd = __ldg(drow + bb);
-                    idx = dd.x;
-                    idy = dd.y;
-                } else if (fan) {
-                    const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
-                    idx = safe_rcp((-g.sdd * c - ub * s) * rn);
-                    idy = safe_rcp((-g.sdd * s + ub * c) * rn);
+                    dd = ld4(drow + bb);
                 } else {
-                    idx = safe_rcp(c);
-                    idy = safe_rcp(s);
+                    // no table: the same four numbers from the ray's direction
+                    T dx = c, dy = s;
+                    if (fan) {
+                        const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
+                        dx = (-g.sdd * c - ub * s) * rn;
+                        dy = (-g.sdd * s + ub * c) * rn;
+                    }
+                    dd.z = safe_rcp(dx);
+                    dd.w = safe_rcp(dy);
+                    dd.x = s * dd.z;
+                    dd.y = -c * dd.w;
                 }
+                const T a = delta * dd.x, b = delta * dd.y;
+                const T Ax = hx * fabs(dd.z), Ay = hy * fabs(dd.w);
                 const T q = __ldg(row + bb);
-                if (det) {
-                    T c00, c01, c10, c11;
-                    child_chords(qx, qy, idx, idy, hx, hy, c00, c01, c10, c11);
+                if (four) {
+                    T cFF, cFS, cSF, cSS;
+                    child_chords_ab(a, b, Ax, Ay, cFF, cFS, cSF, cSS);
                     const T qs = q * scale;
-                    aA += qs * (c00 + c01 + c10 + c11);
-                    const T ph = qs * (c00 + c01 - c10 - c11);
-                    const T pv = qs * (c00 - c01 + c10 - c11);
-                    const T pd = qs * (c00 - c01 - c10 + c11);
-                    if (ph > T(0)) hP += ph; else hM += ph;
-                    if (pv > T(0)) vP += pv; else vM += pv;
-                    if (pd > T(0)) dP += pd; else dM += pd;
+                    const T xF = cFF + cFS, xS = cSF + cSS;      // first / second x half
+                    const T yF = cFF + cSF, yS = cFS + cSS;
+                    aA += qs * (xF + xS);
+                    // lower half minus upper half, by the travel direction's signs
+                    const T ph = qs * flip(yF - yS, dd.w);
+                    const T pv = qs * flip(xF - xS, dd.z);
+                    const T pd = qs * flip2((cFF + cSS) - (cFS + cSF), dd.z, dd.w);
+                    if (quad) {
+                        hP += ph;
+                        vP += pv;
+                        dP += pd;
+                    } else {
+                        if (ph > T(0)) hP += ph; else hM += ph;
+                        if (pv > T(0)) vP += pv; else vM += pv;
+                        if (pd > T(0)) dP += pd; else dM += pd;
+                    }
                 } else {
-                    aA += q * scale * block_chord(qx, qy, idx, idy, hx, hy);
+                    aA += q * scale * block_chord_ab(a, b, Ax, Ay);
                 }
             }
         }
     }
-    add_work(work, det ? 4u * evals : evals);
+    add_work(work, four ? 4u * evals : evals);
     // fixed-order sum of the 8 view lanes, one partial per (item, view range)
     red[wv][0][lane] = aA;
     red[wv][1][lane] = hP; red[wv][2][lane] = hM;
@@ -304,14 +351,35 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
     if (t < 7 * kItemsPerCta) {
         const int k = t / kItemsPerCta, l = t - k * kItemsPerCta;
         const int it = tile * kItemsPerCta + l;
-        // slot k of the segment: 0 = approximation when present, then h+ .. d-
-        const int slot = S.has_approx ? k : k - 1;
-        const bool used = (k == 0) ? S.has_approx != 0 : det;
-        if (used && it < S.n_items) {
-            T sum = red[0][k][l];
+        if (it < S.n_items) {
+            if (quad) {
+                // inverse Hadamard of (A, h, v, d): pixel k = (ylo,xlo), (ylo,xhi),
+                // (yhi,xlo), (yhi,xhi); summed over the 8 lanes first
+                if (k < 4) {
+                    T A = 0, h = 0, vv = 0, d = 0;
 #pragma unroll
-            for (int w = 1; w < kViewLanes; ++w) sum += red[w][k][l];
-            part[S.part_off + ((size_t)chunk * S.n_slots + slot) * S.n_items + it] = sum;
+                    for (int w = 0; w < kViewLanes; ++w) {
+                        A += red[w][0][l];
+                        h += red[w][1][l];
+                        vv += red[w][3][l];
+                        d += red[w][5][l];
+                    }
+                    const T sh = (k & 2) ? -h : h, sv = (k & 1) ? -vv : vv;
+                    const T sd = ((k == 1) || (k == 2)) ? -d : d;
+                    part[S.part_off + ((size_t)chunk * S.n_slots + k) * S.n_items + it] =
+                        T(0.25) * (A + sh + sv + sd);
+                }
+            } else {
+                // slot k of the segment: 0 = approximation when present, then h+ .. d-
+                const int slot = S.has_approx ? k : k - 1;
+                const bool used = (k == 0) ? S.has_approx != 0 : det;
+                if (used) {
+                    T sumk = red[0][k][l];
+#pragma unroll
+                    for (int w = 1; w < kViewLanes; ++w) sumk += red[w][k][l];
+                    part[S.part_off + ((size_t)chunk * S.n_slots + slot) * S.n_items + it] = sumk;
+                }
+            }
         }
     }
 }
@@ -424,6 +492,14 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     int bx, by;
     item_block(S, item, bx, by);
     const double z0 = *z0p;
+    if (S.quad) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
+            beta[z] += am_step(bvec[z], sum_slot(S, part, item, k), T(0), z0, clamp);
+        }
+        return;
+    }
     int slot = 0;
     if (S.has_approx) {
         const long long z = approx_index(lay, S.level, bx, by);
@@ -452,6 +528,14 @@ __global__ void k_split_out(SegTable tab, Layout lay, const T* __restrict__ part
     const int item = gid - S.item_begin;
     int bx, by;
     item_block(S, item, bx, by);
+    if (S.quad) {
+        for (int k = 0; k < 4; ++k) {
+            const long long z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
+            bplus[z] = (double)sum_slot(S, part, item, k);
+            if (bminus) bminus[z] = 0.0;
+        }
+        return;
+    }
     int slot = 0;
     if (S.has_approx) {
         const long long z = approx_index(lay, S.level, bx, by);
@@ -470,12 +554,19 @@ __global__ void k_split_out(SegTable tab, Layout lay, const T* __restrict__ part
 
 // Pixel-basis back-projection result (level-0 segment) into an image.
 template <typename T, typename O>
-__global__ void k_reduce_pixels(SegTable tab, const T* __restrict__ part, O* __restrict__ out)
+__global__ void k_reduce_pixels(SegTable tab, int nx, long long npix, const T* __restrict__ part,
+                                O* __restrict__ out)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= tab.total_items) return;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
     const Segment& S = tab.s[0];
-    out[gid] = (O)sum_slot(S, part, gid, 0);
+    if (S.quad) {
+        const int ix = (int)(p % nx), iy = (int)(p / nx);
+        const int item = (iy >> 1) * S.gw + (ix >> 1);
+        out[p] = (O)sum_slot(S, part, item, ((iy & 1) << 1) | (ix & 1));
+    } else {
+        out[p] = (O)sum_slot(S, part, (int)p, 0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -703,19 +794,19 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, c
     return cudaGetLastError();
 }
 
-int forward_parts(int V, int B) { return (int)nblk(B, kFwdTPB) * V; }
+int forward_parts(int V, int B) { return (int)nblk(B, kFwdTPB) * V * (kFwdTPB / 32); }
 
 cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st)
 {
     COUNT_LAUNCH();
-    k_sum_final<<<1, 256, 0, st>>>(part, n, out);
+    k_sum_final<<<1, 1024, 0, st>>>(part, n, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st)
 {
     COUNT_LAUNCH();
-    k_max_final<<<1, 256, 0, st>>>(part, n, out);
+    k_max_final<<<1, 1024, 0, st>>>(part, n, out);
     return cudaGetLastError();
 }
 
@@ -735,7 +826,7 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
     if (tab.total_ctas == 0) return cudaSuccess;
     COUNT_LAUNCH();
     k_backproject<T><<<tab.total_ctas, kBackTPB, 0, st>>>(
-        g, tab, sino, static_cast<const typename Vec2<T>::type*>(dirtab), part, work);
+        g, tab, sino, static_cast<const typename Vec4<T>::type*>(dirtab), part, work);
     return cudaGetLastError();
 }
 
@@ -760,10 +851,11 @@ cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* pa
 }
 
 template <typename T, typename O>
-cudaError_t launch_reduce_pixels(const SegTable& tab, const T* part, O* out, cudaStream_t st)
+cudaError_t launch_reduce_pixels(const SegTable& tab, int nx, long long npix, const T* part, O* out,
+                                 cudaStream_t st)
 {
     COUNT_LAUNCH();
-    k_reduce_pixels<T, O><<<nblk(tab.total_items, 256), 256, 0, st>>>(tab, part, out);
+    k_reduce_pixels<T, O><<<nblk(npix, 256), 256, 0, st>>>(tab, nx, npix, part, out);
     return cudaGetLastError();
 }
 
@@ -904,9 +996,12 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
 WAM_INST(float)
 WAM_INST(double)
 #undef WAM_INST
-template cudaError_t launch_reduce_pixels<float, float>(const SegTable&, const float*, float*, cudaStream_t);
-template cudaError_t launch_reduce_pixels<float, double>(const SegTable&, const float*, double*, cudaStream_t);
-template cudaError_t launch_reduce_pixels<double, double>(const SegTable&, const double*, double*, cudaStream_t);
+template cudaError_t launch_reduce_pixels<float, float>(const SegTable&, int, long long, const float*, float*,
+                                                       cudaStream_t);
+template cudaError_t launch_reduce_pixels<float, double>(const SegTable&, int, long long, const float*, double*,
+                                                        cudaStream_t);
+template cudaError_t launch_reduce_pixels<double, double>(const SegTable&, int, long long, const double*, double*,
+                                                         cudaStream_t);
 template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
 

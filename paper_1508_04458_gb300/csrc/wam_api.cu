@@ -250,6 +250,7 @@ struct ListInfo {
     int level, has_approx, has_details, n;
     const uint32_t* items;
     int gw;
+    int quad = 0;
 };
 
 // Split every list into view ranges so that the grid is about one full wave
@@ -265,7 +266,7 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
     double total = 0.0;
     for (size_t i = 0; i < lists.size(); ++i) {
         const double shadow = (double)(1 << lists[i].level) * diag * mag / w.bin_pitch + 1.0;
-        cost[i] = shadow * (lists[i].has_details ? 3.0 : 1.0);
+        cost[i] = shadow * ((lists[i].has_details || lists[i].quad) ? 3.0 : 1.0);
         total += (double)lists[i].n * w.n_views * cost[i];
     }
     const double target_ctas = (double)c->num_sms * 8.0;
@@ -281,6 +282,7 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         s.level = li.level;
         s.has_approx = li.has_approx;
         s.has_details = li.has_details;
+        s.quad = li.quad;
         s.n_items = li.n;
         s.items = li.items;
         s.gw = li.gw;
@@ -292,7 +294,7 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         s.tiles = (li.n + kItemsPerCta - 1) / kItemsPerCta;
         s.cta_begin = cta;
         s.item_begin = items;
-        s.n_slots = li.has_approx + 6 * li.has_details;
+        s.n_slots = li.quad ? 4 : li.has_approx + 6 * li.has_details;
         s.part_off = part;
         cta += s.tiles * s.n_chunks;
         items += li.n;
@@ -303,19 +305,20 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
     return ensure_t(c, B_PART, (size_t)std::max<long long>(part, 1), part_out);
 }
 
-// Reciprocal unit direction (1/dx, 1/dy) of every ray, computed in FP64 on
-// the host once per context and precision.
+// Per ray (s/dx, -c/dy, 1/dx, 1/dy): the reciprocal unit direction and its
+// products with the view's sin and -cos, computed in FP64 on the host once
+// per context and precision.
 template <typename T>
 wam_status dir_table(wam_ctx* c, const void** out)
 {
     const BufId id = sizeof(T) == 4 ? B_DIR32 : B_DIR64;
     const wam_geometry& w = c->g;
     const size_t n = (size_t)w.n_views * w.n_bins;
-    if (c->buf[id].p && c->buf[id].bytes >= n * 2 * sizeof(T)) {
+    if (c->buf[id].p && c->buf[id].bytes >= n * 4 * sizeof(T)) {
         *out = c->buf[id].p;
         return WAM_OK;
     }
-    std::vector<T> h(2 * n);
+    std::vector<T> h(4 * n);
     const double tiny = sizeof(T) == 4 ? 1e-30 : 1e-200;
     auto rcp = [tiny](double d) {
         double a = std::fabs(d);
@@ -333,21 +336,35 @@ wam_status dir_table(wam_ctx* c, const void** out)
                 dx = (-w.sdd * cs - ub * sn) * rn;
                 dy = (-w.sdd * sn + ub * cs) * rn;
             }
-            h[2 * ((size_t)k * w.n_bins + b)] = (T)rcp(dx);
-            h[2 * ((size_t)k * w.n_bins + b) + 1] = (T)rcp(dy);
+            const double ix = rcp(dx), iy = rcp(dy);
+            T* e = &h[4 * ((size_t)k * w.n_bins + b)];
+            e[0] = (T)(sn * ix);
+            e[1] = (T)(-cs * iy);
+            e[2] = (T)ix;
+            e[3] = (T)iy;
         }
     }
     T* d = nullptr;
-    WST(ensure_t(c, id, 2 * n, &d));
+    WST(ensure_t(c, id, 4 * n, &d));
     WCK(c, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     *out = d;
     return WAM_OK;
 }
 
+// Pixel basis (Omega = I): items are 2x2 pixel quads when both sides are
+// even (one shadow per quad, four chords per ray), else single pixels.
 template <typename T>
 wam_status plan_pixels(wam_ctx* c, SegTable* tab, T** part)
 {
-    std::vector<ListInfo> lists = {{0, 1, 0, (int)c->N, nullptr, c->g.nx}};
+    const int nx = c->g.nx, ny = c->g.ny;
+    std::vector<ListInfo> lists;
+    if (nx % 2 == 0 && ny % 2 == 0) {
+        ListInfo li{1, 0, 0, (nx / 2) * (ny / 2), nullptr, nx / 2};
+        li.quad = 1;
+        lists.push_back(li);
+    } else {
+        lists.push_back({0, 1, 0, (int)c->N, nullptr, nx});
+    }
     return plan_segments<T>(c, lists, tab, part);
 }
 
@@ -407,7 +424,7 @@ wam_status check_geometry(const wam_geometry* g, std::string* why)
     if (g->kind == WAM_FAN2D_FLAT) {
         const double r = 0.5 * std::hypot(g->nx * g->vx, g->ny * g->vy);
         if (!(g->sod > r)) { *why = "fan beam: SOD must exceed the image circumradius"; return WAM_ERR_ARG; }
-        if (!(g->sdd > g->sod)) { *why = "fan beam: SDD must exceed SOD"; return WAM_ERR_ARG; }
+        if (!(g->sdd - g->sod > r)) { *why = "fan beam: the detector must lie outside the image"; return WAM_ERR_ARG; }
     }
     return WAM_OK;
 }
@@ -478,7 +495,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     }
     {
         PROF(WAM_K_TREE);
-        WCK(c, (launch_reduce_pixels<T, double>(pix, part, gimg, st)));
+        WCK(c, (launch_reduce_pixels<T, double>(pix, c->g.nx, N, part, gimg, st)));
         WCK(c, launch_haar(lay, gimg, bvec, 0, tmpa, tmpb, st));
     }
 
@@ -597,7 +614,7 @@ wam_status backproject_impl(wam_ctx* c, const T* s, T* out, void* stream)
         const void* dirt = nullptr;
         WST(dir_table<T>(c, &dirt));
         WCK(c, launch_backproject(g, tab, s, dirt, part, nullptr, st));
-        WCK(c, (launch_reduce_pixels<T, T>(tab, part, out, st)));
+        WCK(c, (launch_reduce_pixels<T, T>(tab, c->g.nx, c->N, part, out, st)));
         return WAM_OK;
     } catch (...) {
         return fail(c, WAM_ERR_OOM, "host allocation failed");

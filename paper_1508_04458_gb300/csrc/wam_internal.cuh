@@ -46,6 +46,7 @@ struct Segment {
     int level;          // 0: pixel basis (Omega = I); 1..L: Haar level
     int has_approx;     // accumulates the (unsigned) approximation slot
     int has_details;    // accumulates h+, h-, v+, v-, d+, d-
+    int quad;           // pixel basis, item = 2x2 pixels: slots = the four pixel sums
     int n_items;
     const uint32_t* items;   // packed (by << 16) | bx, or null: implicit row-major
     int gw;             // block-grid width for implicit items
@@ -186,7 +187,7 @@ __device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& 
     const T tx0 = (g.X0 + T(ix + (xpos ? 1 : 0)) * g.vx - r.px) * r.idx;
     const T ty0 = (g.Y0 + T(iy + (ypos ? 1 : 0)) * g.vy - r.py) * r.idy;
     T tx = tx0, ty = ty0;
-    int kx = 0, ky = 0;
+    T kx = T(0), ky = T(0);     // crossing counts, exact in T
     const int max_steps = g.nx + g.ny + 4;
     for (int step = 0; step < max_steps; ++step) {
         T te = fmin(fmin(tx, ty), r.tout);
@@ -196,12 +197,12 @@ __device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& 
         if (te >= r.tout) break;
         if (tx <= ty) {
             ix += sx;
-            ++kx;
-            tx = tx0 + T(kx) * ax;
+            kx += T(1);
+            tx = tx0 + kx * ax;
         } else {
             iy += sy;
-            ++ky;
-            ty = ty0 + T(ky) * ay;
+            ky += T(1);
+            ty = ty0 + ky * ay;
         }
         if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny) break;
     }
@@ -238,6 +239,34 @@ __device__ __forceinline__ void child_chords(T qx, T qy, T idx, T idy, T hx, T h
     c01 = fmax(fmin(xh1, yl1) - fmax(xh0, yl0), T(0));
     c10 = fmax(fmin(xl1, yh1) - fmax(xl0, yh0), T(0));
     c11 = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
+}
+
+// Crossing-ordered form of the same chords.  Measured along the unit
+// direction from a point of the ray, the ray crosses the block's centre lines
+// x = cx at t = a and y = cy at t = b, and its faces at a -+ Ax (x) and
+// b -+ Ay (y), Ax = hx |1/dx|, Ay = hy |1/dy|, always in this order.  The
+// half it crosses first along x is "F", the other "S" (likewise along y), so
+// the four child chords need no sorting:
+//   cFF = [max(a - Ax, b - Ay), min(a, b)]        (first x half, first y half)
+//   cFS = [max(a - Ax, b), min(a, b + Ay)]
+//   cSF = [max(a, b - Ay), min(a + Ax, b)]
+//   cSS = [max(a, b), min(a + Ax, b + Ay)]
+// (interval lengths, clamped at 0).  The first half along x is the lower one
+// when 1/dx > 0, the upper one otherwise (likewise y).
+template <typename T>
+__device__ __forceinline__ T block_chord_ab(T a, T b, T Ax, T Ay)
+{
+    return fmax(fmin(a + Ax, b + Ay) - fmax(a - Ax, b - Ay), T(0));
+}
+
+template <typename T>
+__device__ __forceinline__ void child_chords_ab(T a, T b, T Ax, T Ay, T& cFF, T& cFS, T& cSF, T& cSS)
+{
+    const T a0 = a - Ax, a2 = a + Ax, b0 = b - Ay, b2 = b + Ay;
+    cFF = fmax(fmin(a, b) - fmax(a0, b0), T(0));
+    cFS = fmax(fmin(a, b2) - fmax(a0, b), T(0));
+    cSF = fmax(fmin(a2, b) - fmax(a, b0), T(0));
+    cSS = fmax(fmin(a2, b2) - fmax(a, b), T(0));
 }
 
 }  // namespace wam

@@ -24,7 +24,8 @@ template <typename T>
 cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
                              cudaStream_t st);
 template <typename T, typename O>
-cudaError_t launch_reduce_pixels(const SegTable& tab, const T* part, O* out, cudaStream_t st);
+cudaError_t launch_reduce_pixels(const SegTable& tab, int nx, long long npix, const T* part, O* out,
+                                 cudaStream_t st);
 template <typename T>
 cudaError_t launch_synth(const Layout& lay, const uint8_t* leaf, const double* beta, T* mu, cudaStream_t st);
 cudaError_t launch_leafmap(const Layout& lay, const uint8_t* mask, uint8_t* leaf, cudaStream_t st);

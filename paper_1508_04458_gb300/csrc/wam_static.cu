@@ -50,7 +50,7 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
         return WAM_ERR_ARG;
     if (w->kind == WAM_FAN2D_FLAT) {
         const double r = 0.5 * std::hypot(w->nx * w->vx, w->ny * w->vy);
-        if (!(w->sod > r) || !(w->sdd > w->sod)) return WAM_ERR_ARG;
+        if (!(w->sod > r) || !(w->sdd - w->sod > r)) return WAM_ERR_ARG;
     }
     const long long N = (long long)w->nx * w->ny;
     const int V = w->n_views;
@@ -133,6 +133,6 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
     // every partial of every (pixel, view range) is written before it is read:
     // nothing in the scratch needs clearing
     if (launch_backproject<float>(g, tab, s, nullptr, part, nullptr, cst) != cudaSuccess) return WAM_ERR_CUDA;
-    if (launch_reduce_pixels<float, float>(tab, part, out, cst) != cudaSuccess) return WAM_ERR_CUDA;
+    if (launch_reduce_pixels<float, float>(tab, w->nx, N, part, out, cst) != cudaSuccess) return WAM_ERR_CUDA;
     return WAM_OK;
 }
