@@ -246,6 +246,18 @@ def run_wam(args, problem, world, rank, local_rank):
         _, ttt_mr = timed(lambda: step(n_iters=j_hit))
     # plain AM's own time to its final value is its full run
     (_, _, _, _), full_ms2 = timed(lambda: step(full=True, levels=0))
+    # objective-versus-time comparison: time for each method to reach plain
+    # AM's cost after k iterations (+1e-3), k = 10, 20, 50, 100
+    curve = []
+    for k in (10, 20, 50, 100):
+        tgt = float(hist_f[k]) * (1.0 + 1e-3)
+        _, t_full = timed(lambda: step(n_iters=k, full=True, levels=0))
+        jh = np.nonzero(hist_long <= tgt)[0]
+        t_mr = None
+        if jh.size:
+            _, t_mr = timed(lambda: step(n_iters=int(jh[0])))
+        curve.append({"full_am_iters": k, "target_idiv": tgt, "full_am_ms": t_full,
+                      "multires_iters": int(jh[0]) if jh.size else None, "multires_ms": t_mr})
 
     # ---- e2e through the C-ABI from host buffers
     d_host = np.ascontiguousarray(problem.d.astype(np.float32).ravel())
@@ -317,6 +329,7 @@ def run_wam(args, problem, world, rank, local_rank):
             "full_am": {"iters_per_s": N_ITERS / (full_ms2 / 1e3), "final_idiv": float(hist_f[-1]),
                         "ms_per_iter": full_ms2 / N_ITERS, "time_to_target_ms": full_ms2},
             "target_idiv": target,
+            "time_to_equal_objective": curve,
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "work": v["work"]}
                         for k, v in stats.items()},
             "wall_s_timed": wall,

@@ -204,6 +204,45 @@ wam_status wam_update(wam_ctx* ctx, int levels, const unsigned char* masks, cons
 wam_status wam_expand(wam_ctx* ctx, int levels, const float* S, double tau,
                       const unsigned char* mask_in, unsigned char* mask_out, void* stream);
 
+/* ---- operators of the full Haar basis and gradients ----------------------- */
+/* These treat every coefficient of the L-level basis as active (the full
+ * tree) and use FP32 device arrays in the coefficient layout above.  They
+ * serve differentiation through the method; calls on one context must not
+ * overlap (they share the context's work buffers). */
+
+/* p = Phi beta = H Omega beta (Sec. II, Eq. 1.2).  beta [nx*ny], p [V*B]. */
+wam_status wam_project_coef(wam_ctx* ctx, int levels, const float* beta, float* p, void* stream);
+
+/* g = Phi^T s = Omega^T H^T s.  s [V*B], g [nx*ny]. */
+wam_status wam_backproject_coef(wam_ctx* ctx, int levels, const float* s, float* g, void* stream);
+
+/* Value and gradient of L(beta) = I(d || I0 exp(-Phi beta)) + lambda *
+ * sum over detail coefficients of |beta| (the data term of Eq. 1.1 in the
+ * wavelet domain of Eq. 1.3, plus an L1 penalty on the details):
+ * dL/dbeta = Phi^T (d - qhat) + lambda sign(beta_detail).  loss: one device
+ * double (FP64 sum); grad [nx*ny]; qhat [V*B] optional output (may be NULL).
+ * Needs wam_set_data.  Errors: WAM_ERR_ARG for lambda < 0 or non-finite. */
+wam_status wam_idiv_grad(wam_ctx* ctx, int levels, const float* beta, float lambda, double* loss,
+                         float* grad, float* qhat, void* stream);
+
+/* Derivatives of the AM step Delta(b, bhat+, bhat-) of Eq. 1.9 with respect
+ * to bhat+ and bhat- (FP64 arithmetic): with u the positive root,
+ * dDelta/dbhat+ = u / (Z0 sqrt(b^2 - 4 bhat+ bhat-)),
+ * dDelta/dbhat- = 1 / (Z0 u sqrt(b^2 - 4 bhat+ bhat-)); 0 where the step is
+ * clamped or degenerate.  b, bplus, bminus [nx*ny] FP64, z0 device double;
+ * dplus, dminus [nx*ny] FP32. */
+wam_status wam_am_derivs(wam_ctx* ctx, int levels, const double* b, const double* bplus,
+                         const double* bminus, const double* z0, double clamp, float* dplus,
+                         float* dminus, void* stream);
+
+/* out(y) = qhat(y) * sum_z [max(phi(y|z), 0) gbar(z) dplus(z) +
+ * min(phi(y|z), 0) gbar(z) dminus(z)] over every z of the full basis: the
+ * projection through the positive and negative parts of Phi used by
+ * Eq. 1.10, here to apply the transposed Jacobian of bhat+-(beta).
+ * qhat may be NULL (factor 1).  gbar, dplus, dminus [nx*ny], out [V*B]. */
+wam_status wam_phi_split_project(wam_ctx* ctx, int levels, const float* gbar, const float* dplus,
+                                 const float* dminus, const float* qhat, float* out, void* stream);
+
 /* ---- back-projection without device allocation ---------------------------- */
 
 /* Size of the library's fixed device scratch used by wam_backproject_static. */

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kFwdTPB)
 k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
           const float* __restrict__ d, const double* __restrict__ dterm,
           const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
-          double* __restrict__ cost_part, unsigned long long* __restrict__ work)
+          T* __restrict__ resid, double* __restrict__ cost_part, unsigned long long* __restrict__ work)
 {
     const int v = blockIdx.y;
     const int b = blockIdx.x * kFwdTPB + threadIdx.x;
@@ -88,9 +88,10 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
         }
         const size_t y = (size_t)v * g.B + b;
         if (p_out) p_out[y] = acc;
-        if (qhat) {
+        if (qhat || resid) {
             const T q = T(I0[y]) * exp(-acc);
-            qhat[y] = q;
+            if (qhat) qhat[y] = q;
+            if (resid) resid[y] = T(d[y]) - q;   // dI/dp = d - q
             // d log(d/q) - d + q = [d (log d - log I0) - d] + d p + q
             term = dterm[y] + (double)d[y] * (double)acc + (double)q;
         }
@@ -778,19 +779,22 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 template <typename T>
 cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d,
-                           const double* dterm, const float* I0, T* qhat, T* p_out, double* cost_part,
+                           const double* dterm, const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st)
 {
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
     COUNT_LAUNCH();
     if (leaf)
-        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
+        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, resid, cost_part,
+                                                      work);
     else
-        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, cost_part, work);
+        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, resid, cost_part,
+                                                     work);
     return cudaGetLastError();
 }
 
@@ -982,7 +986,7 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
 // explicit instantiations
 #define WAM_INST(T)                                                                                              \
     template cudaError_t launch_forward<T>(const Geom<T>&, const T*, const uint8_t*, const float*, const double*, \
-                                           const float*, T*, T*, double*, unsigned long long*, cudaStream_t);    \
+                                           const float*, T*, T*, T*, double*, unsigned long long*, cudaStream_t); \
     template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \

@@ -24,7 +24,7 @@ enum BufId {
     B_CS32, B_CS64, B_D, B_I0, B_DTERM,
     B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
-    B_DIR32, B_DIR64,
+    B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
     B_NBUF
 };
 
@@ -531,7 +531,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
         }
         {
             PROF(WAM_K_FORWARD);                                                            // a2, a3
-            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
             WCK(c, launch_sum_final(cpart, np, costs + j, st));
         }
@@ -568,7 +568,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     }
     {
         PROF(WAM_K_FORWARD);
-        WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, cpart,
+        WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                               work_ptr(c, WAM_K_FORWARD), st));
         WCK(c, launch_sum_final(cpart, np, costs + J, st));
     }
@@ -594,7 +594,7 @@ wam_status project_impl(wam_ctx* c, const T* mu, T* p, void* stream)
     if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
     Geom<T> g;
     WST(make_geom<T>(c, &g));
-    WCK(c, launch_forward<T>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+    WCK(c, launch_forward<T>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, nullptr,
                              as_stream(stream)));
     return WAM_OK;
 }
@@ -650,7 +650,8 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
     WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
     WCK(c, launch_forward<T>(g, mu, leaf, static_cast<const float*>(c->buf[B_D].p),
                              static_cast<const double*>(c->buf[B_DTERM].p),
-                             static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, cpart, nullptr, st));
+                             static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr, cpart, nullptr,
+                             st));
     WCK(c, launch_sum_final(cpart, np, cost, st));
     return WAM_OK;
 }
@@ -937,5 +938,148 @@ wam_status wam_get_stats(wam_ctx* c, wam_stats* out)
 }
 
 unsigned long long wam_kernel_launches(void) { return wam::kernel_launches(); }
+
+}  // extern "C"
+
+// ---- operators of the full Haar basis and the gradient pieces ---------------
+
+namespace {
+
+// mu = Omega beta (full L-level basis), float in and out; FP64 synthesis
+wam_status coef_to_image(wam_ctx* c, const Layout& lay, const float* beta, float** mu, cudaStream_t st)
+{
+    double* b64 = nullptr;
+    WST(ensure_t(c, B_GBETA, (size_t)c->N, &b64));
+    WST(ensure_t(c, B_GMU, (size_t)c->N, mu));
+    WCK(c, (launch_convert<float, double>(beta, b64, c->N, st)));
+    WCK(c, launch_synth<float>(lay, nullptr, b64, *mu, st));
+    return WAM_OK;
+}
+
+// coef (FP64) = Omega^T H^T s
+wam_status sino_to_coef(wam_ctx* c, const Layout& lay, const float* s, double** coef, cudaStream_t st)
+{
+    Geom<float> g;
+    WST(make_geom<float>(c, &g));
+    const void* dirt = nullptr;
+    WST(dir_table<float>(c, &dirt));
+    SegTable tab;
+    float* part = nullptr;
+    WST(plan_pixels<float>(c, &tab, &part));
+    double *gimg = nullptr, *ta = nullptr, *tb = nullptr;
+    WST(ensure_t(c, B_GIMG, (size_t)c->N, &gimg));
+    WST(ensure_t(c, B_TMPA, (size_t)c->N, &ta));
+    WST(ensure_t(c, B_TMPB, (size_t)c->N, &tb));
+    WST(ensure_t(c, B_GCOEF, (size_t)c->N, coef));
+    WCK(c, launch_backproject(g, tab, s, dirt, part, nullptr, st));
+    WCK(c, (launch_reduce_pixels<float, double>(tab, c->g.nx, c->N, part, gimg, st)));
+    WCK(c, launch_haar(lay, gimg, *coef, 0, ta, tb, st));
+    return WAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!beta || !p) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        cudaStream_t st = as_stream(stream);
+        float* mu = nullptr;
+        WST(coef_to_image(c, lay, beta, &mu, st));
+        Geom<float> g;
+        WST(make_geom<float>(c, &g));
+        WCK(c, launch_forward<float>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+                                     nullptr, st));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_backproject_coef(wam_ctx* c, int levels, const float* s, float* gout, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!s || !gout) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        cudaStream_t st = as_stream(stream);
+        double* coef = nullptr;
+        WST(sino_to_coef(c, lay, s, &coef, st));
+        WCK(c, (launch_convert<double, float>(coef, gout, c->N, st)));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda, double* loss, float* grad,
+                         float* qhat, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    if (!beta || !loss || !grad) return fail(c, WAM_ERR_ARG, "null pointer");
+    if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(c, WAM_ERR_ARG, "lambda must be finite and >= 0");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        cudaStream_t st = as_stream(stream);
+        float* mu = nullptr;
+        WST(coef_to_image(c, lay, beta, &mu, st));
+        Geom<float> g;
+        WST(make_geom<float>(c, &g));
+        const int np = forward_parts(g.V, g.B);
+        double* cpart = nullptr;
+        float* res = nullptr;
+        WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+        WST(ensure_t(c, B_GRES, (size_t)c->M, &res));
+        WCK(c, launch_forward<float>(g, mu, nullptr, static_cast<const float*>(c->buf[B_D].p),
+                                     static_cast<const double*>(c->buf[B_DTERM].p),
+                                     static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, res, cpart, nullptr,
+                                     st));
+        double* coef = nullptr;
+        WST(sino_to_coef(c, lay, res, &coef, st));
+        const int nl1 = (int)((c->N + 255) / 256);
+        double* l1 = nullptr;
+        WST(ensure_t(c, B_L1PART, (size_t)nl1 + np, &l1));
+        WCK(c, launch_l1(lay, beta, coef, lambda, grad, l1, nl1, st));
+        // loss = sum of the cost partials and the L1 partials, fixed order
+        WCK(c, cudaMemcpyAsync(l1 + nl1, cpart, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        WCK(c, launch_sum_final(l1, nl1 + np, loss, st));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_am_derivs(wam_ctx* c, int levels, const double* b, const double* bplus, const double* bminus,
+                         const double* z0, double clamp, float* dplus, float* dminus, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!b || !bplus || !bminus || !z0 || !dplus || !dminus) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    WCK(c, launch_am_derivs(lay, b, bplus, bminus, z0, clamp > 0 ? clamp : 30.0, dplus, dminus,
+                            as_stream(stream)));
+    return WAM_OK;
+}
+
+wam_status wam_phi_split_project(wam_ctx* c, int levels, const float* gbar, const float* dplus,
+                                 const float* dminus, const float* qhat, float* out, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!gbar || !dplus || !dminus || !out) return fail(c, WAM_ERR_ARG, "null pointer");
+    Layout lay;
+    WST(make_layout(c, levels, &lay));
+    Geom<float> g;
+    WST(make_geom<float>(c, &g));
+    WCK(c, launch_phi_project(g, lay, gbar, dplus, dminus, qhat, out, as_stream(stream)));
+    return WAM_OK;
+}
 
 }  // extern "C"

@@ -7,8 +7,8 @@ namespace wam {
 
 template <typename T>
 cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d, const double* dterm,
-                           const float* I0, T* qhat, T* p_out, double* cost_part, unsigned long long* work,
-                           cudaStream_t st);
+                           const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
+                           unsigned long long* work, cudaStream_t st);
 int forward_parts(int V, int B);
 cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st);
 cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st);
@@ -44,5 +44,14 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
                                 const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st);
 
 unsigned long long kernel_launches();
+void count_launch();
+
+// grad.cu: operators for the gradient and the unrolled-AM patterns
+cudaError_t launch_phi_project(const Geom<float>& g, const Layout& lay, const float* gbar, const float* dplus,
+                               const float* dminus, const float* qhat, float* out, cudaStream_t st);
+cudaError_t launch_am_derivs(const Layout& lay, const double* b, const double* bp, const double* bm,
+                             const double* z0, double clamp, float* dplus, float* dminus, cudaStream_t st);
+cudaError_t launch_l1(const Layout& lay, const float* beta, const double* g, float lambda, float* grad,
+                      double* part, int nparts, cudaStream_t st);
 
 }  // namespace wam

@@ -86,6 +86,11 @@ _PROTOS = {
     "wam_z0": (_S, [_P, _I, _P, _P, _P]),
     "wam_update": (_S, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "wam_expand": (_S, [_P, _I, _P, _D, _P, _P, _P]),
+    "wam_project_coef": (_S, [_P, _I, _P, _P, _P]),
+    "wam_backproject_coef": (_S, [_P, _I, _P, _P, _P]),
+    "wam_idiv_grad": (_S, [_P, _I, _P, ctypes.c_float, _P, _P, _P, _P]),
+    "wam_am_derivs": (_S, [_P, _I, _P, _P, _P, _P, _D, _P, _P, _P]),
+    "wam_phi_split_project": (_S, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "wam_backproject_static": (_S, [ctypes.POINTER(wam_geometry), _P, _P, _P]),
     "wam_profile": (_S, [_P, _I]),
     "wam_get_stats": (_S, [_P, _P]),
