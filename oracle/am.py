@@ -226,3 +226,74 @@ def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None) -> AMResult:
     costs.append(idiv(d, I0, Hc @ mu))
     out = mu.reshape(shape) if shape is not None else mu
     return AMResult(mu, out, np.array(costs), np.array(z0s), None, [], np.array([H.shape[1]] * n_iter))
+
+
+# ---------------------------------------------------------------------------
+# 3-D Haar trees (volume blocks of 2^l voxels per side, seven details each)
+# ---------------------------------------------------------------------------
+
+def empty_tree3d(nx: int, ny: int, nz: int, L: int) -> List[np.ndarray]:
+    """tree[l-1][bz, by, bx] is True when the level-l block's 7 details are active."""
+    return [np.zeros((nz >> l, ny >> l, nx >> l), dtype=bool) for l in range(1, L + 1)]
+
+
+def active_mask3d(tree, nx: int, ny: int, nz: int, L: int) -> np.ndarray:
+    from . import haar3d
+    level, typ, bx, by, bz = haar3d.coefficient_info(nx, ny, nz, L)
+    act = typ == 0
+    for l in range(1, L + 1):
+        sel = (level == l) & (typ > 0)
+        act[sel] = tree[l - 1][bz[sel], by[sel], bx[sel]]
+    return act
+
+
+def leaf_levels3d(tree, nx: int, ny: int, nz: int, L: int) -> np.ndarray:
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lev = np.full((nz, ny, nx), L, dtype=np.int64)
+    descending = np.ones((nz, ny, nx), dtype=bool)
+    for l in range(L, 0, -1):
+        descending &= tree[l - 1][iz >> l, iy >> l, ix >> l]
+        lev[descending] = l - 1
+    return lev
+
+
+def expand3d(tree, S: np.ndarray, tau: float):
+    """The expansion rule on a volume S ([nz, ny, nx])."""
+    nz, ny, nx = S.shape
+    L = len(tree)
+    S64 = np.asarray(S, dtype=np.float64)
+    sel = np.ones_like(S64, dtype=bool) if tau < 0 else S64 > float(tau) * float(S64.max())
+    lev = leaf_levels3d(tree, nx, ny, nz, L)
+    new = [t.copy() for t in tree]
+    iz, iy, ix = np.nonzero(sel & (lev >= 1))
+    for l in range(1, L + 1):
+        m = lev[iz, iy, ix] == l
+        new[l - 1][iz[m] >> l, iy[m] >> l, ix[m] >> l] = True
+    return new
+
+
+def wavelet_am3d(H: sp.spmatrix, d, I0, nx: int, ny: int, nz: int, L: int, n_iter: int,
+                 expand_at: Sequence[int] = (), taus: Sequence[float] = ()) -> AMResult:
+    """Algorithm 1 with a 3-D Haar basis and a 3-D tree (criterion S = mu)."""
+    from . import haar3d
+    d = np.asarray(d, dtype=np.float64).ravel()
+    Omega = haar3d.basis_matrix(nx, ny, nz, L)
+    Phi = (H @ Omega).tocsc()
+    b = Phi.T @ d
+    beta = np.zeros(nx * ny * nz)
+    tree = empty_tree3d(nx, ny, nz, L)
+    costs, z0s, trees, nact = [], [], [], []
+    sched = dict(zip(expand_at, taus))
+    for j in range(n_iter):
+        act = active_mask3d(tree, nx, ny, nz, L)
+        delta, cost, Z0 = am_step(Phi[:, act], b[act], beta[act], d, I0)
+        costs.append(cost)
+        z0s.append(Z0)
+        nact.append(int(act.sum()))
+        beta[act] += delta
+        if (j + 1) in sched:
+            tree = expand3d(tree, (Omega @ beta).reshape(nz, ny, nx), sched[j + 1])
+            trees.append([t.copy() for t in tree])
+    costs.append(idiv(d, I0, Phi @ beta))
+    return AMResult(beta, (Omega @ beta).reshape(nz, ny, nx), np.array(costs), np.array(z0s), tree, trees,
+                    np.array(nact))

@@ -84,6 +84,27 @@ def siddon_matrix(seg: np.ndarray, shape, size) -> sp.csr_matrix:
     return sp.csr_matrix((vals, cols, rowptr), shape=(R, N))
 
 
+def ray_segments_cone(g) -> np.ndarray:
+    """(n_rays, 6) segments of a circular cone-beam scan: from the source
+    SOD e (z = 0) to the flat-detector point -(SDD - SOD) e + u_b u + v_r z,
+    v_r = (r - (n_rows - 1)/2) * row_pitch; rays indexed
+    (view * n_rows + row) * n_bins + bin."""
+    th = g.angle0 + np.arange(g.n_views, dtype=np.float64) * (g.angle_span / g.n_views)
+    ub = (np.arange(g.n_bins, dtype=np.float64) - 0.5 * (g.n_bins - 1)) * g.bin_pitch
+    vr = (np.arange(g.n_rows, dtype=np.float64) - 0.5 * (g.n_rows - 1)) * g.row_pitch
+    seg = np.zeros((g.n_views, g.n_rows, g.n_bins, 6))
+    c = np.cos(th)[:, None, None]
+    s = np.sin(th)[:, None, None]
+    seg[..., 0] = g.sod * c
+    seg[..., 1] = g.sod * s
+    seg[..., 3] = -(g.sdd - g.sod) * c - ub[None, None, :] * s
+    seg[..., 4] = -(g.sdd - g.sod) * s + ub[None, None, :] * c
+    seg[..., 5] = vr[None, :, None]
+    return seg.reshape(-1, 6)
+
+
 def system_matrix(g) -> sp.csr_matrix:
-    """H for a 2-D scan (rays x pixels)."""
+    """H for a 2-D scan (rays x pixels) or a cone-beam scan (rays x voxels)."""
+    if g.kind == 2:
+        return siddon_matrix(ray_segments_cone(g), (g.nx, g.ny, g.nz), (g.vx, g.vy, g.vz))
     return siddon_matrix(ray_segments(g), (g.nx, g.ny), (g.vx, g.vy))
