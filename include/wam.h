@@ -31,6 +31,21 @@
  *    ..., 1 in turn, each level (ny>>l) x (nx>>l) row-major; nonzero = the
  *    block is expanded, i.e. its three level-l details are active.  The
  *    level-L approximations are always active.  Total size wam_mask_bytes().
+ *  - Cone beam (kind WAM_CONE3D_FLAT_CIRCULAR): volume nx*ny*nz voxels,
+ *    index (iz*ny + iy)*nx + ix, centred at the origin; ray (view k, row r,
+ *    bin b) from the source SOD e (z = 0) to -(SDD - SOD) e + u_b u + v_r z,
+ *    v_r = (r - (n_rows - 1)/2) * row_pitch; sinogram [n_views][n_rows][n_bins].
+ *    Two wavelet modes (wam_schedule.dims): 3 = orthonormal 3-D Haar (block of
+ *    2^l voxels per side, value +-2^(-3l/2); seven details of type t = 1..7,
+ *    a bit mask of the differenced axes x = 1, y = 2, z = 4, - on the upper
+ *    half; layout: level-L approximations z-major, then for l = L..1 the planes
+ *    t = 1..7, each (nz>>l, ny>>l, nx>>l); masks per level (nz>>l)(ny>>l)(nx>>l));
+ *    2 with zsum_criterion = 1 = the 2-D Haar above applied to every z-slice
+ *    (coefficients slice-major, nx*ny per slice) under one 2-D tree shared
+ *    by all slices, expansion criterion S = sum over z of mu.  Cone-beam
+ *    contexts support wam_set_data, wam_reconstruct (precision 32),
+ *    wam_project, wam_backproject and the measurement calls; the other
+ *    step-level calls return WAM_ERR_ARG.
  *  - Pointers named on_device / documented as device pointers are
  *    caller-owned CUDA device memory used on `stream` (a cudaStream_t, NULL =
  *    the legacy default stream); the library never retains them after the
@@ -66,7 +81,7 @@ enum { WAM_PARALLEL2D = 0, WAM_FAN2D_FLAT = 1, WAM_CONE3D_FLAT_CIRCULAR = 2 };
 
 /* Scan geometry (Sec. II names H only abstractly; the scan is ours). */
 typedef struct {
-    int kind;                 /* WAM_PARALLEL2D or WAM_FAN2D_FLAT */
+    int kind;                 /* WAM_PARALLEL2D, WAM_FAN2D_FLAT or WAM_CONE3D_FLAT_CIRCULAR */
     int nx, ny, nz;           /* voxels; nz = 1 for 2-D */
     double vx, vy, vz;        /* voxel size, mm */
     int n_views;
@@ -79,12 +94,12 @@ typedef struct {
 /* Reconstruction schedule (Algorithm 1 + the Results section's tree growth). */
 typedef struct {
     int levels;               /* Haar levels L, 0..WAM_MAX_LEVELS (ignored if full_am) */
-    int dims;                 /* 2 */
+    int dims;                 /* 2 (2-D Haar; per z-slice for cone beam) or 3 (3-D Haar) */
     int n_iters;              /* J */
     int n_expand;             /* number of tree expansions */
     const int* expand_at;     /* host [n_expand]: expand after this many iterations */
     const double* tau;        /* host [n_expand]: threshold factor; < 0 = every leaf */
-    int zsum_criterion;       /* reserved for the per-slice 3-D mode (0) */
+    int zsum_criterion;       /* cone beam, dims 2: 1 = expansion criterion summed over z */
     int precision;            /* 32 (FP32 bulk) or 64 (FP64 everywhere) */
     int full_am;              /* 1: plain AM, Omega = I, every pixel active */
     double dmax_clamp;        /* clamp on |Z0 * delta|; <= 0 means 30 */
@@ -110,6 +125,10 @@ const char* wam_last_error(const wam_ctx* ctx);
 /* Bytes of a tree mask for L levels (sum over l = 1..L of (ny>>l)(nx>>l)). */
 size_t wam_mask_bytes(const wam_ctx* ctx, int levels);
 
+/* The same for a schedule's dims: 3 gives the 3-D Haar tree of a cone-beam
+ * context (sum of (nz>>l)(ny>>l)(nx>>l)); otherwise wam_mask_bytes. */
+size_t wam_mask_bytes_dims(const wam_ctx* ctx, int levels, int dims);
+
 /* ---- data --------------------------------------------------------------- */
 
 /* Set the counts d [n_views][n_bins] (>= 0, finite) and the incident counts
@@ -131,7 +150,8 @@ wam_status wam_set_data(wam_ctx* ctx, const float* d, const float* I0, int I0_is
  *   idiv_hist [n_iters + 1] I(d || qhat^(j)), j = 0..n_iters, FP64, host or
  *             device per on_device (entry j is the cost before update j; the
  *             last one is the cost of the final image)
- *   mask_out  [wam_mask_bytes(L)] final tree, host or device per on_device
+ *   mask_out  [wam_mask_bytes_dims(L, dims)] final tree, host or device per
+ *             on_device
  * Returns WAM_WARN_NONMONOTONE when some cost exceeded its predecessor by
  * more than 1e-6 relative (FP32) or 1e-11 (FP64).  Errors: WAM_ERR_STATE if
  * no data were set; WAM_ERR_ARG for a bad schedule (nx, ny not divisible by

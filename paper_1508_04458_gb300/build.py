@@ -12,8 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libwam.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["kernels.cu", "wam_api.cu", "wam_static.cu", "grad.cu"]
-HEADERS = ["wam_internal.cuh", "wam_kernels.h"]
+SOURCES = ["kernels.cu", "wam_api.cu", "wam_static.cu", "grad.cu", "cone3d.cu"]
+HEADERS = ["wam_internal.cuh", "wam_kernels.h", "cone3d.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

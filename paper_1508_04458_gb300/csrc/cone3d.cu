@@ -1,0 +1,942 @@
+// 3-D circular cone-beam kernels (sm_103a, FP32 bulk, FP64 cost and
+// update): the same steps as the 2-D path (Algorithm 1 with the Results
+// section's tree growth) for a volume, with either the 3-D Haar transform
+// (octree blocks, seven details) or the 2-D Haar transform of each z-slice
+// under one shared tree (the paper's own 3-D setting).  All sums run in a
+// fixed order.
+#include "cone3d.cuh"
+#include "wam_kernels.h"
+
+#include <math.h>
+
+namespace wam {
+
+namespace {
+
+inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename V>
+__device__ __forceinline__ V wsum(V x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+template <typename V>
+__device__ __forceinline__ V wmax(V x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const V y = __shfl_down_sync(0xffffffffu, x, o);
+        x = x > y ? x : y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void add_work3(unsigned long long* work, unsigned cnt)
+{
+    if (!work) return;
+    const unsigned m = __activemask();
+    const unsigned tot = __reduce_add_sync(m, cnt);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicAdd(work, (unsigned long long)tot);
+}
+
+// x with its sign flipped where sgn < 0
+__device__ __forceinline__ float flipf(float x, float sgn)
+{
+    return __int_as_float(__float_as_int(x) ^ (__float_as_int(sgn) & 0x80000000));
+}
+
+// 2^(-3l/2) (3-D Haar) or 2^-l (2-D Haar per slice)
+__host__ __device__ __forceinline__ double basis_scale(int z3, int l)
+{
+    return z3 ? 1.0 / ((double)(1 << l) * sqrt((double)(1 << l))) : 1.0 / (double)(1 << l);
+}
+
+// ---------------------------------------------------------------------------
+// one cone-beam ray: P(t) = P0 + t dir, |dir| = 1, P0 the ray's point in the
+// plane through the rotation axis normal to e (|P0| <= the image reach)
+// ---------------------------------------------------------------------------
+struct Ray3 {
+    float px, py, pz, dx, dy, dz, idx, idy, idz, tin, tout;
+};
+
+__device__ __forceinline__ float srcp(float d)
+{
+    float a = fabsf(d);
+    a = a < 1e-30f ? 1e-30f : a;
+    const float r = 1.0f / a;
+    return signbit(d) ? -r : r;
+}
+
+__device__ __forceinline__ bool make_ray3(const Geom3& g, int v, int r, int b, Ray3& ray)
+{
+    const float c = g.cs[2 * v], s = g.cs[2 * v + 1];
+    const float ub = ((float)b - g.ucen) * g.pitch;
+    const float vr = ((float)r - g.rcen) * g.rpitch;
+    const float Dx = -g.sdd * c - ub * s, Dy = -g.sdd * s + ub * c, Dz = vr;
+    const float n = g.dlen[(size_t)r * g.B + b];
+    const float in = 1.0f / n;
+    ray.dx = Dx * in;
+    ray.dy = Dy * in;
+    ray.dz = Dz * in;
+    const float al = g.sod / g.sdd;
+    ray.px = -al * ub * s;
+    ray.py = al * ub * c;
+    ray.pz = al * vr;
+    const float tlo = -al * n, thi = (1.0f - al) * n;
+    ray.idx = srcp(ray.dx);
+    ray.idy = srcp(ray.dy);
+    ray.idz = srcp(ray.dz);
+    const float X1 = g.X0 + g.nx * g.vx, Y1 = g.Y0 + g.ny * g.vy, Z1 = g.Z0 + g.nz * g.vz;
+    const float a0 = (g.X0 - ray.px) * ray.idx, a1 = (X1 - ray.px) * ray.idx;
+    const float b0 = (g.Y0 - ray.py) * ray.idy, b1 = (Y1 - ray.py) * ray.idy;
+    const float e0 = (g.Z0 - ray.pz) * ray.idz, e1 = (Z1 - ray.pz) * ray.idz;
+    ray.tin = fmaxf(tlo, fmaxf(fmaxf(fminf(a0, a1), fminf(b0, b1)), fminf(e0, e1)));
+    ray.tout = fminf(thi, fminf(fminf(fmaxf(a0, a1), fmaxf(b0, b1)), fmaxf(e0, e1)));
+    return ray.tout > ray.tin;
+}
+
+// Visit the leaf blocks crossed by the ray.  leaf: level per voxel (z3) or
+// per (ix, iy) (slices); null: every voxel is a leaf.  visit(ix, iy, iz,
+// lam, bx0, by0, bz0, chord).  Each step crosses one grid plane forward.
+template <typename F>
+__device__ __forceinline__ void walk3(const Geom3& g, const uint8_t* __restrict__ leaf, int z3, const Ray3& r,
+                                      F&& visit)
+{
+    float t = r.tin;
+    int ix = clampi((int)floorf((r.px + t * r.dx - g.X0) * g.ivx), 0, g.nx - 1);
+    int iy = clampi((int)floorf((r.py + t * r.dy - g.Y0) * g.ivy), 0, g.ny - 1);
+    int iz = clampi((int)floorf((r.pz + t * r.dz - g.Z0) * g.ivz), 0, g.nz - 1);
+    const bool xp = r.idx > 0.0f, yp = r.idy > 0.0f, zp = r.idz > 0.0f;
+    const int max_steps = g.nx + g.ny + g.nz + 6;
+    for (int step = 0; step < max_steps; ++step) {
+        int lam = 0;
+        if (leaf) lam = z3 ? (int)leaf[((size_t)iz * g.ny + iy) * g.nx + ix] : (int)leaf[(size_t)iy * g.nx + ix];
+        const int bs = 1 << lam, bsz = z3 ? bs : 1;
+        const int bx0 = (ix >> lam) << lam, by0 = (iy >> lam) << lam;
+        const int bz0 = z3 ? (iz >> lam) << lam : iz;
+        const float tx = (g.X0 + (float)(xp ? bx0 + bs : bx0) * g.vx - r.px) * r.idx;
+        const float ty = (g.Y0 + (float)(yp ? by0 + bs : by0) * g.vy - r.py) * r.idy;
+        const float tz = (g.Z0 + (float)(zp ? bz0 + bsz : bz0) * g.vz - r.pz) * r.idz;
+        float te = fminf(fminf(fminf(tx, ty), tz), r.tout);
+        te = fmaxf(te, t);
+        visit(ix, iy, iz, lam, bx0, by0, bz0, te - t);
+        t = te;
+        if (te >= r.tout) break;
+        const float ex = r.px + te * r.dx, ey = r.py + te * r.dy, ez = r.pz + te * r.dz;
+        if (tx <= ty && tx <= tz) {
+            ix = xp ? bx0 + bs : bx0 - 1;
+            iy = clampi((int)floorf((ey - g.Y0) * g.ivy), by0, by0 + bs - 1);
+            iz = clampi((int)floorf((ez - g.Z0) * g.ivz), bz0, bz0 + bsz - 1);
+        } else if (ty <= tz) {
+            iy = yp ? by0 + bs : by0 - 1;
+            ix = clampi((int)floorf((ex - g.X0) * g.ivx), bx0, bx0 + bs - 1);
+            iz = clampi((int)floorf((ez - g.Z0) * g.ivz), bz0, bz0 + bsz - 1);
+        } else {
+            iz = zp ? bz0 + bsz : bz0 - 1;
+            ix = clampi((int)floorf((ex - g.X0) * g.ivx), bx0, bx0 + bs - 1);
+            iy = clampi((int)floorf((ey - g.Y0) * g.ivy), by0, by0 + bs - 1);
+        }
+        if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny || (unsigned)iz >= (unsigned)g.nz)
+            break;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// a2 + a3: projection (leaf or voxel walk), Beer's law, FP64 cost terms
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFwdTPB)
+k_forward3(Geom3 g, const float* __restrict__ mu, const uint8_t* __restrict__ leaf, int z3,
+           const float* __restrict__ d, const double* __restrict__ dterm, const float* __restrict__ I0,
+           float* __restrict__ qhat, float* __restrict__ p_out, double* __restrict__ cost_part,
+           unsigned long long* __restrict__ work)
+{
+    const int v = blockIdx.z, r = blockIdx.y;
+    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    double term = 0.0;
+    unsigned steps = 0;
+    if (b < g.B) {
+        Ray3 ray;
+        float acc = 0.0f;
+        if (make_ray3(g, v, r, b, ray)) {
+            walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
+                acc += c * __ldg(mu + ((size_t)iz * g.ny + iy) * g.nx + ix);
+                ++steps;
+            });
+        }
+        const size_t y = ((size_t)v * g.R + r) * g.B + b;
+        if (p_out) p_out[y] = acc;
+        if (qhat) {
+            const float q = I0[y] * expf(-acc);
+            qhat[y] = q;
+            term = dterm[y] + (double)d[y] * (double)acc + (double)q;
+        }
+    }
+    add_work3(work, steps);
+    if (cost_part) {
+        term = wsum(term);
+        if ((threadIdx.x & 31) == 0)
+            cost_part[(((size_t)v * g.R + r) * gridDim.x + blockIdx.x) * (kFwdTPB / 32) + (threadIdx.x >> 5)] = term;
+    }
+}
+
+int forward3_parts(const Geom3& g) { return (int)nb(g.B, kFwdTPB) * g.V * g.R * (kFwdTPB / 32); }
+
+cudaError_t launch_forward3(const Geom3& g, const float* mu, const uint8_t* leaf, int z3, const float* d,
+                            const double* dterm, const float* I0, float* qhat, float* p_out, double* cost_part,
+                            unsigned long long* work, cudaStream_t st)
+{
+    count_launch();
+    dim3 grid(nb(g.B, kFwdTPB), g.R, g.V);
+    k_forward3<<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, z3, d, dterm, I0, qhat, p_out, cost_part, work);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a0, a4: voxel-driven split back-projection.  CTA = 32 items x 8 warps (each
+// warp its own views).  Per (block, view) the shadow (bins x rows) from the 8
+// corners; per ray the chords through the children in crossing-ordered form
+// (parameter tau along D = -SDD e + u_b u + v_r z; chords in mm = dtau |D|):
+//   x halves [a - Ax, a], [a, a + Ax], y halves [b - Ay, b], [b, b + Ay],
+//   z halves [c - Az, c], [c, c + Az]  (first / second along the ray).
+// Modes: octet (voxel basis, 2x2x2 voxels: the 8 voxel chords in physical
+// order, sums of non-negative terms), 3-D Haar (8 octants: approximation + 7
+// details split by sign), per-slice 2-D Haar (4 quadrants clipped to the
+// slice: approximation + 3 details), or a single block chord.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void decode3(const Segment3& S, int item, int& bx, int& by, int& bz)
+{
+    if (S.items) {
+        const uint32_t w = S.items[S.rep > 0 ? item % S.rep : item];
+        bx = (int)(w & 1023u);
+        by = (int)((w >> 10) & 1023u);
+        bz = S.rep > 0 ? item / S.rep : (int)(w >> 20);
+    } else {
+        bx = item % S.gw;
+        const int rest = item / S.gw;
+        by = rest % S.gh;
+        bz = rest / S.gh;
+    }
+}
+
+__global__ void __launch_bounds__(kBackTPB)
+k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, float* __restrict__ part,
+               unsigned long long* __restrict__ work)
+{
+    __shared__ float red[kViewLanes][kSlots3][kItemsPerCta];
+    const int cta = blockIdx.x;
+    int si = 0;
+    while (si + 1 < tab.n && cta >= tab.s[si + 1].cta_begin) ++si;
+    const Segment3& S = tab.s[si];
+    const int local = cta - S.cta_begin;
+    const int chunk = local / S.tiles, tile = local - chunk * S.tiles;
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int item = tile * kItemsPerCta + lane;
+    const bool valid = item < S.n_items;
+    const bool oct = S.octet != 0, det = S.has_details != 0;
+    // 0: single chord; 1: 8 octant chords; 2: 4 quadrant chords within the slice
+    const int mode = (oct || (det && z3)) ? 1 : (det ? 2 : 0);   // oct handled inside mode 1
+    float acc[kSlots3];
+#pragma unroll
+    for (int k = 0; k < kSlots3; ++k) acc[k] = 0.0f;
+    unsigned evals = 0;
+    if (valid) {
+        int bx, by, bz;
+        decode3(S, item, bx, by, bz);
+        const int l = S.level;
+        const int bs = 1 << l;
+        const int bsz = oct ? 2 : (z3 ? bs : 1);
+        const float hx = 0.5f * bs * g.vx, hy = 0.5f * bs * g.vy, hz = 0.5f * bsz * g.vz;
+        const float cx = g.X0 + (2 * bx + 1) * hx, cy = g.Y0 + (2 * by + 1) * hy;
+        const float cz = g.Z0 + (2 * bz + 1) * hz;
+        const float scale = oct ? 1.0f : (float)basis_scale(z3, l);
+        const int v0 = chunk * S.vpc, v1 = min(g.V, v0 + S.vpc);
+        const float isdd = 1.0f / g.sdd, ipitch = 1.0f / g.pitch, irp = 1.0f / g.rpitch;
+        for (int v = v0 + wv; v < v1; v += kViewLanes) {
+            const float c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
+            const float ac = cx * c + cy * s, wc = -cx * s + cy * c;
+            float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy, oz = (k & 4) ? hz : -hz;
+                const float den = __fdividef(g.sdd, g.sod - (ac + ox * c + oy * s));
+                const float uu = (wc - ox * s + oy * c) * den, vv = (cz + oz) * den;
+                umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+                vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+            }
+            const int blo = max(0, (int)floorf(umin * ipitch + g.ucen - 1e-4f));
+            const int bhi = min(g.B - 1, (int)ceilf(umax * ipitch + g.ucen + 1e-4f));
+            const int rlo = max(0, (int)floorf(vmin * irp + g.rcen - 1e-4f));
+            const int rhi = min(g.R - 1, (int)ceilf(vmax * irp + g.rcen + 1e-4f));
+            if (blo > bhi || rlo > rhi) continue;
+            evals += (unsigned)((bhi - blo + 1) * (rhi - rlo + 1));
+            const float kappa = (g.sod - ac) * isdd;
+            const float4* drow = g.dirt + (size_t)v * g.B;
+            for (int rr = rlo; rr <= rhi; ++rr) {
+                const float vr = ((float)rr - g.rcen) * g.rpitch;
+                const float ri = __ldg(g.rowinv + rr);
+                // z intervals (in tau) of the first / second z half and of the whole block
+                float z0l, z0h, z1l, z1h, zsl, zsh;
+                if (vr != 0.0f) {
+                    const float cc = -(vr * kappa - cz) * ri;      // z centre-plane crossing
+                    const float Az = hz * fabsf(ri);
+                    z0l = cc - Az; z0h = cc; z1l = cc; z1h = cc + Az; zsl = cc - Az; zsh = cc + Az;
+                } else {
+                    // the ray stays in the plane z = 0: it belongs to the half (block)
+                    // whose half-open z range [lo, hi) holds 0; 1/v_r = +inf, so the
+                    // first half is the lower one
+                    const float B = 1e30f;
+                    const bool lo = (cz - hz <= 0.0f) && (0.0f < cz), hi = (cz <= 0.0f) && (0.0f < cz + hz);
+                    const bool in = (cz - hz <= 0.0f) && (0.0f < cz + hz);
+                    z0l = lo ? -B : B; z0h = lo ? B : -B;
+                    z1l = hi ? -B : B; z1h = hi ? B : -B;
+                    zsl = in ? -B : B; zsh = in ? B : -B;
+                }
+                const float* row = sino + ((size_t)v * g.R + rr) * g.B;
+                const float* dl = g.dlen + (size_t)rr * g.B;
+                for (int bb = blo; bb <= bhi; ++bb) {
+                    const float ub = ((float)bb - g.ucen) * g.pitch;
+                    const float dw = ub * kappa - wc;
+                    const float4 T = __ldg(drow + bb);
+                    const float a = dw * T.x, b = dw * T.y;
+                    const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
+                    const float q = __ldg(row + bb) * __ldg(dl + bb) * scale;
+                    if (mode == 0) {
+                        const float ch = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh) -
+                                               fmaxf(fmaxf(a - Ax, b - Ay), zsl), 0.0f);
+                        acc[0] += q * ch;
+                    } else if (mode == 2) {
+                        // quadrants of the block within the slice's z slab
+                        const float zl = zsl, zh = zsh;
+                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
+                        float w[4];   // index i + 2 j: i x half, j y half (0 first)
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+#pragma unroll
+                            for (int i = 0; i < 2; ++i)
+                                w[i + 2 * j] = fmaxf(fminf(fminf(xh[i], yh[j]), zh) - fmaxf(fmaxf(xl[i], yl[j]), zl),
+                                                     0.0f);
+                        // Walsh-Hadamard over (x, y): t = 1 x, 2 y, 3 xy; + on the lower halves
+                        const float s1 = w[0] + w[1], s2 = w[2] + w[3], d1 = w[0] - w[1], d2 = w[2] - w[3];
+                        acc[0] += q * (s1 + s2);
+                        const float W[3] = {flipf(d1 + d2, T.z), flipf(s1 - s2, T.w),
+                                            flipf(flipf(d1 - d2, T.z), T.w)};
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const float ph = q * W[t];
+                            if (ph > 0.0f) acc[1 + 2 * t] += ph; else acc[2 + 2 * t] += ph;
+                        }
+                    } else if (oct) {
+                        // voxel basis: chords of the 8 voxels in physical order (index
+                        // x + 2 y + 4 z, 0 = lower half); a half crossed first is the
+                        // lower one when the direction along that axis is positive
+                        const bool px = T.z > 0.0f, py = T.w > 0.0f, pz = ri > 0.0f;
+                        const float xl[2] = {px ? a - Ax : a, px ? a : a - Ax};
+                        const float xh[2] = {px ? a : a + Ax, px ? a + Ax : a};
+                        const float yl[2] = {py ? b - Ay : b, py ? b : b - Ay};
+                        const float yh[2] = {py ? b : b + Ay, py ? b + Ay : b};
+                        const float zl[2] = {pz ? z0l : z1l, pz ? z1l : z0l};
+                        const float zh[2] = {pz ? z0h : z1h, pz ? z1h : z0h};
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
+#pragma unroll
+                                for (int k = 0; k < 2; ++k)
+                                    acc[i + 2 * j + 4 * k] += q * fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                            }
+                    } else {
+                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
+                        const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
+                        float w[8];   // index i + 2 j + 4 k
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
+#pragma unroll
+                                for (int k = 0; k < 2; ++k)
+                                    w[i + 2 * j + 4 * k] = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                            }
+                        // in-place Walsh-Hadamard transform over (x, y, z)
+#pragma unroll
+                        for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                if (!(i & h)) {
+                                    const float u0 = w[i], u1 = w[i + h];
+                                    w[i] = u0 + u1;
+                                    w[i + h] = u0 - u1;
+                                }
+                        acc[0] += q * w[0];
+#pragma unroll
+                        for (int t = 1; t < 8; ++t) {
+                            float wt = w[t];
+                            if (t & 1) wt = flipf(wt, T.z);
+                            if (t & 2) wt = flipf(wt, T.w);
+                            if (t & 4) wt = flipf(wt, ri);
+                            const float ph = q * wt;
+                            if (ph > 0.0f) acc[2 * t - 1] += ph; else acc[2 * t] += ph;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    add_work3(work, mode == 1 ? 8u * evals : (mode == 2 ? 4u * evals : evals));
+#pragma unroll
+    for (int k = 0; k < kSlots3; ++k) red[wv][k][lane] = acc[k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < kSlots3 * kItemsPerCta; t += kBackTPB) {
+        const int k = t / kItemsPerCta, l = t - k * kItemsPerCta;
+        const int it = tile * kItemsPerCta + l;
+        if (it >= S.n_items) continue;
+        if (oct) {
+            if (k >= 8) continue;
+            // voxel k = cx + 2 cy + 4 cz
+            float v = red[0][k][l];
+#pragma unroll
+            for (int w = 1; w < kViewLanes; ++w) v += red[w][k][l];
+            part[S.part_off + ((size_t)chunk * S.n_slots + k) * S.n_items + it] = v;
+        } else {
+            const int ndet = z3 ? 7 : 3;
+            int slot;
+            if (k == 0) {
+                if (!S.has_approx) continue;
+                slot = 0;
+            } else {
+                if (!det || k > 2 * ndet) continue;
+                slot = S.has_approx + (k - 1);
+            }
+            float sum = red[0][k][l];
+#pragma unroll
+            for (int w = 1; w < kViewLanes; ++w) sum += red[w][k][l];
+            part[S.part_off + ((size_t)chunk * S.n_slots + slot) * S.n_items + it] = sum;
+        }
+    }
+}
+
+cudaError_t launch_backproject3(const Geom3& g, const SegTable3& tab, int z3, const float* sino, float* part,
+                                unsigned long long* work, cudaStream_t st)
+{
+    if (tab.total_ctas == 0) return cudaSuccess;
+    count_launch();
+    k_backproject3<<<tab.total_ctas, kBackTPB, 0, st>>>(g, tab, z3, sino, part, work);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// coefficient indices
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long approx3(const Layout3& lay, int bx, int by, int bz)
+{
+    const int L = lay.L;
+    if (lay.z3) return ((long long)bz * lay.gh[L] + by) * lay.gw[L] + bx;
+    return (long long)bz * lay.nslice + (long long)by * lay.gw[L] + bx;
+}
+
+// detail t: z3: t = 1..7 (bit mask x 1, y 2, z 4); slices: t = 1 (x, "v"),
+// 2 (y, "h"), 3 (xy, "d") stored in the 2-D plane order h, v, d
+__device__ __forceinline__ long long detail3(const Layout3& lay, int l, int t, int bx, int by, int bz)
+{
+    if (lay.z3) {
+        const long long n = (long long)lay.gw[l] * lay.gh[l] * lay.gd[l];
+        return lay.coff[l] + (long long)(t - 1) * n + ((long long)bz * lay.gh[l] + by) * lay.gw[l] + bx;
+    }
+    const long long n = (long long)lay.gw[l] * lay.gh[l];
+    const int plane = (t == 2) ? 0 : (t == 1 ? 1 : 2);
+    return (long long)bz * lay.nslice + lay.coff[l] + plane * n + (long long)by * lay.gw[l] + bx;
+}
+
+__device__ __forceinline__ float sum_slot3(const Segment3& S, const float* __restrict__ part, int item, int slot)
+{
+    float s = 0.0f;
+    const float* p = part + S.part_off + (size_t)slot * S.n_items + item;
+    const size_t stride = (size_t)S.n_slots * S.n_items;
+    for (int c = 0; c < S.n_chunks; ++c) s += p[c * stride];
+    return s;
+}
+
+// the AM root in FP32 with the FP64 fallback near zero counts (as in 2-D)
+__device__ __forceinline__ double am_delta64(double b, double bp, double bm, double z0, double clamp)
+{
+    double t;
+    if (bp > 0.0) {
+        const double disc = sqrt(b * b - 4.0 * bp * bm);
+        const double u = (b >= 0.0) ? (b + disc) / (2.0 * bp) : 2.0 * bm / (b - disc);
+        t = (u > 0.0) ? -log(u) : clamp;
+    } else if (bm < 0.0) {
+        t = (b < 0.0) ? -log(bm / b) : -clamp;
+    } else {
+        t = 0.0;
+    }
+    t = fmin(fmax(t, -clamp), clamp);
+    return t / z0;
+}
+
+__device__ __forceinline__ double am_delta32(double b, float bp, float bm, double z0, double clamp)
+{
+    const float bf = (float)b;
+    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta64(b, bp, bm, z0, clamp);
+    float t;
+    if (bp > 0.0f) {
+        const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
+        const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
+        t = (u > 0.0f) ? -logf(u) : (float)clamp;
+    } else if (bm < 0.0f) {
+        t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
+    } else {
+        t = 0.0f;
+    }
+    t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
+    return (double)t / z0;
+}
+
+__global__ void k_update3(SegTable3 tab, Layout3 lay, const float* __restrict__ part, const double* __restrict__ bvec,
+                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= tab.total_items) return;
+    int si = 0;
+    while (si + 1 < tab.n && gid >= tab.s[si + 1].item_begin) ++si;
+    const Segment3& S = tab.s[si];
+    const int item = gid - S.item_begin;
+    int bx, by, bz;
+    decode3(S, item, bx, by, bz);
+    const double z0 = *z0p;
+    if (S.octet) {
+        for (int k = 0; k < 8; ++k) {
+            const long long z = ((long long)(2 * bz + (k >> 2)) * lay.ny + 2 * by + ((k >> 1) & 1)) * lay.nx +
+                                2 * bx + (k & 1);
+            beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, k), 0.0f, z0, clamp);
+        }
+        return;
+    }
+    int slot = 0;
+    if (S.has_approx) {
+        const long long z = approx3(lay, bx, by, bz);
+        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, 0), 0.0f, z0, clamp);
+        slot = 1;
+    }
+    if (S.has_details) {
+        const int ndet = lay.z3 ? 7 : 3;
+        for (int t = 1; t <= ndet; ++t) {
+            const long long z = detail3(lay, S.level, t, bx, by, bz);
+            beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, slot + 2 * (t - 1)),
+                                  sum_slot3(S, part, item, slot + 2 * (t - 1) + 1), z0, clamp);
+        }
+    }
+}
+
+cudaError_t launch_update3(const SegTable3& tab, const Layout3& lay, const float* part, const double* b,
+                           const double* z0, double clamp, double* beta, cudaStream_t st)
+{
+    if (tab.total_items == 0) return cudaSuccess;
+    count_launch();
+    k_update3<<<nb(tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    return cudaGetLastError();
+}
+
+// voxel-basis back-projection (octet segment) into a volume
+__global__ void k_reduce_voxels3(SegTable3 tab, Layout3 lay, const float* __restrict__ part, double* __restrict__ out,
+                                 float* __restrict__ outf)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = (long long)lay.nx * lay.ny * lay.nz;
+    if (p >= N) return;
+    const Segment3& S = tab.s[0];
+    const int ix = (int)(p % lay.nx);
+    const long long r = p / lay.nx;
+    const int iy = (int)(r % lay.ny), iz = (int)(r / lay.ny);
+    const int item = ((iz >> 1) * S.gh + (iy >> 1)) * S.gw + (ix >> 1);
+    const float v = sum_slot3(S, part, item, (ix & 1) + 2 * (iy & 1) + 4 * (iz & 1));
+    if (out) out[p] = (double)v;
+    if (outf) outf[p] = v;
+}
+
+cudaError_t launch_reduce_voxels3(const SegTable3& tab, const Layout3& lay, const float* part, double* out,
+                                  float* outf, cudaStream_t st)
+{
+    const long long N = (long long)lay.nx * lay.ny * lay.nz;
+    count_launch();
+    k_reduce_voxels3<<<nb(N, 256), 256, 0, st>>>(tab, lay, part, out, outf);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a5: Z0 row sums over the tree (ancestor accumulators as in 2-D; octants for
+// the 3-D Haar, quadrants of the ray's current slice for the slices mode)
+// ---------------------------------------------------------------------------
+constexpr int kMaxL3 = 5;
+
+__global__ void __launch_bounds__(kFwdTPB)
+k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict__ part)
+{
+    const int v = blockIdx.z, r = blockIdx.y;
+    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    double rowsum = 0.0;
+    if (b < g.B) {
+        Ray3 ray;
+        if (make_ray3(g, v, r, b, ray)) {
+            const int L = lay.L, z3 = lay.z3;
+            float acc[kMaxL3][8];
+            long long cur[kMaxL3];
+#pragma unroll
+            for (int l = 0; l < kMaxL3; ++l) {
+                cur[l] = -1;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[l][k] = 0.0f;
+            }
+            float total = 0.0f, rs = 0.0f;
+            auto flush = [&](int li) {
+                if (cur[li] >= 0) {
+                    float w[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) w[k] = acc[li][k];
+#pragma unroll
+                    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (!(i & h)) {
+                                const float u0 = w[i], u1 = w[i + h];
+                                w[i] = u0 + u1;
+                                w[i + h] = u0 - u1;
+                            }
+                    float sa = 0.0f;
+                    const int nt = z3 ? 8 : 4;
+                    for (int t = 1; t < nt; ++t) sa += fabsf(w[t]);
+                    rs += (float)basis_scale(z3, li + 1) * sa;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[li][k] = 0.0f;
+            };
+            walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int lam, int bx0, int by0, int bz0, float c) {
+                total += c;
+#pragma unroll
+                for (int li = 0; li < kMaxL3; ++li) {
+                    const int l = li + 1;
+                    if (l > lam && l <= L) {
+                        const long long id = z3 ? (((long long)(iz >> l) * 1024 + (iy >> l)) * 1024 + (ix >> l))
+                                                : (((long long)iz * 1024 + (iy >> l)) * 1024 + (ix >> l));
+                        if (id != cur[li]) {
+                            flush(li);
+                            cur[li] = id;
+                        }
+                        const int q = ((bx0 >> li) & 1) + 2 * ((by0 >> li) & 1) + (z3 ? 4 * ((bz0 >> li) & 1) : 0);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[li][k] += (q == k) ? c : 0.0f;
+                    }
+                }
+            });
+#pragma unroll
+            for (int li = 0; li < kMaxL3; ++li) flush(li);
+            rowsum = (double)rs + (double)total * basis_scale(z3, L);
+        }
+    }
+    rowsum = wmax(rowsum);
+    if ((threadIdx.x & 31) == 0)
+        part[(((size_t)v * g.R + r) * gridDim.x + blockIdx.x) * (kFwdTPB / 32) + (threadIdx.x >> 5)] = rowsum;
+}
+
+cudaError_t launch_z03(const Geom3& g, const Layout3& lay, const uint8_t* leaf, double* part, cudaStream_t st)
+{
+    if (lay.L > kMaxL3) return cudaErrorInvalidValue;
+    count_launch();
+    dim3 grid(nb(g.B, kFwdTPB), g.R, g.V);
+    k_z03<<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a1 synthesis, leaf map, a7 expansion, block lists, full analysis
+// ---------------------------------------------------------------------------
+__global__ void k_synth3(Layout3 lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
+                         float* __restrict__ mu)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = (long long)lay.nx * lay.ny * lay.nz;
+    if (p >= N) return;
+    const int ix = (int)(p % lay.nx);
+    const long long rr = p / lay.nx;
+    const int iy = (int)(rr % lay.ny), iz = (int)(rr / lay.ny);
+    const int L = lay.L;
+    if (L == 0) {
+        mu[p] = (float)beta[p];
+        return;
+    }
+    const int lam = leaf ? (lay.z3 ? (int)leaf[p] : (int)leaf[(long long)iy * lay.nx + ix]) : 0;
+    double v = beta[approx3(lay, ix >> L, iy >> L, lay.z3 ? iz >> L : iz)] * basis_scale(lay.z3, L);
+    for (int l = L; l > lam; --l) {
+        const int bx = ix >> l, by = iy >> l, bz = lay.z3 ? iz >> l : iz;
+        const int cx = (ix >> (l - 1)) & 1, cy = (iy >> (l - 1)) & 1, cz = lay.z3 ? (iz >> (l - 1)) & 1 : 0;
+        const int nt = lay.z3 ? 7 : 3;
+        double s = 0.0;
+        for (int t = 1; t <= nt; ++t) {
+            const int par = ((t & 1) & cx) ^ (((t >> 1) & 1) & cy) ^ (((t >> 2) & 1) & cz);
+            const double bz_ = beta[detail3(lay, l, t, bx, by, bz)];
+            s += par ? -bz_ : bz_;
+        }
+        v += s * basis_scale(lay.z3, l);
+    }
+    mu[p] = (float)v;
+}
+
+cudaError_t launch_synth3(const Layout3& lay, const uint8_t* leaf, const double* beta, float* mu, cudaStream_t st)
+{
+    const long long N = (long long)lay.nx * lay.ny * lay.nz;
+    count_launch();
+    k_synth3<<<nb(N, 256), 256, 0, st>>>(lay, leaf, beta, mu);
+    return cudaGetLastError();
+}
+
+__global__ void k_leafmap3(Layout3 lay, const uint8_t* __restrict__ mask, uint8_t* __restrict__ leaf)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = lay.z3 ? (long long)lay.nx * lay.ny * lay.nz : lay.nslice;
+    if (p >= n) return;
+    const int ix = (int)(p % lay.nx);
+    const long long rr = p / lay.nx;
+    const int iy = (int)(rr % lay.ny), iz = lay.z3 ? (int)(rr / lay.ny) : 0;
+    int lam = lay.L;
+    for (int l = lay.L; l >= 1; --l) {
+        const long long m = lay.moff[l] + (((long long)(iz >> l)) * lay.gh[l] + (iy >> l)) * lay.gw[l] + (ix >> l);
+        if (mask[m]) lam = l - 1;
+        else break;
+    }
+    leaf[p] = (uint8_t)lam;
+}
+
+cudaError_t launch_leafmap3(const Layout3& lay, const uint8_t* mask, uint8_t* leaf, cudaStream_t st)
+{
+    const long long n = lay.z3 ? (long long)lay.nx * lay.ny * lay.nz : lay.nslice;
+    count_launch();
+    k_leafmap3<<<nb(n, 256), 256, 0, st>>>(lay, mask, leaf);
+    return cudaGetLastError();
+}
+
+// S = sum over z of mu (slices mode), fixed order
+__global__ void k_zsum(Layout3 lay, const float* __restrict__ mu, float* __restrict__ s2d)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= lay.nslice) return;
+    float s = 0.0f;
+    for (int z = 0; z < lay.nz; ++z) s += mu[(long long)z * lay.nslice + p];
+    s2d[p] = s;
+}
+
+__global__ void k_max3(const float* __restrict__ S, long long n, double* __restrict__ part)
+{
+    double m = -INFINITY;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, (double)S[i]);
+    __shared__ double sh[32];
+    m = wmax(m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+        part[blockIdx.x] = r;
+    }
+}
+
+__global__ void k_thr3(const double* __restrict__ part, int n, double tau, double* __restrict__ thr)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = -INFINITY;
+        for (int i = 0; i < n; ++i) m = fmax(m, part[i]);
+        *thr = tau * m;
+    }
+}
+
+__global__ void k_mark3(Layout3 lay, const float* __restrict__ S, const double* __restrict__ thr, int all,
+                        const uint8_t* __restrict__ leaf_old, uint8_t* __restrict__ mask_new)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = lay.z3 ? (long long)lay.nx * lay.ny * lay.nz : lay.nslice;
+    if (p >= n) return;
+    const int lam = leaf_old[p];
+    if (lam < 1) return;
+    if (!all && !((double)S[p] > *thr)) return;
+    const int ix = (int)(p % lay.nx);
+    const long long rr = p / lay.nx;
+    const int iy = (int)(rr % lay.ny), iz = lay.z3 ? (int)(rr / lay.ny) : 0;
+    mask_new[lay.moff[lam] + (((long long)(iz >> lam)) * lay.gh[lam] + (iy >> lam)) * lay.gw[lam] + (ix >> lam)] = 1;
+}
+
+cudaError_t launch_expand3(const Layout3& lay, const float* mu, double tau, const uint8_t* leaf_old,
+                           uint8_t* mask_new, float* s2d, double* scratch, cudaStream_t st)
+{
+    const float* S = mu;
+    long long n = (long long)lay.nx * lay.ny * lay.nz;
+    if (!lay.z3) {
+        count_launch();
+        k_zsum<<<nb(lay.nslice, 256), 256, 0, st>>>(lay, mu, s2d);
+        S = s2d;
+        n = lay.nslice;
+    }
+    const int parts = 256;
+    count_launch();
+    k_max3<<<parts, 256, 0, st>>>(S, n, scratch);
+    count_launch();
+    k_thr3<<<1, 32, 0, st>>>(scratch, parts, tau, scratch + parts);
+    count_launch();
+    k_mark3<<<nb(n, 256), 256, 0, st>>>(lay, S, scratch + parts, tau < 0.0 ? 1 : 0, leaf_old, mask_new);
+    return cudaGetLastError();
+}
+
+// Block lists in Morton order: list 0 level-L blocks not expanded, list 1
+// level-L expanded, list 1 + k expanded blocks of level L - k.  Entries
+// (bx | by << 10 | bz << 20); in the slices mode the lists hold 2-D blocks
+// (bz = 0) and the driver repeats them over the slices.
+__device__ __forceinline__ uint32_t part1by2(uint32_t x, int sh)
+{
+    uint32_t r = 0;
+    for (int i = 0; i < 10; ++i) r |= ((x >> (3 * i + sh)) & 1u) << i;
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_compact3(Layout3 lay, const uint8_t* __restrict__ mask,
+                                                   uint32_t* __restrict__ lists, long long stride,
+                                                   int* __restrict__ counts)
+{
+    const int list = blockIdx.x;
+    const int level = list <= 1 ? lay.L : lay.L - (list - 1);
+    const int want = list == 0 ? 0 : 1;
+    const int gw = lay.gw[level], gh = lay.gh[level], gd = lay.z3 ? lay.gd[level] : 1;
+    int side = 1;
+    while (side < gw || side < gh || side < gd) side <<= 1;
+    const long long ncode = lay.z3 ? (long long)side * side * side : (long long)side * side;
+    uint32_t* out = lists + stride * list;
+    __shared__ int wc[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long m0 = 0; m0 < ncode; m0 += blockDim.x) {
+        const long long m = m0 + threadIdx.x;
+        bool keep = false;
+        int bx = 0, by = 0, bz = 0;
+        if (m < ncode) {
+            if (lay.z3) {
+                bx = (int)part1by2((uint32_t)m, 0);
+                by = (int)part1by2((uint32_t)m, 1);
+                bz = (int)part1by2((uint32_t)m, 2);
+            } else {
+                uint32_t x = (uint32_t)m, y = (uint32_t)(m >> 1);
+                uint32_t rx = 0, ry = 0;
+                for (int i = 0; i < 16; ++i) {
+                    rx |= ((x >> (2 * i)) & 1u) << i;
+                    ry |= ((y >> (2 * i)) & 1u) << i;
+                }
+                bx = (int)rx;
+                by = (int)ry;
+            }
+            if (bx < gw && by < gh && bz < gd) {
+                const int e = mask[lay.moff[level] + ((long long)bz * gh + by) * gw + bx] ? 1 : 0;
+                keep = (e == want);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wc[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < wid) off += wc[w];
+            tot += wc[w];
+        }
+        if (keep)
+            out[base + off + __popc(bal & ((1u << lane) - 1u))] =
+                (uint32_t)bx | ((uint32_t)by << 10) | ((uint32_t)bz << 20);
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[list] = base;
+}
+
+cudaError_t launch_compact3(const Layout3& lay, const uint8_t* mask, uint32_t* lists, long long stride, int* counts,
+                            cudaStream_t st)
+{
+    count_launch();
+    k_compact3<<<lay.L + 1, 1024, 0, st>>>(lay, mask, lists, stride, counts);
+    return cudaGetLastError();
+}
+
+// analysis of one level: z3 from the (nz>>(l-1), ...) approximation volume,
+// slices from per-slice (ny>>(l-1), nx>>(l-1)) images stacked in z
+__global__ void k_haar3_level(Layout3 lay, int l, const double* __restrict__ a, double* __restrict__ a_next,
+                              double* __restrict__ coef)
+{
+    const int gw = lay.gw[l], gh = lay.gh[l], gd = lay.z3 ? lay.gd[l] : lay.nz;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)gw * gh * gd) return;
+    const int bx = (int)(i % gw);
+    const long long r = i / gw;
+    const int by = (int)(r % gh), bz = (int)(r / gh);
+    const int w = 2 * gw, h = 2 * gh;
+    if (lay.z3) {
+        double c[8];
+        for (int k = 0; k < 8; ++k)
+            c[k] = a[(((long long)(2 * bz + (k >> 2))) * h + 2 * by + ((k >> 1) & 1)) * w + 2 * bx + (k & 1)];
+        const double s = 1.0 / (2.0 * sqrt(2.0));
+        const long long n = (long long)gw * gh * gd;
+        for (int t = 0; t < 8; ++t) {
+            double acc = 0.0;
+            for (int k = 0; k < 8; ++k) acc += (__popc(t & k) & 1) ? -c[k] : c[k];
+            if (t == 0) a_next[i] = acc * s;
+            else coef[lay.coff[l] + (long long)(t - 1) * n + i] = acc * s;
+        }
+    } else {
+        const long long base = (long long)bz * h * w;
+        const double ll = a[base + (2 * by) * w + 2 * bx], lh = a[base + (2 * by) * w + 2 * bx + 1];
+        const double hl = a[base + (2 * by + 1) * w + 2 * bx], hh = a[base + (2 * by + 1) * w + 2 * bx + 1];
+        const long long n = (long long)gw * gh;
+        const long long j = (long long)by * gw + bx;
+        a_next[(long long)bz * n + j] = 0.5 * (ll + lh + hl + hh);
+        double* cs = coef + (long long)bz * lay.nslice + lay.coff[l];
+        cs[j] = 0.5 * (ll + lh - hl - hh);
+        cs[n + j] = 0.5 * (ll - lh + hl - hh);
+        cs[2 * n + j] = 0.5 * (ll - lh - hl + hh);
+    }
+}
+
+// copy the level-L approximations into the coefficient vector
+__global__ void k_haar3_approx(Layout3 lay, const double* __restrict__ a, double* __restrict__ coef)
+{
+    const int L = lay.L;
+    const long long nA = (long long)lay.gw[L] * lay.gh[L];
+    const long long n = lay.z3 ? nA * lay.gd[L] : nA * lay.nz;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (lay.z3) coef[i] = a[i];
+    else coef[(i / nA) * lay.nslice + (i % nA)] = a[i];
+}
+
+cudaError_t launch_haar3(const Layout3& lay, const double* img, double* coef, double* ta, double* tb,
+                         cudaStream_t st)
+{
+    const long long N = (long long)lay.nx * lay.ny * lay.nz;
+    if (lay.L == 0) return cudaMemcpyAsync(coef, img, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    const double* a = img;
+    double* bufs[2] = {ta, tb};
+    for (int l = 1; l <= lay.L; ++l) {
+        double* an = bufs[l & 1];
+        const long long n = (long long)lay.gw[l] * lay.gh[l] * (lay.z3 ? lay.gd[l] : lay.nz);
+        count_launch();
+        k_haar3_level<<<nb(n, 256), 256, 0, st>>>(lay, l, a, an, coef);
+        a = an;
+    }
+    const long long nA = (long long)lay.gw[lay.L] * lay.gh[lay.L] * (lay.z3 ? lay.gd[lay.L] : lay.nz);
+    count_launch();
+    k_haar3_approx<<<nb(nA, 256), 256, 0, st>>>(lay, a, coef);
+    return cudaGetLastError();
+}
+
+}  // namespace wam

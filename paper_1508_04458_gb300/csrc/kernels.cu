@@ -249,7 +249,7 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
     const bool quad = S.quad != 0;
     const bool four = det || quad;       // chords through the four children
     // accumulators: Haar split (A, h+, h-, v+, v-, d+, d-); a pixel quad keeps
-    // the Hadamard sums (A, h, v, d) of its four pixels in (A, h+, v+, d+)
+    // its four pixel sums in the first four
     T aA = 0, hP = 0, hM = 0, vP = 0, vM = 0, dP = 0, dM = 0;
     unsigned evals = 0;
     if (valid) {
@@ -315,7 +315,22 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
                 const T a = delta * dd.x, b = delta * dd.y;
                 const T Ax = hx * fabs(dd.z), Ay = hy * fabs(dd.w);
                 const T q = __ldg(row + bb);
-                if (four) {
+                if (quad) {
+                    // pixel basis: the four pixels' chords in physical order (sums of
+                    // non-negative terms); the half crossed first is the lower one
+                    // when the direction along that axis is positive
+                    T cFF, cFS, cSF, cSS;
+                    child_chords_ab(a, b, Ax, Ay, cFF, cFS, cSF, cSS);
+                    const bool px = dd.z > T(0), py = dd.w > T(0);
+                    const T xlyl = px ? (py ? cFF : cFS) : (py ? cSF : cSS);
+                    const T xhyl = px ? (py ? cSF : cSS) : (py ? cFF : cFS);
+                    const T xlyh = px ? (py ? cFS : cFF) : (py ? cSS : cSF);
+                    const T xhyh = px ? (py ? cSS : cSF) : (py ? cFS : cFF);
+                    aA += q * xlyl;
+                    hP += q * xhyl;
+                    hM += q * xlyh;
+                    vP += q * xhyh;
+                } else if (four) {
                     T cFF, cFS, cSF, cSS;
                     child_chords_ab(a, b, Ax, Ay, cFF, cFS, cSF, cSS);
                     const T qs = q * scale;
@@ -326,15 +341,9 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
                     const T ph = qs * flip(yF - yS, dd.w);
                     const T pv = qs * flip(xF - xS, dd.z);
                     const T pd = qs * flip2((cFF + cSS) - (cFS + cSF), dd.z, dd.w);
-                    if (quad) {
-                        hP += ph;
-                        vP += pv;
-                        dP += pd;
-                    } else {
-                        if (ph > T(0)) hP += ph; else hM += ph;
-                        if (pv > T(0)) vP += pv; else vM += pv;
-                        if (pd > T(0)) dP += pd; else dM += pd;
-                    }
+                    if (ph > T(0)) hP += ph; else hM += ph;
+                    if (pv > T(0)) vP += pv; else vM += pv;
+                    if (pd > T(0)) dP += pd; else dM += pd;
                 } else {
                     aA += q * scale * block_chord_ab(a, b, Ax, Ay);
                 }
@@ -354,21 +363,12 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
         const int it = tile * kItemsPerCta + l;
         if (it < S.n_items) {
             if (quad) {
-                // inverse Hadamard of (A, h, v, d): pixel k = (ylo,xlo), (ylo,xhi),
-                // (yhi,xlo), (yhi,xhi); summed over the 8 lanes first
+                // pixel k = (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) in slots 0..3
                 if (k < 4) {
-                    T A = 0, h = 0, vv = 0, d = 0;
+                    T sumk = red[0][k][l];
 #pragma unroll
-                    for (int w = 0; w < kViewLanes; ++w) {
-                        A += red[w][0][l];
-                        h += red[w][1][l];
-                        vv += red[w][3][l];
-                        d += red[w][5][l];
-                    }
-                    const T sh = (k & 2) ? -h : h, sv = (k & 1) ? -vv : vv;
-                    const T sd = ((k == 1) || (k == 2)) ? -d : d;
-                    part[S.part_off + ((size_t)chunk * S.n_slots + k) * S.n_items + it] =
-                        T(0.25) * (A + sh + sv + sd);
+                    for (int w = 1; w < kViewLanes; ++w) sumk += red[w][k][l];
+                    part[S.part_off + ((size_t)chunk * S.n_slots + k) * S.n_items + it] = sumk;
                 }
             } else {
                 // slot k of the segment: 0 = approximation when present, then h+ .. d-

@@ -2,6 +2,7 @@
 // the Results section's tree growth, or plain AM) and the step-level calls.
 // No exception crosses the boundary; every call returns a wam_status.
 #include "../../include/wam.h"
+#include "cone3d.cuh"
 #include "wam_internal.cuh"
 #include "wam_kernels.h"
 
@@ -25,6 +26,7 @@ enum BufId {
     B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
+    B_DIR3, B_ROWINV, B_DLEN, B_S2D,
     B_NBUF
 };
 
@@ -412,6 +414,24 @@ wam_status compute_z0(wam_ctx* c, const Geom<T>& g, const Layout& lay, const uin
 wam_status check_geometry(const wam_geometry* g, std::string* why)
 {
     if (!g) { *why = "geometry is NULL"; return WAM_ERR_ARG; }
+    if (g->kind == WAM_CONE3D_FLAT_CIRCULAR) {
+        if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->n_views <= 0 || g->n_bins <= 0 || g->n_rows <= 0) {
+            *why = "sizes must be positive"; return WAM_ERR_ARG;
+        }
+        if (!(g->vx > 0) || !(g->vy > 0) || !(g->vz > 0) || !(g->bin_pitch > 0) || !(g->row_pitch > 0)) {
+            *why = "voxel sizes and pitches must be > 0"; return WAM_ERR_ARG;
+        }
+        if (g->nx > 2046 || g->ny > 2046 || g->nz > 1022) { *why = "volume too large"; return WAM_ERR_ARG; }
+        if ((long long)g->nx * g->ny * g->nz > (1LL << 31) - 1 ||
+            (long long)g->n_views * g->n_rows * g->n_bins > (1LL << 31) - 1) {
+            *why = "problem too large for 32-bit indices"; return WAM_ERR_ARG;
+        }
+        const double r = 0.5 * std::hypot(g->nx * g->vx, g->ny * g->vy);
+        if (!(g->sod > r) || !(g->sdd - g->sod > r)) {
+            *why = "cone beam: source and detector must lie outside the volume's circumradius"; return WAM_ERR_ARG;
+        }
+        return WAM_OK;
+    }
     if (g->kind != WAM_PARALLEL2D && g->kind != WAM_FAN2D_FLAT) { *why = "unsupported geometry kind"; return WAM_ERR_ARG; }
     if (g->nx <= 0 || g->ny <= 0 || g->n_views <= 0 || g->n_bins <= 0) { *why = "sizes must be positive"; return WAM_ERR_ARG; }
     if (g->nz > 1 || g->n_rows > 1) { *why = "2-D geometry expected (nz = n_rows = 1)"; return WAM_ERR_ARG; }
@@ -591,6 +611,7 @@ template <typename T>
 wam_status project_impl(wam_ctx* c, const T* mu, T* p, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
     Geom<T> g;
     WST(make_geom<T>(c, &g));
@@ -603,6 +624,7 @@ template <typename T>
 wam_status backproject_impl(wam_ctx* c, const T* s, T* out, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!s || !out) return fail(c, WAM_ERR_ARG, "null pointer");
     try {
         Geom<T> g;
@@ -636,6 +658,7 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
                                double* cost, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
     if (!mu || !qhat || !cost) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
@@ -656,6 +679,315 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
     return WAM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 3-D circular cone beam
+// ---------------------------------------------------------------------------
+
+// Tables of the cone geometry, computed in FP64 on the host once:
+// in-plane direction D_xy = -SDD e + u_b u per (view, bin) as
+// (s/Dx, -c/Dy, 1/Dx, 1/Dy); 1/v_r per row; |D| per (row, bin).
+wam_status make_geom3(wam_ctx* c, Geom3* g)
+{
+    const wam_geometry& w = c->g;
+    g->nx = w.nx; g->ny = w.ny; g->nz = w.nz; g->V = w.n_views; g->R = w.n_rows; g->B = w.n_bins;
+    g->vx = (float)w.vx; g->vy = (float)w.vy; g->vz = (float)w.vz;
+    g->X0 = (float)(-0.5 * w.nx * w.vx); g->Y0 = (float)(-0.5 * w.ny * w.vy); g->Z0 = (float)(-0.5 * w.nz * w.vz);
+    g->ivx = (float)(1.0 / w.vx); g->ivy = (float)(1.0 / w.vy); g->ivz = (float)(1.0 / w.vz);
+    g->pitch = (float)w.bin_pitch; g->ucen = (float)(0.5 * (w.n_bins - 1));
+    g->rpitch = (float)w.row_pitch; g->rcen = (float)(0.5 * (w.n_rows - 1));
+    g->sod = (float)w.sod; g->sdd = (float)w.sdd;
+    g->cs = static_cast<const float*>(c->buf[B_CS32].p);
+    const size_t nvb = (size_t)w.n_views * w.n_bins, nrb = (size_t)w.n_rows * w.n_bins;
+    if (!c->buf[B_DIR3].p || c->buf[B_DIR3].bytes < nvb * 16) {
+        auto rcp = [](double d) {
+            double a = std::fabs(d);
+            a = a < 1e-30 ? 1e-30 : a;
+            return std::signbit(d) ? -1.0 / a : 1.0 / a;
+        };
+        std::vector<float> dir(4 * nvb), rinv(w.n_rows), dl(nrb);
+        for (int k = 0; k < w.n_views; ++k) {
+            const double th = w.angle0 + k * (w.angle_span / w.n_views);
+            const double cs = std::cos(th), sn = std::sin(th);
+            for (int b = 0; b < w.n_bins; ++b) {
+                const double ub = (b - 0.5 * (w.n_bins - 1)) * w.bin_pitch;
+                const double ix = rcp(-w.sdd * cs - ub * sn), iy = rcp(-w.sdd * sn + ub * cs);
+                float* e = &dir[4 * ((size_t)k * w.n_bins + b)];
+                e[0] = (float)(sn * ix); e[1] = (float)(-cs * iy); e[2] = (float)ix; e[3] = (float)iy;
+            }
+        }
+        for (int r = 0; r < w.n_rows; ++r) {
+            const double vr = (r - 0.5 * (w.n_rows - 1)) * w.row_pitch;
+            rinv[r] = (float)rcp(vr);
+            for (int b = 0; b < w.n_bins; ++b) {
+                const double ub = (b - 0.5 * (w.n_bins - 1)) * w.bin_pitch;
+                dl[(size_t)r * w.n_bins + b] = (float)std::sqrt(w.sdd * w.sdd + ub * ub + vr * vr);
+            }
+        }
+        float *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
+        WST(ensure_t(c, B_DIR3, 4 * nvb, &d1));
+        WST(ensure_t(c, B_ROWINV, (size_t)w.n_rows, &d2));
+        WST(ensure_t(c, B_DLEN, nrb, &d3));
+        WCK(c, cudaMemcpy(d1, dir.data(), dir.size() * 4, cudaMemcpyHostToDevice));
+        WCK(c, cudaMemcpy(d2, rinv.data(), rinv.size() * 4, cudaMemcpyHostToDevice));
+        WCK(c, cudaMemcpy(d3, dl.data(), dl.size() * 4, cudaMemcpyHostToDevice));
+    }
+    g->dirt = static_cast<const float4*>(c->buf[B_DIR3].p);
+    g->rowinv = static_cast<const float*>(c->buf[B_ROWINV].p);
+    g->dlen = static_cast<const float*>(c->buf[B_DLEN].p);
+    return WAM_OK;
+}
+
+wam_status make_layout3(wam_ctx* c, int L, int z3, Layout3* lay)
+{
+    const wam_geometry& w = c->g;
+    if (L < 0 || L > 5) return fail(c, WAM_ERR_ARG, "cone beam: levels must be in 0..5");
+    if (w.nx % (1 << L) || w.ny % (1 << L) || (z3 && w.nz % (1 << L)))
+        return fail(c, WAM_ERR_ARG, "volume sides must be divisible by 2^levels");
+    if (w.nx % 2 || w.ny % 2 || w.nz % 2) return fail(c, WAM_ERR_ARG, "cone beam: nx, ny, nz must be even");
+    std::memset(lay, 0, sizeof(*lay));
+    lay->L = L; lay->nx = w.nx; lay->ny = w.ny; lay->nz = w.nz; lay->z3 = z3;
+    lay->nslice = (long long)w.nx * w.ny;
+    for (int l = 0; l <= L; ++l) {
+        lay->gw[l] = w.nx >> l; lay->gh[l] = w.ny >> l; lay->gd[l] = z3 ? (w.nz >> l) : w.nz;
+    }
+    const int nd = z3 ? 7 : 3;
+    long long off = (long long)lay->gw[L] * lay->gh[L] * (z3 ? lay->gd[L] : 1);
+    long long moff = 0;
+    for (int l = L; l >= 1; --l) {
+        const long long nbk = (long long)lay->gw[l] * lay->gh[l] * (z3 ? lay->gd[l] : 1);
+        lay->coff[l] = off;
+        off += nd * nbk;
+        lay->moff[l] = moff;
+        moff += nbk;
+    }
+    lay->mask_bytes = moff;
+    return WAM_OK;
+}
+
+struct ListInfo3 {
+    int level, has_approx, has_details, octet, n;
+    const uint32_t* items;
+    int rep, gw, gh;
+};
+
+wam_status plan3(wam_ctx* c, int z3, const std::vector<ListInfo3>& lists, SegTable3* tab, float** part_out)
+{
+    const wam_geometry& w = c->g;
+    std::memset(tab, 0, sizeof(*tab));
+    const double mag = 1.3 * w.sdd / w.sod;
+    std::vector<double> cost(lists.size());
+    double total = 0.0;
+    for (size_t i = 0; i < lists.size(); ++i) {
+        const ListInfo3& li = lists[i];
+        const double sxy = (double)(1 << li.level) * std::hypot(w.vx, w.vy);
+        const double sz = (li.octet ? 2.0 : (z3 ? (double)(1 << li.level) : 1.0)) * w.vz;
+        const double rays = (sxy * mag / w.bin_pitch + 1.0) * (sz * mag / w.row_pitch + 1.0);
+        cost[i] = rays * ((li.has_details || li.octet) ? 4.0 : 1.0);
+        total += (double)li.n * w.n_views * cost[i];
+    }
+    const double per_cta = std::max(total / ((double)c->num_sms * 8.0), 1.0);
+    const int max_chunks = std::max(1, w.n_views / kViewLanes);
+    int cta = 0, items = 0;
+    long long part = 0;
+    const int nd = z3 ? 7 : 3;
+    for (size_t i = 0; i < lists.size(); ++i) {
+        const ListInfo3& li = lists[i];
+        if (li.n == 0) continue;
+        Segment3& s = tab->s[tab->n++];
+        s.level = li.level; s.has_approx = li.has_approx; s.has_details = li.has_details; s.octet = li.octet;
+        s.n_items = li.n; s.items = li.items; s.rep = li.rep; s.gw = li.gw; s.gh = li.gh;
+        int chunks = (int)std::ceil((double)kItemsPerCta * w.n_views * cost[i] / per_cta);
+        chunks = std::max(1, std::min(chunks, max_chunks));
+        s.vpc = (w.n_views + chunks - 1) / chunks;
+        s.n_chunks = (w.n_views + s.vpc - 1) / s.vpc;
+        s.tiles = (li.n + kItemsPerCta - 1) / kItemsPerCta;
+        s.cta_begin = cta; s.item_begin = items;
+        s.n_slots = li.octet ? 8 : li.has_approx + 2 * nd * li.has_details;
+        s.part_off = part;
+        cta += s.tiles * s.n_chunks;
+        items += li.n;
+        part += (long long)s.n_slots * s.n_chunks * li.n;
+    }
+    tab->total_ctas = cta;
+    tab->total_items = items;
+    return ensure_t(c, B_PART, (size_t)std::max<long long>(part, 1), part_out);
+}
+
+wam_status plan_voxels3(wam_ctx* c, int z3, SegTable3* tab, float** part)
+{
+    const wam_geometry& w = c->g;
+    std::vector<ListInfo3> li = {{1, 0, 0, 1, (w.nx / 2) * (w.ny / 2) * (w.nz / 2), nullptr, 0, w.nx / 2, w.ny / 2}};
+    return plan3(c, z3, li, tab, part);
+}
+
+wam_status plan_tree3(wam_ctx* c, const Layout3& lay, const uint8_t* mask, uint8_t* leaf, SegTable3* tab,
+                      float** part, long long* leaves, cudaStream_t st)
+{
+    PROF(WAM_K_TREE);
+    WCK(c, launch_leafmap3(lay, mask, leaf, st));
+    const int L = lay.L;
+    const long long stride = (long long)lay.gw[1] * lay.gh[1] * (lay.z3 ? lay.gd[1] : 1);
+    uint32_t* lists = nullptr;
+    int* counts = nullptr;
+    WST(ensure_t(c, B_LISTS, (size_t)stride * (L + 1), &lists));
+    WST(ensure_t(c, B_COUNTS, (size_t)(L + 1), &counts));
+    WCK(c, launch_compact3(lay, mask, lists, stride, counts, st));
+    std::vector<int> h(L + 1);
+    WCK(c, cudaMemcpyAsync(h.data(), counts, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
+    WCK(c, cudaStreamSynchronize(st));
+    const int rep = lay.z3 ? 0 : 1;
+    const int nzr = lay.z3 ? 1 : lay.nz;
+    const int nd = lay.z3 ? 7 : 3;
+    long long lv = (long long)lay.gw[L] * lay.gh[L] * (lay.z3 ? lay.gd[L] : 1);
+    for (int k = 1; k <= L; ++k) lv += (long long)nd * h[k];
+    *leaves = lv * nzr;
+    std::vector<ListInfo3> li;
+    li.push_back({L, 1, 0, 0, h[0] * nzr, lists, rep ? h[0] : 0, lay.gw[L], lay.gh[L]});
+    li.push_back({L, 1, 1, 0, h[1] * nzr, lists + stride, rep ? h[1] : 0, lay.gw[L], lay.gh[L]});
+    for (int k = 1; k < L; ++k)
+        li.push_back({L - k, 0, 1, 0, h[k + 1] * nzr, lists + stride * (k + 1), rep ? h[k + 1] : 0, lay.gw[L - k],
+                      lay.gh[L - k]});
+    return plan3(c, lay.z3, li, tab, part);
+}
+
+wam_status compute_z03(wam_ctx* c, const Geom3& g, const Layout3& lay, const uint8_t* leaf, double* z0,
+                       cudaStream_t st)
+{
+    const int np = forward3_parts(g);
+    double* part = nullptr;
+    WST(ensure_t(c, B_COSTPART, (size_t)np, &part));
+    WCK(c, launch_z03(g, lay, leaf, part, st));
+    WCK(c, launch_max_final(part, np, z0, st));
+    return WAM_OK;
+}
+
+wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist,
+                             unsigned char* mask_out, int on_device, cudaStream_t st)
+{
+    if (sc->precision != 32) return fail(c, WAM_ERR_ARG, "cone beam: precision 32 only");
+    const int L = sc->full_am ? 0 : sc->levels;
+    int z3 = 1;
+    if (!sc->full_am && L > 0) {
+        if (sc->dims == 3) z3 = 1;
+        else if (sc->dims == 2 && sc->zsum_criterion) z3 = 0;
+        else return fail(c, WAM_ERR_ARG, "cone beam: dims 3, or dims 2 with zsum_criterion = 1");
+    }
+    Layout3 lay;
+    WST(make_layout3(c, L, z3, &lay));
+    Geom3 g;
+    WST(make_geom3(c, &g));
+    const long long N = c->N, M = c->M;
+    const int J = sc->n_iters;
+    const double clamp = sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0;
+    float *q = nullptr, *mu = nullptr, *s2d = nullptr;
+    double *beta = nullptr, *bvec = nullptr, *costs = nullptr, *z0 = nullptr, *scratch = nullptr;
+    double *tmpa = nullptr, *tmpb = nullptr, *gimg = nullptr, *cpart = nullptr;
+    uint8_t *mask = nullptr, *mask2 = nullptr, *leaf = nullptr;
+    WST(ensure_t(c, B_Q, (size_t)M, &q));
+    WST(ensure_t(c, B_MU, (size_t)N, &mu));
+    WST(ensure_t(c, B_BETA, (size_t)N, &beta));
+    WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
+    WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
+    WST(ensure_t(c, B_Z0, 1, &z0));
+    WST(ensure_t(c, B_SCRATCH, 1024, &scratch));
+    WST(ensure_t(c, B_TMPA, (size_t)N, &tmpa));
+    WST(ensure_t(c, B_TMPB, (size_t)N, &tmpb));
+    WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
+    WST(ensure_t(c, B_S2D, (size_t)lay.nslice, &s2d));
+    const int np = forward3_parts(g);
+    WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+    if (L > 0) {
+        WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
+        WST(ensure_t(c, B_MASK_B, (size_t)lay.mask_bytes, &mask2));
+        WST(ensure_t(c, B_LEAF, (size_t)N, &leaf));
+    }
+    const float* dsino = static_cast<const float*>(c->buf[B_D].p);
+    const float* I0 = static_cast<const float*>(c->buf[B_I0].p);
+    const double* dterm = static_cast<const double*>(c->buf[B_DTERM].p);
+
+    // a0: b = Omega^T H^T d
+    SegTable3 vox;
+    float* part = nullptr;
+    WST(plan_voxels3(c, z3, &vox, &part));
+    {
+        PROF(WAM_K_BACKPROJECT);
+        WCK(c, launch_backproject3(g, vox, z3, dsino, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+    }
+    {
+        PROF(WAM_K_TREE);
+        WCK(c, launch_reduce_voxels3(vox, lay, part, gimg, nullptr, st));
+        WCK(c, launch_haar3(lay, gimg, bvec, tmpa, tmpb, st));
+    }
+    WCK(c, cudaMemsetAsync(beta, 0, N * sizeof(double), st));
+    SegTable3 tab;
+    long long leaves = N;
+    if (L > 0) {
+        WCK(c, cudaMemsetAsync(mask, 0, lay.mask_bytes, st));
+        WST(plan_tree3(c, lay, mask, leaf, &tab, &part, &leaves, st));
+    } else {
+        tab = vox;
+    }
+    {
+        PROF(WAM_K_Z0);
+        WST(compute_z03(c, g, lay, leaf, z0, st));
+    }
+    auto pick = [&]() -> const uint8_t* { return (L > 0 && 4 * leaves < N) ? leaf : nullptr; };
+    const uint8_t* fleaf = pick();
+    std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
+                            sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
+    size_t next_exp = 0;
+    for (int j = 0; j <= J; ++j) {
+        {
+            PROF(WAM_K_SYNTH);
+            WCK(c, launch_synth3(lay, leaf, beta, mu, st));
+        }
+        {
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_forward3(g, mu, fleaf, z3, dsino, dterm, I0, q, nullptr, cpart, work_ptr(c, WAM_K_FORWARD),
+                                   st));
+            WCK(c, launch_sum_final(cpart, np, costs + j, st));
+        }
+        if (j == J) break;
+        {
+            PROF(WAM_K_BACKPROJECT);
+            WCK(c, launch_backproject3(g, tab, z3, q, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+        }
+        {
+            PROF(WAM_K_UPDATE);
+            WCK(c, launch_update3(tab, lay, part, bvec, z0, clamp, beta, st));
+        }
+        if (L > 0 && next_exp < exp_at.size() && exp_at[next_exp] == j + 1) {
+            const double tau = sc->tau[next_exp];
+            ++next_exp;
+            {
+                PROF(WAM_K_TREE);
+                WCK(c, launch_synth3(lay, leaf, beta, mu, st));
+                WCK(c, cudaMemcpyAsync(mask2, mask, lay.mask_bytes, cudaMemcpyDeviceToDevice, st));
+                WCK(c, launch_expand3(lay, mu, tau, leaf, mask2, s2d, scratch, st));
+            }
+            std::swap(mask, mask2);
+            std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
+            WST(plan_tree3(c, lay, mask, leaf, &tab, &part, &leaves, st));
+            fleaf = pick();
+            {
+                PROF(WAM_K_Z0);
+                WST(compute_z03(c, g, lay, leaf, z0, st));
+            }
+        }
+    }
+    const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (mu_out) WCK(c, cudaMemcpyAsync(mu_out, mu, N * sizeof(float), k2, st));
+    if (mask_out && L > 0) WCK(c, cudaMemcpyAsync(mask_out, mask, lay.mask_bytes, k2, st));
+    std::vector<double> h(J + 1);
+    WCK(c, cudaMemcpyAsync(h.data(), costs, (J + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
+    WCK(c, cudaStreamSynchronize(st));
+    if (c->prof) WST(prof_resolve(c));
+    for (int j = 0; j < J; ++j)
+        if (h[j + 1] > h[j] + 1e-6 * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
+    return WAM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -672,8 +1004,9 @@ wam_status wam_create(const wam_geometry* g, wam_ctx** out)
     try {
         wam_ctx* c = new wam_ctx();
         c->g = *g;
-        c->N = (long long)g->nx * g->ny;
-        c->M = (long long)g->n_views * g->n_bins;
+        const bool cone = g->kind == WAM_CONE3D_FLAT_CIRCULAR;
+        c->N = (long long)g->nx * g->ny * (cone ? g->nz : 1);
+        c->M = (long long)g->n_views * g->n_bins * (cone ? g->n_rows : 1);
         if (cudaGetDevice(&c->device) != cudaSuccess) {
             cudaGetLastError();
             delete c;
@@ -709,6 +1042,16 @@ void wam_destroy(wam_ctx* c)
 }
 
 const char* wam_last_error(const wam_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t wam_mask_bytes_dims(const wam_ctx* c, int levels, int dims)
+{
+    if (!c || levels < 0 || levels > WAM_MAX_LEVELS) return 0;
+    if (dims != 3) return wam_mask_bytes(c, levels);
+    size_t s = 0;
+    for (int l = 1; l <= levels; ++l)
+        s += (size_t)(c->g.nx >> l) * (size_t)(c->g.ny >> l) * (size_t)(c->g.nz >> l);
+    return s;
+}
 
 size_t wam_mask_bytes(const wam_ctx* c, int levels)
 {
@@ -772,6 +1115,8 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
     }
     try {
         cudaStream_t st = as_stream(stream);
+        if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR)
+            return reconstruct3_impl(c, sc, mu_out, hist, mask_out, on_device, st);
         if (sc->precision == 32) return reconstruct_impl<float>(c, sc, mu_out, hist, mask_out, on_device, st);
         return reconstruct_impl<double>(c, sc, mu_out, hist, mask_out, on_device, st);
     } catch (...) {
@@ -781,10 +1126,41 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
 
 // ---- steps ------------------------------------------------------------------
 
-wam_status wam_project(wam_ctx* c, const float* mu, float* p, void* s) { return project_impl<float>(c, mu, p, s); }
+wam_status wam_project(wam_ctx* c, const float* mu, float* p, void* s)
+{
+    if (c && c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) {
+        if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
+        Geom3 g;
+        WST(make_geom3(c, &g));
+        WCK(c, launch_forward3(g, mu, nullptr, 1, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+                               as_stream(s)));
+        return WAM_OK;
+    }
+    return project_impl<float>(c, mu, p, s);
+}
 wam_status wam_project_f64(wam_ctx* c, const double* mu, double* p, void* s) { return project_impl<double>(c, mu, p, s); }
 
-wam_status wam_backproject(wam_ctx* c, const float* s, float* g, void* st) { return backproject_impl<float>(c, s, g, st); }
+wam_status wam_backproject(wam_ctx* c, const float* s, float* gout, void* st)
+{
+    if (c && c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) {
+        if (!s || !gout) return fail(c, WAM_ERR_ARG, "null pointer");
+        try {
+            Layout3 lay;
+            WST(make_layout3(c, 0, 1, &lay));
+            Geom3 g;
+            WST(make_geom3(c, &g));
+            SegTable3 tab;
+            float* part = nullptr;
+            WST(plan_voxels3(c, 1, &tab, &part));
+            WCK(c, launch_backproject3(g, tab, 1, s, part, nullptr, as_stream(st)));
+            WCK(c, launch_reduce_voxels3(tab, lay, part, nullptr, gout, as_stream(st)));
+            return WAM_OK;
+        } catch (...) {
+            return fail(c, WAM_ERR_OOM, "host allocation failed");
+        }
+    }
+    return backproject_impl<float>(c, s, gout, st);
+}
 wam_status wam_backproject_f64(wam_ctx* c, const double* s, double* g, void* st)
 {
     return backproject_impl<double>(c, s, g, st);
@@ -793,6 +1169,7 @@ wam_status wam_backproject_f64(wam_ctx* c, const double* s, double* g, void* st)
 wam_status wam_haar(wam_ctx* c, int levels, const double* in, double* out, int inverse, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!in || !out || in == out) return fail(c, WAM_ERR_ARG, "in and out must be distinct non-null arrays");
     Layout lay;
     WST(make_layout(c, levels, &lay));
@@ -807,6 +1184,7 @@ wam_status wam_synthesize(wam_ctx* c, int levels, const unsigned char* masks, co
                           void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!beta || !mu || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
     WST(make_layout(c, levels, &lay));
@@ -833,6 +1211,7 @@ wam_status wam_split_backproject(wam_ctx* c, int levels, const unsigned char* ma
                                  double* bplus, double* bminus, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!qhat || !bplus || !bminus || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
     try {
         Layout lay;
@@ -864,6 +1243,7 @@ wam_status wam_split_backproject(wam_ctx* c, int levels, const unsigned char* ma
 wam_status wam_z0(wam_ctx* c, int levels, const unsigned char* masks, double* z0, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!z0 || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
     WST(make_layout(c, levels, &lay));
@@ -879,6 +1259,7 @@ wam_status wam_update(wam_ctx* c, int levels, const unsigned char* masks, const 
                       const double* bminus, const double* z0, double clamp, double* beta, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!b || !bplus || !bminus || !z0 || !beta || (levels > 0 && !masks)) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
     WST(make_layout(c, levels, &lay));
@@ -890,6 +1271,7 @@ wam_status wam_expand(wam_ctx* c, int levels, const float* S, double tau, const 
                       unsigned char* mask_out, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (levels < 1) return fail(c, WAM_ERR_ARG, "levels must be >= 1");
     if (!S || !mask_in || !mask_out || mask_in == mask_out) return fail(c, WAM_ERR_ARG, "bad pointers");
     if (!std::isfinite(tau)) return fail(c, WAM_ERR_ARG, "tau must be finite");
@@ -984,6 +1366,7 @@ extern "C" {
 wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!beta || !p) return fail(c, WAM_ERR_ARG, "null pointer");
     try {
         Layout lay;
@@ -1004,6 +1387,7 @@ wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p,
 wam_status wam_backproject_coef(wam_ctx* c, int levels, const float* s, float* gout, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!s || !gout) return fail(c, WAM_ERR_ARG, "null pointer");
     try {
         Layout lay;
@@ -1022,6 +1406,7 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
                          float* qhat, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
     if (!beta || !loss || !grad) return fail(c, WAM_ERR_ARG, "null pointer");
     if (!(lambda >= 0.0f) || !std::isfinite(lambda)) return fail(c, WAM_ERR_ARG, "lambda must be finite and >= 0");
@@ -1061,6 +1446,7 @@ wam_status wam_am_derivs(wam_ctx* c, int levels, const double* b, const double* 
                          const double* z0, double clamp, float* dplus, float* dminus, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!b || !bplus || !bminus || !z0 || !dplus || !dminus) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
     WST(make_layout(c, levels, &lay));
@@ -1073,6 +1459,7 @@ wam_status wam_phi_split_project(wam_ctx* c, int levels, const float* gbar, cons
                                  const float* dminus, const float* qhat, float* out, void* stream)
 {
     if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
     if (!gbar || !dplus || !dminus || !out) return fail(c, WAM_ERR_ARG, "null pointer");
     Layout lay;
     WST(make_layout(c, levels, &lay));

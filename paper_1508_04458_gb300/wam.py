@@ -72,6 +72,7 @@ _PROTOS = {
     "wam_destroy": (None, [_P]),
     "wam_last_error": (ctypes.c_char_p, [_P]),
     "wam_mask_bytes": (ctypes.c_size_t, [_P, _I]),
+    "wam_mask_bytes_dims": (ctypes.c_size_t, [_P, _I, _I]),
     "wam_set_data": (_S, [_P, _P, _P, _I, _I, _P]),
     "wam_reconstruct": (_S, [_P, ctypes.POINTER(wam_schedule), _P, _P, _P, _I, _P]),
     "wam_project": (_S, [_P, _P, _P, _P]),
@@ -138,13 +139,14 @@ def geometry(g) -> wam_geometry:
 
 
 def schedule(levels: int, n_iters: int, expand_at: Sequence[int] = (), tau: Sequence[float] = (),
-             precision: int = 32, full_am: bool = False, clamp: float = 30.0):
+             precision: int = 32, full_am: bool = False, clamp: float = 30.0, dims: int = 2,
+             zsum: bool = False):
     """wam_schedule plus the arrays it points to (keep the tuple alive)."""
     ea = (ctypes.c_int * max(1, len(expand_at)))(*expand_at)
     ta = (ctypes.c_double * max(1, len(tau)))(*tau)
-    s = wam_schedule(levels=levels, dims=2, n_iters=n_iters, n_expand=len(expand_at),
+    s = wam_schedule(levels=levels, dims=dims, n_iters=n_iters, n_expand=len(expand_at),
                      expand_at=ctypes.cast(ea, ctypes.POINTER(ctypes.c_int)),
-                     tau=ctypes.cast(ta, ctypes.POINTER(ctypes.c_double)), zsum_criterion=0,
+                     tau=ctypes.cast(ta, ctypes.POINTER(ctypes.c_double)), zsum_criterion=1 if zsum else 0,
                      precision=precision, full_am=1 if full_am else 0, dmax_clamp=clamp)
     return s, (ea, ta)
 
@@ -177,8 +179,8 @@ class Context:
             raise WamError(st, (wam_last_error(self.h) or b"").decode())
         return st
 
-    def mask_bytes(self, levels: int) -> int:
-        return int(wam_mask_bytes(self.h, levels))
+    def mask_bytes(self, levels: int, dims: int = 2) -> int:
+        return int(wam_mask_bytes_dims(self.h, levels, dims))
 
     def set_data(self, d, I0, stream: Optional[int] = None):
         """d: numpy (host) or torch (device) float32 [V][B]; I0 scalar or array."""
@@ -197,27 +199,29 @@ class Context:
         return self.check(wam_set_data(self.h, hptr(d), hptr(i0), int(scalar), 0, s))
 
     def reconstruct(self, levels: int, n_iters: int, expand_at=(), tau=(), precision: int = 32,
-                    full_am: bool = False, device_out: bool = False, stream: Optional[int] = None):
-        """Run the method; returns (mu, idiv history, masks, status)."""
+                    full_am: bool = False, device_out: bool = False, stream: Optional[int] = None,
+                    dims: int = 2, zsum: bool = False):
+        """Run the method; returns (mu, idiv history, masks, status).  Cone-beam
+        contexts: dims = 3 (3-D Haar) or dims = 2 with zsum (per-slice Haar)."""
         import torch
-        sc, keep = schedule(levels, n_iters, expand_at, tau, precision, full_am)
+        sc, keep = schedule(levels, n_iters, expand_at, tau, precision, full_am, dims=dims, zsum=zsum)
         L = 0 if full_am else levels
-        N = self.geom.nx * self.geom.ny
+        N = self.geom.nx * self.geom.ny * max(1, getattr(self.geom, "nz", 1))
         s = current_stream() if stream is None else stream
         if device_out:
             dt = torch.float32 if precision == 32 else torch.float64
             mu = torch.empty(N, dtype=dt, device="cuda")
             hist = torch.empty(n_iters + 1, dtype=torch.float64, device="cuda")
-            masks = torch.empty(max(1, self.mask_bytes(L)), dtype=torch.uint8, device="cuda")
+            masks = torch.empty(max(1, self.mask_bytes(L, dims)), dtype=torch.uint8, device="cuda")
             st = wam_reconstruct(self.h, ctypes.byref(sc), ptr(mu), ptr(hist), ptr(masks), 1, s)
         else:
             mu = np.empty(N, dtype=np.float32 if precision == 32 else np.float64)
             hist = np.empty(n_iters + 1, dtype=np.float64)
-            masks = np.empty(max(1, self.mask_bytes(L)), dtype=np.uint8)
+            masks = np.empty(max(1, self.mask_bytes(L, dims)), dtype=np.uint8)
             st = wam_reconstruct(self.h, ctypes.byref(sc), hptr(mu), hptr(hist), hptr(masks), 0, s)
         del keep
         self.check(st, allow=(WAM_OK, WAM_WARN_NONMONOTONE))
-        return mu, hist, masks[: self.mask_bytes(L)], st
+        return mu, hist, masks[: self.mask_bytes(L, dims)], st
 
     def profile(self, enable: bool = True):
         """Reset and enable (or stop) per-kernel event timing of reconstruct()."""

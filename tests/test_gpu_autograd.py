@@ -76,7 +76,7 @@ def test_idiv_loss_gradient(lam):
     loss = IDivLoss.apply(bt, ops, lam)
     loss.backward()
     ref = _oracle_loss(Phi, p, beta, lam, nA)
-    assert abs(float(loss) - ref) <= 1e-5 * ref
+    assert abs(float(loss.detach()) - ref) <= 1e-5 * ref
     q = p.I0 * np.exp(-(Phi @ beta))
     g_ref = Phi.T @ (p.d.ravel() - q)
     g_ref[nA:] += lam * np.sign(beta[nA:])
