@@ -160,6 +160,32 @@ wam_status wam_reconstruct(wam_ctx* ctx, const wam_schedule* sched, void* mu_out
                            double* idiv_hist, unsigned char* mask_out, int on_device,
                            void* stream);
 
+/* Many independent scans (bags) of any sizes with one schedule, 2-D contexts,
+ * precision 32.  Their iterations are interleaved: all bags share the
+ * schedule, so between two expansions every bag runs on the same tree epoch;
+ * with use_graph = 1 one iteration of every bag (each bag on its own stream,
+ * forked from and joined into `stream`) is captured once per epoch into a
+ * CUDA graph that is then launched once per iteration of the epoch (a
+ * device-side counter places each iteration's cost); use_graph = 0 launches
+ * the same kernels without a graph.  Results equal n calls of
+ * wam_reconstruct bit for bit (same kernels, fixed-order sums).
+ *   ctxs      [n] distinct contexts with data set
+ *   mu_out    [n] pointers to each bag's image (float, host or device per
+ *             on_device), or NULL; hist likewise [n] pointers to n_iters + 1
+ *             doubles, or NULL.
+ * Returns WAM_WARN_NONMONOTONE if any bag's cost rose; errors as
+ * wam_reconstruct (the first failing context keeps the message). */
+wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule* sched,
+                                 void* const* mu_out, double* const* hist, int on_device,
+                                 int use_graph, void* stream);
+
+/* Tuning knobs (set by the caller or by an autotuner that times them). */
+enum {
+    WAM_TUNE_BACK_CTAS_PER_SM = 1   /* back-projector launches aim at this many 256-thread CTAs
+                                       per SM (default 8, range 0.25 .. 256) by splitting views */
+};
+wam_status wam_set_tuning(wam_ctx* ctx, int key, double value);
+
 /* ---- the steps of one iteration (device pointers) ------------------------ */
 
 /* H: p(y) = sum_x h(y|x) mu(x) by exact ray traversal (Sec. II).

@@ -114,6 +114,18 @@ __global__ void k_sum_final(const double* __restrict__ part, int n, double* __re
     if (threadIdx.x == 0) *out = s;
 }
 
+// Same, written to out[*counter], then the counter advances (graph replays).
+__global__ void k_sum_at(const double* __restrict__ part, int n, double* __restrict__ out, int* __restrict__ counter)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_reduce(s, OpSum(), 0.0);
+    if (threadIdx.x == 0) {
+        out[*counter] = s;
+        *counter += 1;
+    }
+}
+
 __global__ void k_max_final(const double* __restrict__ part, int n, double* __restrict__ out)
 {
     double s = -INFINITY;
@@ -804,6 +816,13 @@ cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_
 {
     COUNT_LAUNCH();
     k_sum_final<<<1, 1024, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_at(const double* part, int n, double* out, int* counter, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_sum_at<<<1, 1024, 0, st>>>(part, n, out, counter);
     return cudaGetLastError();
 }
 

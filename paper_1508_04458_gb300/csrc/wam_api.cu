@@ -26,7 +26,7 @@ enum BufId {
     B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
-    B_DIR3, B_ROWINV, B_DLEN, B_S2D,
+    B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER,
     B_NBUF
 };
 
@@ -46,6 +46,8 @@ struct wam_ctx {
     wam_stats stats{};
     unsigned long long* dwork = nullptr;   // device [WAM_NKERNEL]
     long long last_leaves = 0;             // leaves of the tree last planned
+    // tuning
+    double back_ctas_per_sm = 8.0;         // back-projector work split: CTAs per SM per launch
     cudaStream_t prof_stream = nullptr;
     int device = 0;
     int num_sms = 148;
@@ -271,7 +273,7 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         cost[i] = shadow * ((lists[i].has_details || lists[i].quad) ? 3.0 : 1.0);
         total += (double)lists[i].n * w.n_views * cost[i];
     }
-    const double target_ctas = (double)c->num_sms * 8.0;
+    const double target_ctas = (double)c->num_sms * c->back_ctas_per_sm;
     const double per_cta = std::max(total / target_ctas, 1.0);
     const int max_chunks = std::max(1, w.n_views / kViewLanes);
     int cta = 0, items = 0;
@@ -456,95 +458,115 @@ inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 // ---------------------------------------------------------------------------
 // the reconstruction driver
 // ---------------------------------------------------------------------------
+// One reconstruction split into phases.  iteration() and final_cost() only
+// launch kernels on the given stream (no allocation, no host wait), so a
+// batch of runs can capture them in a CUDA graph; expand() reads the new
+// block-list lengths back to the host.
 template <typename T>
-wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
-                            int on_device, cudaStream_t st)
-{
-    const int L = sc->full_am ? 0 : sc->levels;
-    Layout lay;
-    WST(make_layout(c, L, &lay));
-    Geom<T> g;
-    WST(make_geom<T>(c, &g));
-    const long long N = c->N, M = c->M;
-    const int J = sc->n_iters;
-    const double clamp = sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0;
-
-    T *q = nullptr, *mu = nullptr, *sino = nullptr;
+struct Run {
+    wam_ctx* c = nullptr;
+    const wam_schedule* sc = nullptr;
+    int L = 0, J = 0, np = 0;
+    double clamp = 30.0;
+    long long N = 0, M = 0;
+    Layout lay{};
+    Geom<T> g{};
+    T *q = nullptr, *mu = nullptr, *sino = nullptr, *part = nullptr;
     double *beta = nullptr, *bvec = nullptr, *costs = nullptr, *z0 = nullptr, *scratch = nullptr;
     double *tmpa = nullptr, *tmpb = nullptr, *gimg = nullptr, *cpart = nullptr;
     uint8_t *mask = nullptr, *mask2 = nullptr, *leaf = nullptr;
-    WST(ensure_t(c, B_Q, (size_t)M, &q));
-    WST(ensure_t(c, B_MU, (size_t)N, &mu));
-    WST(ensure_t(c, B_BETA, (size_t)N, &beta));
-    WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
-    WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
-    WST(ensure_t(c, B_Z0, 1, &z0));
-    WST(ensure_t(c, B_SCRATCH, 1024, &scratch));
-    WST(ensure_t(c, B_TMPA, (size_t)N, &tmpa));
-    WST(ensure_t(c, B_TMPB, (size_t)N, &tmpb));
-    WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
-    const int np = forward_parts(g.V, g.B);
-    WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
-    if (L > 0) {
-        WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
-        WST(ensure_t(c, B_MASK_B, (size_t)lay.mask_bytes, &mask2));
-        WST(ensure_t(c, B_LEAF, (size_t)N, &leaf));
-    }
-    const float* dsino = static_cast<const float*>(c->buf[B_D].p);
-    const float* I0 = static_cast<const float*>(c->buf[B_I0].p);
-    const double* dterm = static_cast<const double*>(c->buf[B_DTERM].p);
-
+    int* counter = nullptr;
+    const float *dsino = nullptr, *I0 = nullptr;
+    const double* dterm = nullptr;
     const void* dirt = nullptr;
-    WST(dir_table<T>(c, &dirt));
-
-    // a0, Eq. 1.6: b = Phi^T d = Omega^T (H^T d) for every coefficient
-    SegTable pix;
-    T* part = nullptr;
-    WST(plan_pixels<T>(c, &pix, &part));
-    const T* dT;
-    if (sizeof(T) == sizeof(float)) {
-        dT = reinterpret_cast<const T*>(dsino);
-    } else {
-        WST(ensure_t(c, B_SINO, (size_t)M, &sino));
-        WCK(c, (launch_convert<float, double>(dsino, reinterpret_cast<double*>(sino), M, st)));
-        dT = sino;
-    }
-    {
-        PROF(WAM_K_BACKPROJECT);
-        WCK(c, launch_backproject(g, pix, dT, dirt, part, work_ptr(c, WAM_K_BACKPROJECT), st));
-    }
-    {
-        PROF(WAM_K_TREE);
-        WCK(c, (launch_reduce_pixels<T, double>(pix, c->g.nx, N, part, gimg, st)));
-        WCK(c, launch_haar(lay, gimg, bvec, 0, tmpa, tmpb, st));
-    }
-
-    // beta^(0) = 0; the tree holds the approximations only
-    WCK(c, cudaMemsetAsync(beta, 0, N * sizeof(double), st));
-    SegTable tab;
-    if (L > 0) {
-        WCK(c, cudaMemsetAsync(mask, 0, lay.mask_bytes, st));
-        WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
-    } else {
-        tab = pix;
-    }
-    {
-        PROF(WAM_K_Z0);
-        WST(compute_z0<T>(c, g, lay, leaf, z0, st));
-    }
+    SegTable tab{};
+    const uint8_t* fwd_leaf = nullptr;
+    std::vector<int> exp_at;
+    size_t next_exp = 0;
 
     // The leaf walk pays per leaf what the pixel walk pays per pixel, about
     // 2.5 times over; once leaves average fewer than 4 pixels the image mu
     // (constant on leaves) is projected pixel by pixel instead.
-    auto pick_leaf = [&]() -> const uint8_t* {
-        return (L > 0 && 4 * c->last_leaves < N) ? leaf : nullptr;
-    };
-    const uint8_t* fwd_leaf = pick_leaf();
+    const uint8_t* pick_leaf() const { return (L > 0 && 4 * c->last_leaves < N) ? leaf : nullptr; }
 
-    std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
-                            sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
-    size_t next_exp = 0;
-    for (int j = 0; j < J; ++j) {
+    wam_status setup(wam_ctx* ctx, const wam_schedule* sched, cudaStream_t st)
+    {
+        c = ctx;
+        sc = sched;
+        L = sc->full_am ? 0 : sc->levels;
+        J = sc->n_iters;
+        clamp = sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0;
+        WST(make_layout(c, L, &lay));
+        WST(make_geom<T>(c, &g));
+        N = c->N;
+        M = c->M;
+        WST(ensure_t(c, B_Q, (size_t)M, &q));
+        WST(ensure_t(c, B_MU, (size_t)N, &mu));
+        WST(ensure_t(c, B_BETA, (size_t)N, &beta));
+        WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
+        WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
+        WST(ensure_t(c, B_Z0, 1, &z0));
+        WST(ensure_t(c, B_SCRATCH, 1024, &scratch));
+        WST(ensure_t(c, B_TMPA, (size_t)N, &tmpa));
+        WST(ensure_t(c, B_TMPB, (size_t)N, &tmpb));
+        WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
+        WST(ensure_t(c, B_COUNTER, 1, &counter));
+        np = forward_parts(g.V, g.B);
+        WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+        if (L > 0) {
+            WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
+            WST(ensure_t(c, B_MASK_B, (size_t)lay.mask_bytes, &mask2));
+            WST(ensure_t(c, B_LEAF, (size_t)N, &leaf));
+        }
+        dsino = static_cast<const float*>(c->buf[B_D].p);
+        I0 = static_cast<const float*>(c->buf[B_I0].p);
+        dterm = static_cast<const double*>(c->buf[B_DTERM].p);
+        WST(dir_table<T>(c, &dirt));
+
+        // a0, Eq. 1.6: b = Phi^T d = Omega^T (H^T d) for every coefficient
+        SegTable pix;
+        WST(plan_pixels<T>(c, &pix, &part));
+        const T* dT;
+        if (sizeof(T) == sizeof(float)) {
+            dT = reinterpret_cast<const T*>(dsino);
+        } else {
+            WST(ensure_t(c, B_SINO, (size_t)M, &sino));
+            WCK(c, (launch_convert<float, double>(dsino, reinterpret_cast<double*>(sino), M, st)));
+            dT = sino;
+        }
+        {
+            PROF(WAM_K_BACKPROJECT);
+            WCK(c, launch_backproject(g, pix, dT, dirt, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+        }
+        {
+            PROF(WAM_K_TREE);
+            WCK(c, (launch_reduce_pixels<T, double>(pix, c->g.nx, N, part, gimg, st)));
+            WCK(c, launch_haar(lay, gimg, bvec, 0, tmpa, tmpb, st));
+        }
+        // beta^(0) = 0; the tree holds the approximations only
+        WCK(c, cudaMemsetAsync(beta, 0, N * sizeof(double), st));
+        WCK(c, cudaMemsetAsync(counter, 0, sizeof(int), st));
+        if (L > 0) {
+            WCK(c, cudaMemsetAsync(mask, 0, lay.mask_bytes, st));
+            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+        } else {
+            tab = pix;
+        }
+        {
+            PROF(WAM_K_Z0);
+            WST(compute_z0<T>(c, g, lay, leaf, z0, st));
+        }
+        fwd_leaf = pick_leaf();
+        exp_at.assign(sc->n_expand > 0 ? sc->expand_at : nullptr,
+                      sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
+        next_exp = 0;
+        return WAM_OK;
+    }
+
+    // a1 - a6 of iteration j; with use_counter the cost goes to
+    // costs[*counter] (then counter + 1) instead of costs[j]
+    wam_status iteration(int j, cudaStream_t st, bool use_counter)
+    {
         {
             PROF(WAM_K_SYNTH);
             WCK(c, launch_synth(lay, leaf, beta, mu, st));                                  // a1
@@ -553,7 +575,8 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
             PROF(WAM_K_FORWARD);                                                            // a2, a3
             WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
-            WCK(c, launch_sum_final(cpart, np, costs + j, st));
+            if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
+            else WCK(c, launch_sum_final(cpart, np, costs + j, st));
         }
         {
             PROF(WAM_K_BACKPROJECT);                                                        // a4
@@ -563,48 +586,90 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
             PROF(WAM_K_UPDATE);                                                             // a6
             WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, st));
         }
-        if (L > 0 && next_exp < exp_at.size() && exp_at[next_exp] == j + 1) {              // a7
-            const double tau = sc->tau[next_exp];
-            ++next_exp;
-            {
-                PROF(WAM_K_TREE);
-                WCK(c, launch_synth(lay, leaf, beta, mu, st));
-                WCK(c, cudaMemcpyAsync(mask2, mask, lay.mask_bytes, cudaMemcpyDeviceToDevice, st));
-                WCK(c, launch_expand<T>(lay, mu, tau, leaf, mask2, scratch, st));
-            }
-            std::swap(mask, mask2);
-            std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
-            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
-            fwd_leaf = pick_leaf();
-            {
-                PROF(WAM_K_Z0);
-                WST(compute_z0<T>(c, g, lay, leaf, z0, st));                              // a5
-            }
-        }
-    }
-    {
-        PROF(WAM_K_SYNTH);
-        WCK(c, launch_synth(lay, leaf, beta, mu, st));
-    }
-    {
-        PROF(WAM_K_FORWARD);
-        WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
-                              work_ptr(c, WAM_K_FORWARD), st));
-        WCK(c, launch_sum_final(cpart, np, costs + J, st));
+        return WAM_OK;
     }
 
-    const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (mu_out) WCK(c, cudaMemcpyAsync(mu_out, mu, N * sizeof(T), k2, st));
-    if (mask_out && L > 0) WCK(c, cudaMemcpyAsync(mask_out, mask, lay.mask_bytes, k2, st));
-    std::vector<double> h(J + 1);
-    WCK(c, cudaMemcpyAsync(h.data(), costs, (J + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
+    bool expands_after(int j) const
+    {
+        return L > 0 && next_exp < exp_at.size() && exp_at[next_exp] == j + 1;
+    }
+
+    // a7 (+ new block lists and a5); call when expands_after(j)
+    wam_status expand(cudaStream_t st)
+    {
+        const double tau = sc->tau[next_exp];
+        ++next_exp;
+        {
+            PROF(WAM_K_TREE);
+            WCK(c, launch_synth(lay, leaf, beta, mu, st));
+            WCK(c, cudaMemcpyAsync(mask2, mask, lay.mask_bytes, cudaMemcpyDeviceToDevice, st));
+            WCK(c, launch_expand<T>(lay, mu, tau, leaf, mask2, scratch, st));
+        }
+        std::swap(mask, mask2);
+        std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
+        WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+        fwd_leaf = pick_leaf();
+        {
+            PROF(WAM_K_Z0);
+            WST(compute_z0<T>(c, g, lay, leaf, z0, st));                                  // a5
+        }
+        return WAM_OK;
+    }
+
+    wam_status final_cost(cudaStream_t st, bool use_counter)
+    {
+        {
+            PROF(WAM_K_SYNTH);
+            WCK(c, launch_synth(lay, leaf, beta, mu, st));
+        }
+        {
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+                                  work_ptr(c, WAM_K_FORWARD), st));
+            if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
+            else WCK(c, launch_sum_final(cpart, np, costs + J, st));
+        }
+        return WAM_OK;
+    }
+
+    // copies results out (on st) and returns the cost history on the host
+    wam_status copy_out(void* mu_out, double* hist, unsigned char* mask_out, int on_device, std::vector<double>* h,
+                        cudaStream_t st)
+    {
+        const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (mu_out) WCK(c, cudaMemcpyAsync(mu_out, mu, N * sizeof(T), k2, st));
+        if (mask_out && L > 0) WCK(c, cudaMemcpyAsync(mask_out, mask, lay.mask_bytes, k2, st));
+        h->resize(J + 1);
+        WCK(c, cudaMemcpyAsync(h->data(), costs, (J + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
+        return WAM_OK;
+    }
+
+    wam_status monotone(const std::vector<double>& h) const
+    {
+        const double band = sizeof(T) == sizeof(float) ? 1e-6 : 1e-11;
+        for (int j = 0; j < J; ++j)
+            if (h[j + 1] > h[j] + band * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
+        return WAM_OK;
+    }
+};
+
+template <typename T>
+wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
+                            int on_device, cudaStream_t st)
+{
+    Run<T> run;
+    WST(run.setup(c, sc, st));
+    for (int j = 0; j < run.J; ++j) {
+        WST(run.iteration(j, st, false));
+        if (run.expands_after(j)) WST(run.expand(st));
+    }
+    WST(run.final_cost(st, false));
+    std::vector<double> h;
+    WST(run.copy_out(mu_out, hist, mask_out, on_device, &h, st));
     WCK(c, cudaStreamSynchronize(st));
     if (c->prof) WST(prof_resolve(c));
-    const double band = sizeof(T) == sizeof(float) ? 1e-6 : 1e-11;
-    for (int j = 0; j < J; ++j)
-        if (h[j + 1] > h[j] + band * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
-    return WAM_OK;
+    return run.monotone(h);
 }
 
 template <typename T>
@@ -785,7 +850,7 @@ wam_status plan3(wam_ctx* c, int z3, const std::vector<ListInfo3>& lists, SegTab
         cost[i] = rays * ((li.has_details || li.octet) ? 4.0 : 1.0);
         total += (double)li.n * w.n_views * cost[i];
     }
-    const double per_cta = std::max(total / ((double)c->num_sms * 8.0), 1.0);
+    const double per_cta = std::max(total / ((double)c->num_sms * c->back_ctas_per_sm), 1.0);
     const int max_chunks = std::max(1, w.n_views / kViewLanes);
     int cta = 0, items = 0;
     long long part = 0;
@@ -1320,6 +1385,162 @@ wam_status wam_get_stats(wam_ctx* c, wam_stats* out)
 }
 
 unsigned long long wam_kernel_launches(void) { return wam::kernel_launches(); }
+
+wam_status wam_set_tuning(wam_ctx* c, int key, double value)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (key == WAM_TUNE_BACK_CTAS_PER_SM) {
+        if (!(value >= 0.25 && value <= 256.0)) return fail(c, WAM_ERR_ARG, "CTAs per SM must be in [0.25, 256]");
+        c->back_ctas_per_sm = value;
+        return WAM_OK;
+    }
+    return fail(c, WAM_ERR_ARG, "unknown tuning key");
+}
+
+wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule* sc, void* const* mu_out,
+                                 double* const* hist, int on_device, int use_graph, void* stream)
+{
+    if (!ctxs || n <= 0 || !sc) return WAM_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return WAM_ERR_ARG;
+        if (ctxs[i]->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(ctxs[i], WAM_ERR_ARG, "2-D contexts only");
+        if (!ctxs[i]->has_data) return fail(ctxs[i], WAM_ERR_STATE, "wam_set_data must be called first");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(ctxs[i], WAM_ERR_ARG, "a context appears twice in the batch");
+    }
+    wam_ctx* c0 = ctxs[0];
+    if (sc->precision != 32) return fail(c0, WAM_ERR_ARG, "batched reconstruction runs in precision 32");
+    if (sc->n_iters < 0 || sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
+        return fail(c0, WAM_ERR_ARG, "bad schedule");
+    for (int k = 0; k < sc->n_expand; ++k)
+        if (sc->expand_at[k] < 1 || (k > 0 && sc->expand_at[k] <= sc->expand_at[k - 1]) || !std::isfinite(sc->tau[k]))
+            return fail(c0, WAM_ERR_ARG, "expand_at must be increasing and >= 1, tau finite");
+    // the batch runs on its own non-blocking stream `st` (graph capture is not
+    // possible on the legacy default stream), ordered after the caller's
+    // stream; the caller's stream waits for it at the end
+    const cudaStream_t user = as_stream(stream);
+    cudaStream_t st = nullptr;
+    std::vector<cudaStream_t> ss(n, nullptr);
+    std::vector<cudaEvent_t> joins(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    std::vector<bool> prof(n);
+    for (int i = 0; i < n; ++i) prof[i] = ctxs[i]->prof;
+    wam_status ret = WAM_OK;
+    auto cleanup = [&]() {
+        if (st && fork && cudaEventRecord(fork, st) == cudaSuccess) cudaStreamWaitEvent(user, fork, 0);
+        for (int i = 0; i < n; ++i) {
+            if (ss[i]) cudaStreamDestroy(ss[i]);
+            if (joins[i]) cudaEventDestroy(joins[i]);
+            ctxs[i]->prof = prof[i];
+        }
+        if (st) cudaStreamDestroy(st);
+        if (fork) cudaEventDestroy(fork);
+        cudaGetLastError();
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(fork, user) != cudaSuccess || cudaStreamWaitEvent(st, fork, 0) != cudaSuccess) {
+        cleanup();
+        return fail(c0, WAM_ERR_CUDA, "stream or event creation failed");
+    }
+    try {
+        std::vector<Run<float>> runs(n);
+        for (int i = 0; i < n; ++i) ctxs[i]->prof = false;
+        for (int i = 0; i < n; ++i) {
+            wam_status s = runs[i].setup(ctxs[i], sc, st);
+            if (s != WAM_OK) { cleanup(); return s; }
+        }
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cleanup();
+            return fail(c0, WAM_ERR_CUDA, "stream or event creation failed");
+        }
+        // one step of every run, each on its own stream, forked from and joined into st
+        auto step_all = [&](bool final_step) -> wam_status {
+            if (cudaEventRecord(fork, st) != cudaSuccess) return fail(c0, WAM_ERR_CUDA, "event record");
+            for (int i = 0; i < n; ++i) {
+                if (cudaStreamWaitEvent(ss[i], fork, 0) != cudaSuccess) return fail(c0, WAM_ERR_CUDA, "stream wait");
+                wam_status s = final_step ? runs[i].final_cost(ss[i], true) : runs[i].iteration(0, ss[i], true);
+                if (s != WAM_OK) return s;
+                if (cudaEventRecord(joins[i], ss[i]) != cudaSuccess) return fail(c0, WAM_ERR_CUDA, "event record");
+                if (cudaStreamWaitEvent(st, joins[i], 0) != cudaSuccess) return fail(c0, WAM_ERR_CUDA, "stream wait");
+            }
+            return WAM_OK;
+        };
+        const int J = sc->n_iters;
+        int j = 0;
+        while (j < J) {
+            int e = J;
+            const Run<float>& r0 = runs[0];
+            if (r0.L > 0 && r0.next_exp < r0.exp_at.size()) e = std::min(J, r0.exp_at[r0.next_exp]);
+            // iterations j .. e-1 share one tree per run
+            if (use_graph) {
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                    cudaGetLastError();
+                    cleanup();
+                    return fail(c0, WAM_ERR_CUDA, "stream capture could not start");
+                }
+                wam_status s = step_all(false);
+                const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+                if (s != WAM_OK || ec != cudaSuccess) {
+                    cudaGetLastError();
+                    if (graph) cudaGraphDestroy(graph);
+                    cleanup();
+                    return s != WAM_OK ? s : fail(c0, WAM_ERR_CUDA, "stream capture failed");
+                }
+                if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphDestroy(graph);
+                    cleanup();
+                    return fail(c0, WAM_ERR_CUDA, "graph instantiation failed");
+                }
+                for (int k = j; k < e && s == WAM_OK; ++k)
+                    if (cudaGraphLaunch(exec, st) != cudaSuccess) s = fail(c0, WAM_ERR_CUDA, "graph launch failed");
+                cudaGraphExecDestroy(exec);
+                cudaGraphDestroy(graph);
+                if (s != WAM_OK) { cleanup(); return s; }
+            } else {
+                for (int k = j; k < e; ++k) {
+                    wam_status s = step_all(false);
+                    if (s != WAM_OK) { cleanup(); return s; }
+                }
+            }
+            j = e;
+            if (j < J || (j == J && runs[0].expands_after(J - 1))) {
+                for (int i = 0; i < n; ++i) {
+                    if (!runs[i].expands_after(j - 1)) continue;
+                    wam_status s = runs[i].expand(st);
+                    if (s != WAM_OK) { cleanup(); return s; }
+                }
+            }
+        }
+        wam_status s = step_all(true);
+        if (s != WAM_OK) { cleanup(); return s; }
+        std::vector<std::vector<double>> hs(n);
+        for (int i = 0; i < n; ++i) {
+            s = runs[i].copy_out(mu_out ? mu_out[i] : nullptr, hist ? hist[i] : nullptr, nullptr, on_device, &hs[i],
+                                 st);
+            if (s != WAM_OK) { cleanup(); return s; }
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            cleanup();
+            return fail(c0, WAM_ERR_CUDA, "synchronisation failed");
+        }
+        for (int i = 0; i < n; ++i)
+            if (runs[i].monotone(hs[i]) != WAM_OK) ret = WAM_WARN_NONMONOTONE;
+    } catch (...) {
+        cleanup();
+        return fail(c0, WAM_ERR_OOM, "host allocation failed");
+    }
+    cleanup();
+    return ret;
+}
 
 }  // extern "C"
 

@@ -12,6 +12,7 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, c
 int forward_parts(int V, int B);
 cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st);
 cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st);
+cudaError_t launch_sum_at(const double* part, int n, double* out, int* counter, cudaStream_t st);
 template <typename T>
 cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, double* part, cudaStream_t st);
 template <typename T>

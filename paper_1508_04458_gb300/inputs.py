@@ -184,13 +184,25 @@ def _shape_intervals(shapes: List[Shape], x1, y1, dx, dy):
     return t0, t1
 
 
-def painter_line_integrals(shapes: List[Shape], x1, y1, x2, y2, chunk: int = 4096) -> np.ndarray:
+def painter_line_integrals(shapes: List[Shape], x1, y1, x2, y2, chunk: int = 4096, device=None) -> np.ndarray:
     """Integral of mu along each segment, where mu at a point is the value of
-    the last shape (in list order) containing it, 0 outside all shapes."""
+    the last shape (in list order) containing it, 0 outside all shapes.
+    device: evaluate with torch on that device instead (large scans)."""
     R = x1.shape[0]
     out = np.zeros(R)
     if not shapes:
         return out
+    if device is not None:
+        # the same computation through the 3-D routine with z = 0 and
+        # infinitely tall prisms / cylinders along z
+        shapes3 = []
+        for s in shapes:
+            if s.kind == "ellipse":
+                shapes3.append(Shape3("ellipsoid", s.cx, s.cy, 0.0, s.a, s.b, 1e9, s.psi, mu=s.mu))
+            else:
+                shapes3.append(Shape3("box", s.cx, s.cy, 0.0, s.a, s.b, 1e9, s.psi, mu=s.mu))
+        seg = np.stack([x1, y1, np.zeros_like(x1), x2, y2, np.zeros_like(x2)], axis=1)
+        return painter_line_integrals_3d(shapes3, seg, chunk=65536, device=device)
     mus = np.array([s.mu for s in shapes])
     K = len(shapes)
     for r0 in range(0, R, chunk):
@@ -273,10 +285,10 @@ def phantom_bag(seed: int, half_width: float, n_min: int = 20, n_max: int = 40) 
 
 
 def simulate(name: str, g: Geometry, shapes: List[Shape], I0: float, seed: int,
-             ss: int = 4) -> Problem:
+             ss: int = 4, device=None) -> Problem:
     """Poisson counts d ~ Poisson(I0 exp(-line integral)) with a seeded PCG64."""
     x1, y1, x2, y2 = _ray_segments_2d(g)
-    li = painter_line_integrals(shapes, x1, y1, x2, y2)
+    li = painter_line_integrals(shapes, x1, y1, x2, y2, device=device)
     rng = np.random.Generator(np.random.PCG64(seed))
     d = rng.poisson(I0 * np.exp(-li)).astype(np.float64).reshape(g.n_views, g.n_bins)
     return Problem(name, g, shapes, float(I0), d, rasterize(shapes, g, ss),
@@ -302,7 +314,7 @@ def problem_fan512(seed: int = SEED_BASE + 1) -> Problem:
 
 
 def problem_fan(n: int, n_views: int, n_bins: int, I0: float, seed: int,
-                bin_pitch: Optional[float] = None) -> Problem:
+                bin_pitch: Optional[float] = None, device=None) -> Problem:
     """A fan-beam bag of any size; the detector covers the image's circumcircle."""
     if bin_pitch is None:
         # half-width of the shadow of the circumscribed circle, x1.03 margin
@@ -310,7 +322,23 @@ def problem_fan(n: int, n_views: int, n_bins: int, I0: float, seed: int,
         half = 1500.0 * r / math.sqrt(1000.0 ** 2 - r * r) * 1.03
         bin_pitch = 2.0 * half / n_bins
     g = geom_fan(n, n_views, n_bins, bin_pitch=bin_pitch)
-    return simulate("fan%d" % n, g, phantom_bag(seed, 0.5 * n), I0, seed)
+    return simulate("fan%d" % n, g, phantom_bag(seed, 0.5 * n), I0, seed, device=device)
+
+
+def batch_bags(n_bags: int = 32, seed0: int = SEED_BASE + 4, device=None, sizes=(256, 768),
+               views=(360, 1440), bins=(512, 1536)) -> List[Problem]:
+    """Seeded bags of uneven size: side U{256..768} in steps of 16, views
+    U{360..1440}, bins U{512..1536}, I0 log-uniform in [1e4, 1e5]; bag i
+    uses seed seed0 + i."""
+    out = []
+    for i in range(n_bags):
+        rng = np.random.Generator(np.random.PCG64(seed0 + i))
+        n = int(rng.integers(sizes[0] // 16, sizes[1] // 16 + 1)) * 16
+        V = int(rng.integers(views[0], views[1] + 1))
+        B = int(rng.integers(bins[0], bins[1] + 1))
+        I0 = float(10.0 ** rng.uniform(4.0, 5.0))
+        out.append(problem_fan(n, V, B, I0, seed0 + i, device=device))
+    return out
 
 
 def small_problem(nx: int, ny: int, n_views: int, n_bins: int, kind: int = FAN2D_FLAT,

@@ -33,6 +33,7 @@ WAM_ERR_TIMEOUT = -4
 WAM_ERR_STATE = -5
 WAM_WARN_NONMONOTONE = 1
 WAM_MAX_LEVELS = 8
+WAM_TUNE_BACK_CTAS_PER_SM = 1
 
 
 class wam_geometry(ctypes.Structure):
@@ -93,6 +94,9 @@ _PROTOS = {
     "wam_am_derivs": (_S, [_P, _I, _P, _P, _P, _P, _D, _P, _P, _P]),
     "wam_phi_split_project": (_S, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "wam_backproject_static": (_S, [ctypes.POINTER(wam_geometry), _P, _P, _P]),
+    "wam_reconstruct_batch": (_S, [ctypes.POINTER(_P), _I, ctypes.POINTER(wam_schedule), ctypes.POINTER(_P),
+                                   ctypes.POINTER(_P), _I, _I, _P]),
+    "wam_set_tuning": (_S, [_P, _I, _D]),
     "wam_profile": (_S, [_P, _I]),
     "wam_get_stats": (_S, [_P, _P]),
     "wam_kernel_launches": (ctypes.c_ulonglong, []),
@@ -237,3 +241,23 @@ class Context:
 def kernel_launches() -> int:
     """Kernels launched by libwam in this process so far."""
     return int(wam_kernel_launches())
+
+
+def reconstruct_batch(ctxs, levels: int, n_iters: int, expand_at=(), tau=(), use_graph: bool = True,
+                      stream: Optional[int] = None):
+    """wam_reconstruct_batch on device outputs; returns ([mu], [hist], status)."""
+    import torch
+    sc, keep = schedule(levels, n_iters, expand_at, tau, 32, False)
+    n = len(ctxs)
+    mus = [torch.empty(c.geom.nx * c.geom.ny, dtype=torch.float32, device="cuda") for c in ctxs]
+    hists = [torch.empty(n_iters + 1, dtype=torch.float64, device="cuda") for _ in ctxs]
+    harr = (_P * n)(*[c.h for c in ctxs])
+    marr = (_P * n)(*[ptr(m) for m in mus])
+    qarr = (_P * n)(*[ptr(h) for h in hists])
+    s = current_stream() if stream is None else stream
+    st = wam_reconstruct_batch(harr, n, ctypes.byref(sc), marr, qarr, 1, 1 if use_graph else 0, s)
+    del keep
+    if st not in (WAM_OK, WAM_WARN_NONMONOTONE):
+        msgs = [(wam_last_error(c.h) or b"").decode() for c in ctxs]
+        raise WamError(st, "; ".join(m for m in msgs if m))
+    return mus, hists, st
