@@ -338,6 +338,81 @@ def run_wam(args, problem, world, rank, local_rank):
     ctx.close()
 
 
+def _timed(fn, stream=None):
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return out, a.elapsed_time(b)
+
+
+def run_batch32(args):
+    """32 seeded bags of uneven size (256^2..768^2, 360..1440 views,
+    512..1536 bins, I0 1e4..1e5), 100 multiresolution iterations each:
+    batched (one CUDA graph per tree epoch) against the per-bag loop."""
+    import torch
+    from paper_1508_04458_gb300 import autotune, inputs as I, wam
+    bags = I.batch_bags(32, device="cuda")
+    ctxs = []
+    for p in bags:
+        c = wam.Context(p.geom)
+        c.set_data(torch.from_numpy(p.d.astype(np.float32).ravel()).cuda(), p.I0)
+        ctxs.append(c)
+    tuned = {}
+    if not args.no_tune:
+        cache = os.path.join(ROOT, "_build", "tune.json")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        for c in ctxs:
+            tuned[autotune.geometry_class(c.geom)] = autotune.tune(c, cache=cache)
+    loop = lambda: [c.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, device_out=True) for c in ctxs]
+    batch = lambda: wam.reconstruct_batch(ctxs, L_LEVELS, N_ITERS, EXPAND_AT, TAU, use_graph=True)
+    for _ in range(max(1, args.warmup)):
+        loop()
+        batch()
+    t_loop = min(_timed(loop)[1] for _ in range(args.steps))
+    t_batch = min(_timed(batch)[1] for _ in range(args.steps))
+    iters = 32 * N_ITERS
+    line = {"workload": "batch32: 32 fan-beam bags 256..768 px, 360..1440 views, 512..1536 bins, "
+                        "L=4, 100 iterations", "unit": "AM iters/s (all bags)",
+            "batched_graph": iters / (t_batch / 1e3), "per_bag_loop": iters / (t_loop / 1e3),
+            "ms_batched": t_batch, "ms_loop": t_loop, "speedup": t_loop / t_batch,
+            "autotuned_back_ctas_per_sm": tuned, "pixels": int(sum(p.geom.nx * p.geom.ny for p in bags)),
+            "rays": int(sum(p.geom.n_views * p.geom.n_bins for p in bags))}
+    print(json.dumps(line), flush=True)
+
+
+def run_cone256(args):
+    """3-D circular cone beam 256x256x128 @1.5 mm, 900 views, 64 x 768,
+    I0 5e4: plain AM and multiresolution AM (3-D Haar, L=3, expansions
+    after 8, 16, 32) and the per-slice 2-D Haar mode, 60 iterations."""
+    import torch
+    from paper_1508_04458_gb300 import inputs as I, wam
+    p = I.problem_cone256(device="cuda")
+    ctx = wam.Context(p.geom)
+    ctx.set_data(torch.from_numpy(p.d.astype(np.float32).ravel()).cuda(), p.I0)
+    J, ea, tau = 60, (8, 16, 32), (0.1, 0.03, -1.0)
+    res = {}
+    for name, kw in (("full_am", dict(levels=0, n_iters=J, full_am=True)),
+                     ("multires_3d_haar", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=3)),
+                     ("multires_per_slice", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=2, zsum=True))):
+        ctx.reconstruct(**kw, device_out=True)
+        ctx.profile(True)
+        (mu, hist, _, st), ms = _timed(lambda: ctx.reconstruct(**kw, device_out=True))
+        k = ctx.stats()
+        ctx.profile(False)
+        h = hist.cpu().numpy()
+        res[name] = {"ms": ms, "iters_per_s": J / (ms / 1e3), "status": st, "idiv0": float(h[0]),
+                     "idiv_final": float(h[-1]),
+                     "kernels": {n: {"ms": round(v["ms"], 2), "launches": v["launches"], "work": v["work"]}
+                                 for n, v in k.items()}}
+    line = {"workload": "cone256: 256x256x128 @1.5 mm, 900 views x 64 rows x 768 bins, I0 5e4, 60 iterations",
+            "unit": "AM iters/s", **res}
+    print(json.dumps(line), flush=True)
+
+
 def profile_case(full: bool):
     """A small case of the same kernels: 256x256 bag, 360 views x 512 bins."""
     import torch
@@ -362,12 +437,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-tune", action="store_true", help="batch32: skip the autotuner")
+    ap.add_argument("--workload", choices=("fan512", "batch32", "cone256"), default="fan512",
+                    help="fan512 (default): the benchmark line; batch32 / cone256: secondary "
+                         "measurements of the batched and 3-D cone-beam paths (one JSON line each)")
     ap.add_argument("--profile-case", choices=("multires", "full"), default=None,
                     help="run two reconstructions (multires or plain AM) of a 256x256 fan-beam bag "
                          "(360 views x 512 bins) for kernel profiling, print nothing")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case == "full")
+        return
+    if args.workload == "batch32":
+        run_batch32(args)
+        return
+    if args.workload == "cone256":
+        run_cone256(args)
         return
 
     world = _env_int("WORLD_SIZE", 1)

@@ -182,7 +182,7 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
 /* Tuning knobs (set by the caller or by an autotuner that times them). */
 enum {
     WAM_TUNE_BACK_CTAS_PER_SM = 1   /* back-projector launches aim at this many 256-thread CTAs
-                                       per SM (default 8, range 0.25 .. 256) by splitting views */
+                                       per SM (default 32, range 0.25 .. 256) by splitting views */
 };
 wam_status wam_set_tuning(wam_ctx* ctx, int key, double value);
 

@@ -15,7 +15,7 @@ from typing import Dict, Optional, Sequence
 
 from . import wam
 
-CANDIDATES = (2.0, 4.0, 8.0, 16.0, 32.0)
+CANDIDATES = (4.0, 8.0, 16.0, 32.0, 64.0, 128.0)
 
 
 def geometry_class(g) -> str:

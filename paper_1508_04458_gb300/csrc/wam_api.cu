@@ -47,7 +47,7 @@ struct wam_ctx {
     unsigned long long* dwork = nullptr;   // device [WAM_NKERNEL]
     long long last_leaves = 0;             // leaves of the tree last planned
     // tuning
-    double back_ctas_per_sm = 8.0;         // back-projector work split: CTAs per SM per launch
+    double back_ctas_per_sm = 32.0;        // back-projector work split: CTAs per SM per launch
     cudaStream_t prof_stream = nullptr;
     int device = 0;
     int num_sms = 148;

@@ -314,22 +314,24 @@ def problem_fan512(seed: int = SEED_BASE + 1) -> Problem:
 
 
 def problem_fan(n: int, n_views: int, n_bins: int, I0: float, seed: int,
-                bin_pitch: Optional[float] = None, device=None) -> Problem:
+                bin_pitch: Optional[float] = None, device=None, sod: float = 1000.0,
+                sdd: float = 1500.0) -> Problem:
     """A fan-beam bag of any size; the detector covers the image's circumcircle."""
     if bin_pitch is None:
         # half-width of the shadow of the circumscribed circle, x1.03 margin
         r = n * math.sqrt(0.5)
-        half = 1500.0 * r / math.sqrt(1000.0 ** 2 - r * r) * 1.03
+        half = sdd * r / math.sqrt(sod ** 2 - r * r) * 1.03
         bin_pitch = 2.0 * half / n_bins
-    g = geom_fan(n, n_views, n_bins, bin_pitch=bin_pitch)
+    g = geom_fan(n, n_views, n_bins, bin_pitch=bin_pitch, sod=sod, sdd=sdd)
     return simulate("fan%d" % n, g, phantom_bag(seed, 0.5 * n), I0, seed, device=device)
 
 
 def batch_bags(n_bags: int = 32, seed0: int = SEED_BASE + 4, device=None, sizes=(256, 768),
                views=(360, 1440), bins=(512, 1536)) -> List[Problem]:
-    """Seeded bags of uneven size: side U{256..768} in steps of 16, views
-    U{360..1440}, bins U{512..1536}, I0 log-uniform in [1e4, 1e5]; bag i
-    uses seed seed0 + i."""
+    """Seeded bags of uneven size: side U{256..768} in steps of 16 (1 mm
+    pixels), views U{360..1440}, bins U{512..1536}, I0 log-uniform in
+    [1e4, 1e5]; bag i uses seed seed0 + i.  SOD 1000 mm, SDD 1600 mm, so the
+    detector stays outside the largest image's circumcircle (543 mm)."""
     out = []
     for i in range(n_bags):
         rng = np.random.Generator(np.random.PCG64(seed0 + i))
@@ -337,7 +339,7 @@ def batch_bags(n_bags: int = 32, seed0: int = SEED_BASE + 4, device=None, sizes=
         V = int(rng.integers(views[0], views[1] + 1))
         B = int(rng.integers(bins[0], bins[1] + 1))
         I0 = float(10.0 ** rng.uniform(4.0, 5.0))
-        out.append(problem_fan(n, V, B, I0, seed0 + i, device=device))
+        out.append(problem_fan(n, V, B, I0, seed0 + i, device=device, sdd=1600.0))
     return out
 
 
@@ -416,8 +418,12 @@ def ray_segments_3d(g: Geometry) -> np.ndarray:
 def _intervals_3d(shapes, P1, D, xp):
     """Entry/exit t in [0, 1] of every ray P1 + t D with every shape."""
     R = P1.shape[0]
-    t0 = xp.zeros((R, len(shapes)), dtype=P1.dtype)
-    t1 = xp.zeros((R, len(shapes)), dtype=P1.dtype)
+    if xp is np:
+        t0 = np.zeros((R, len(shapes)), dtype=P1.dtype)
+        t1 = np.zeros((R, len(shapes)), dtype=P1.dtype)
+    else:
+        t0 = xp.zeros((R, len(shapes)), dtype=P1.dtype, device=P1.device)
+        t1 = xp.zeros((R, len(shapes)), dtype=P1.dtype, device=P1.device)
     for k, sh in enumerate(shapes):
         px, py, pz = P1[:, 0] - sh.cx, P1[:, 1] - sh.cy, P1[:, 2] - sh.cz
         if sh.kind == "rod":
