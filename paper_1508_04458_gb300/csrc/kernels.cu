@@ -59,9 +59,32 @@ struct OpMax {
 // Beer's law and the I-divergence terms (Sec. II and its footnote).
 // One thread per ray; CTA = (bin tile, view).
 // ---------------------------------------------------------------------------
+// The two apron-padded copies the pixel walk reads: py = mu with a zero
+// border ((ny + 2) rows of nx + 2), px = its transpose with a zero border
+// ((nx + 2) rows of ny + 2).  One thread per padded pixel (x, y) in
+// [-1, nx] x [-1, ny]; both writes coalesced through a 32x32 shared tile.
+template <typename T>
+__global__ void k_pad2(const T* __restrict__ mu, int nx, int ny, T* __restrict__ py, T* __restrict__ px)
+{
+    __shared__ T tile[32][33];
+    const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int x = x0 + threadIdx.x, y = y0 + k;
+        T v = T(0);
+        if (x >= 0 && x < nx && y >= 0 && y < ny) v = mu[(size_t)y * nx + x];
+        tile[k][threadIdx.x] = v;
+        if (x <= nx && y <= ny) py[(size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int y = y0 + threadIdx.x, x = x0 + k;
+        if (x <= nx && y <= ny) px[(size_t)(x + 1) * (ny + 2) + (y + 1)] = tile[threadIdx.x][k];
+    }
+}
+
 template <typename T, bool PIX>
 __global__ void __launch_bounds__(kFwdTPB)
-k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
+k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
           const float* __restrict__ d, const double* __restrict__ dterm,
           const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
           T* __restrict__ resid, double* __restrict__ cost_part, unsigned long long* __restrict__ work)
@@ -75,10 +98,22 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const uint8_t* __restrict__ leaf,
         T acc = T(0);
         if (make_ray(g, v, b, r)) {
             if (PIX) {
-                traverse_pixels(g, r, [&](int ix, int iy, T c) {
-                    acc += c * __ldg(mu + iy * g.nx + ix);
-                    ++steps;
+                // y-major rays walk rows of the padded mu, x-major rays rows
+                // of the padded transpose.  Loads run one strip ahead of their
+                // use; the sum keeps the walk's order.
+                const bool ymaj = strip_major_y(g, r);
+                const T* img = ymaj ? pad : pad + (size_t)(g.nx + 2) * (g.ny + 2);
+                T pca = T(0), pva = T(0), pcb = T(0), pvb = T(0);
+                traverse_strips(g, r, ymaj, [&](int la, T ca, int lb, T cb) {
+                    const T va = __ldg(img + la), vb = __ldg(img + lb);
+                    acc += pca * pva;
+                    acc += pcb * pvb;
+                    pca = ca; pva = va;
+                    pcb = cb; pvb = vb;
+                    steps += (ca > T(0)) + (cb > T(0));
                 });
+                acc += pca * pva;
+                acc += pcb * pvb;
             } else {
                 traverse(g, leaf, r, [&](int ix, int iy, int, int, int, T c) {
                     acc += c * __ldg(mu + iy * g.nx + ix);
@@ -795,18 +830,24 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 template <typename T>
-cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d,
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, const float* d,
                            const double* dterm, const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st)
 {
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
-    COUNT_LAUNCH();
-    if (leaf)
-        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, resid, cost_part,
-                                                      work);
-    else
-        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, d, dterm, I0, qhat, p_out, resid, cost_part,
-                                                     work);
+    if (leaf) {
+        COUNT_LAUNCH();
+        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, d, dterm, I0, qhat, p_out, resid,
+                                                      cost_part, work);
+    } else {
+        if (!pad) return cudaErrorInvalidValue;
+        COUNT_LAUNCH();
+        k_pad2<T><<<dim3(nblk(g.nx + 2, 32), nblk(g.ny + 2, 32)), dim3(32, 8), 0, st>>>(
+            mu, g.nx, g.ny, pad, pad + (size_t)(g.nx + 2) * (g.ny + 2));
+        COUNT_LAUNCH();
+        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
+                                                     cost_part, work);
+    }
     return cudaGetLastError();
 }
 
@@ -1004,7 +1045,7 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
 
 // explicit instantiations
 #define WAM_INST(T)                                                                                              \
-    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, const uint8_t*, const float*, const double*, \
+    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, T*, const uint8_t*, const float*, const double*, \
                                            const float*, T*, T*, T*, double*, unsigned long long*, cudaStream_t); \
     template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \

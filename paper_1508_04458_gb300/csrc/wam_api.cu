@@ -26,7 +26,7 @@ enum BufId {
     B_Q, B_MU, B_BETA, B_BVEC, B_MASK_A, B_MASK_B, B_LEAF, B_LISTS, B_COUNTS,
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
-    B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER,
+    B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER, B_MUT,
     B_NBUF
 };
 
@@ -105,6 +105,12 @@ wam_status ensure_t(wam_ctx* c, BufId id, size_t count, P** out)
     WST(ensure(c, id, count * sizeof(P), &p));
     *out = static_cast<P*>(p);
     return WAM_OK;
+}
+
+// Elements of the pixel walk's two apron-padded image copies.
+size_t pad_elems(const wam_ctx* c)
+{
+    return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2);
 }
 
 // --- profiling ---------------------------------------------------------------
@@ -471,7 +477,7 @@ struct Run {
     long long N = 0, M = 0;
     Layout lay{};
     Geom<T> g{};
-    T *q = nullptr, *mu = nullptr, *sino = nullptr, *part = nullptr;
+    T *q = nullptr, *mu = nullptr, *mut = nullptr, *sino = nullptr, *part = nullptr;
     double *beta = nullptr, *bvec = nullptr, *costs = nullptr, *z0 = nullptr, *scratch = nullptr;
     double *tmpa = nullptr, *tmpb = nullptr, *gimg = nullptr, *cpart = nullptr;
     uint8_t *mask = nullptr, *mask2 = nullptr, *leaf = nullptr;
@@ -502,6 +508,7 @@ struct Run {
         M = c->M;
         WST(ensure_t(c, B_Q, (size_t)M, &q));
         WST(ensure_t(c, B_MU, (size_t)N, &mu));
+        WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
         WST(ensure_t(c, B_BETA, (size_t)N, &beta));
         WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
         WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
@@ -573,7 +580,7 @@ struct Run {
         }
         {
             PROF(WAM_K_FORWARD);                                                            // a2, a3
-            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+            WCK(c, launch_forward(g, mu, mut, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, np, costs + j, st));
@@ -624,7 +631,7 @@ struct Run {
         }
         {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_forward(g, mu, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+            WCK(c, launch_forward(g, mu, mut, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, np, costs + J, st));
@@ -680,7 +687,9 @@ wam_status project_impl(wam_ctx* c, const T* mu, T* p, void* stream)
     if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
     Geom<T> g;
     WST(make_geom<T>(c, &g));
-    WCK(c, launch_forward<T>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, nullptr,
+    T* mut = nullptr;
+    WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
+    WCK(c, launch_forward<T>(g, mu, mut, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, nullptr,
                              as_stream(stream)));
     return WAM_OK;
 }
@@ -736,7 +745,9 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
     const int np = forward_parts(g.V, g.B);
     double* cpart = nullptr;
     WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
-    WCK(c, launch_forward<T>(g, mu, leaf, static_cast<const float*>(c->buf[B_D].p),
+    T* mut = nullptr;
+    WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
+    WCK(c, launch_forward<T>(g, mu, mut, leaf, static_cast<const float*>(c->buf[B_D].p),
                              static_cast<const double*>(c->buf[B_DTERM].p),
                              static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr, cpart, nullptr,
                              st));
@@ -1597,7 +1608,9 @@ wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p,
         WST(coef_to_image(c, lay, beta, &mu, st));
         Geom<float> g;
         WST(make_geom<float>(c, &g));
-        WCK(c, launch_forward<float>(g, mu, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+        float* mut = nullptr;
+        WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
+        WCK(c, launch_forward<float>(g, mu, mut, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
                                      nullptr, st));
         return WAM_OK;
     } catch (...) {
@@ -1644,7 +1657,9 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
         float* res = nullptr;
         WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
         WST(ensure_t(c, B_GRES, (size_t)c->M, &res));
-        WCK(c, launch_forward<float>(g, mu, nullptr, static_cast<const float*>(c->buf[B_D].p),
+        float* mut = nullptr;
+        WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
+        WCK(c, launch_forward<float>(g, mu, mut, nullptr, static_cast<const float*>(c->buf[B_D].p),
                                      static_cast<const double*>(c->buf[B_DTERM].p),
                                      static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, res, cpart, nullptr,
                                      st));

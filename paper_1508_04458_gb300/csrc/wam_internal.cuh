@@ -208,6 +208,84 @@ __device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& 
     }
 }
 
+// Exact pixel walk by strips.  The ray's major axis is the one whose grid
+// lines it crosses most often per unit length (|d|/v larger), so within one
+// pixel strip across that axis it crosses at most one line of the other
+// axis: a strip holds one or two pixels.  Strips are visited in increasing
+// major coordinate, the two pixels of a strip in the same order.
+//
+// The minor coordinate is tracked in pixel units oriented along the ray's
+// minor travel and counted from the edge of the entry pixel c0
+// (u = +-(n - N0 - c0 v_minor) / v_minor), so the next grid line is the
+// integer fbo ahead and a crossing is u - fbo >= 0; the piece beyond it is
+// (u - fbo) v_minor / |d_minor| (no division in the loop).  Counting from c0
+// keeps u small for rays near an axis, whose crossing points are the most
+// sensitive to rounding in u.  The two partial end strips are peeled;
+// interior strips have the constant chord v_major / |d_major|.
+//
+// Pixels are addressed in an image with a one-pixel zero apron on every side,
+// (nm + 2) strips of (nn + 2): lin = (j + 1)(nn + 2) + (c + 1).  A step
+// across the image's minor edge (possible only in the exit strip, where the
+// ray leaves through that edge) lands on the apron and reads 0, so the walk
+// needs no range test; the apron also keeps any index the walk can form
+// inside the allocation.  visit(la, ca, lb, cb) once per strip: first pixel
+// and chord, second pixel and chord (cb = 0, lb = la for a one-pixel strip).
+template <typename T>
+__device__ __forceinline__ bool strip_major_y(const Geom<T>& g, const Ray<T>& r)
+{
+    return fabs(r.dy) * g.ivy >= fabs(r.dx) * g.ivx;
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& r, bool ymaj, F&& visit)
+{
+    const T pm = ymaj ? r.py : r.px, pn = ymaj ? r.px : r.py;
+    const T dm = ymaj ? r.dy : r.dx, dn = ymaj ? r.dx : r.dy;
+    const T vm = ymaj ? g.vy : g.vx, vn = ymaj ? g.vx : g.vy;
+    const T ivm = ymaj ? g.ivy : g.ivx, ivn = ymaj ? g.ivx : g.ivy;
+    const T M0 = ymaj ? g.Y0 : g.X0, N0 = ymaj ? g.X0 : g.Y0;
+    const int nm = ymaj ? g.ny : g.nx, nn = ymaj ? g.nx : g.ny;
+    const T sec = fabs(ymaj ? r.idy : r.idx);          // length per unit of major coordinate
+    const T vk = vn * fabs(ymaj ? r.idx : r.idy);      // length per minor pixel unit
+    const T slope = dn * (ymaj ? r.idy : r.idx);       // dn / dm
+    const T s_in = pm + r.tin * dm, s_out = pm + r.tout * dm;
+    const T s_lo = fmin(s_in, s_out), s_hi = fmax(s_in, s_out);
+    const T n0 = pn - pm * slope;                      // minor coordinate at major 0
+    const bool up = slope >= T(0);
+    const int j0 = clampi((int)floor((s_lo - M0) * ivm), 0, nm - 1);
+    const int j1 = clampi((int)floor((s_hi - M0) * ivm), 0, nm - 1);
+    const int c0 = clampi((int)floor((fma(s_lo, slope, n0) - N0) * ivn), 0, nn - 1);
+    const T Nc = fma(T(c0), vn, N0);                   // lower edge of the entry pixel
+    const T G = fabs(slope) * ivn;                     // oriented minor units per unit major
+    const T U0 = (up ? n0 - Nc : Nc - n0) * ivn;       // u at major 0
+    const int sM = nn + 2, dlin = up ? 1 : -1;
+    T fbo = up ? T(1) : T(0);                          // next minor grid line, oriented
+    int lin = (j0 + 1) * sM + c0 + 1;
+    auto strip = [&](T chord, T u) {
+        const T e = u - fbo;
+        const bool cross = e >= T(0);
+        const T cb = cross ? fmin(e * vk, chord) : T(0);
+        const int lb = cross ? lin + dlin : lin;
+        visit(lin, chord - cb, lb, cb);
+        fbo = cross ? fbo + T(1) : fbo;
+        lin = lb + sM;
+    };
+    if (j1 == j0) {
+        strip((s_hi - s_lo) * sec, fma(s_hi, G, U0));
+        return;
+    }
+    const T A = fma(G, M0, U0), D = G * vm;            // u at the end of strip j: A + (j + 1) D
+    T fj = T(j0 + 1);
+    strip(fmax(fma(fj, vm, M0) - s_lo, T(0)) * sec, fma(fj, D, A));
+    const T full = vm * sec;
+#pragma unroll 2
+    for (int k = j1 - j0 - 1; k > 0; --k) {
+        fj += T(1);
+        strip(full, fma(fj, D, A));
+    }
+    strip(fmax(s_hi - fma(T(j1), vm, M0), T(0)) * sec, fma(s_hi, G, U0));
+}
+
 // ---------------------------------------------------------------------------
 // closed-form chords through an axis-aligned block, in block-local
 // coordinates: (qx, qy) a point of the ray relative to the block centre,

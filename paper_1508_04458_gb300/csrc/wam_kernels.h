@@ -6,7 +6,9 @@
 namespace wam {
 
 template <typename T>
-cudaError_t launch_forward(const Geom<T>& g, const T* mu, const uint8_t* leaf, const float* d, const double* dterm,
+// pad: scratch of 2 (nx + 2)(ny + 2) elements, required when leaf is null
+// (the pixel walk reads apron-padded copies of mu written there).
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, const float* d, const double* dterm,
                            const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st);
 int forward_parts(int V, int B);
