@@ -267,12 +267,13 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
                 umin = fminf(umin, uu); umax = fmaxf(umax, uu);
                 vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
             }
-            const int blo = max(0, (int)floorf(umin * ipitch + g.ucen - 1e-4f));
-            const int bhi = min(g.B - 1, (int)ceilf(umax * ipitch + g.ucen + 1e-4f));
-            const int rlo = max(0, (int)floorf(vmin * irp + g.rcen - 1e-4f));
-            const int rhi = min(g.R - 1, (int)ceilf(vmax * irp + g.rcen + 1e-4f));
+            // the bins and rows whose rays pass through the shadow; a margin of
+            // 1e-3 bin (row) covers the fast division's rounding
+            const int blo = max(0, (int)ceilf(umin * ipitch + g.ucen - 1e-3f));
+            const int bhi = min(g.B - 1, (int)floorf(umax * ipitch + g.ucen + 1e-3f));
+            const int rlo = max(0, (int)ceilf(vmin * irp + g.rcen - 1e-3f));
+            const int rhi = min(g.R - 1, (int)floorf(vmax * irp + g.rcen + 1e-3f));
             if (blo > bhi || rlo > rhi) continue;
-            evals += (unsigned)((bhi - blo + 1) * (rhi - rlo + 1));
             const float kappa = (g.sod - ac) * isdd;
             const float4* drow = g.dirt + (size_t)v * g.B;
             for (int rr = rlo; rr <= rhi; ++rr) {
@@ -308,6 +309,7 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
                         const float ch = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh) -
                                                fmaxf(fmaxf(a - Ax, b - Ay), zsl), 0.0f);
                         acc[0] += q * ch;
+                        if (work) evals += ch > 0.0f;
                     } else if (mode == 2) {
                         // quadrants of the block within the slice's z slab
                         const float zl = zsl, zh = zsh;
@@ -320,6 +322,7 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
                             for (int i = 0; i < 2; ++i)
                                 w[i + 2 * j] = fmaxf(fminf(fminf(xh[i], yh[j]), zh) - fmaxf(fmaxf(xl[i], yl[j]), zl),
                                                      0.0f);
+                        if (work) evals += (w[0] > 0.0f) + (w[1] > 0.0f) + (w[2] > 0.0f) + (w[3] > 0.0f);
                         // Walsh-Hadamard over (x, y): t = 1 x, 2 y, 3 xy; + on the lower halves
                         const float s1 = w[0] + w[1], s2 = w[2] + w[3], d1 = w[0] - w[1], d2 = w[2] - w[3];
                         acc[0] += q * (s1 + s2);
@@ -347,8 +350,11 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
                             for (int i = 0; i < 2; ++i) {
                                 const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
 #pragma unroll
-                                for (int k = 0; k < 2; ++k)
-                                    acc[i + 2 * j + 4 * k] += q * fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                                for (int k = 0; k < 2; ++k) {
+                                    const float ch = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                                    acc[i + 2 * j + 4 * k] += q * ch;
+                                    if (work) evals += ch > 0.0f;
+                                }
                             }
                     } else {
                         const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
@@ -364,6 +370,10 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
                                 for (int k = 0; k < 2; ++k)
                                     w[i + 2 * j + 4 * k] = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
                             }
+                        if (work) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) evals += w[i] > 0.0f;
+                        }
                         // in-place Walsh-Hadamard transform over (x, y, z)
 #pragma unroll
                         for (int h = 1; h < 8; h <<= 1)
@@ -389,7 +399,7 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
             }
         }
     }
-    add_work3(work, mode == 1 ? 8u * evals : (mode == 2 ? 4u * evals : evals));
+    add_work3(work, evals);
 #pragma unroll
     for (int k = 0; k < kSlots3; ++k) red[wv][k][lane] = acc[k];
     __syncthreads();
@@ -480,7 +490,7 @@ __device__ __forceinline__ double am_delta64(double b, double bp, double bm, dou
     return t / z0;
 }
 
-__device__ __forceinline__ double am_delta32(double b, float bp, float bm, double z0, double clamp)
+__device__ __forceinline__ double am_delta32(double b, float bp, float bm, double z0, float iz0, double clamp)
 {
     const float bf = (float)b;
     if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta64(b, bp, bm, z0, clamp);
@@ -495,43 +505,43 @@ __device__ __forceinline__ double am_delta32(double b, float bp, float bm, doubl
         t = 0.0f;
     }
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
-    return (double)t / z0;
+    return (double)(t * iz0);
 }
 
+// One thread per coefficient: thread 8 i + k of item i takes voxel k of an
+// octet, or (k = 0) the approximation and (k = 1..7) detail type k of a block
+// (types 1..3 only for the per-slice 2-D tree).
 __global__ void k_update3(SegTable3 tab, Layout3 lay, const float* __restrict__ part, const double* __restrict__ bvec,
                           const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= tab.total_items) return;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 8LL * tab.total_items) return;
+    const int it = (int)(gid >> 3), k = (int)(gid & 7);
     int si = 0;
-    while (si + 1 < tab.n && gid >= tab.s[si + 1].item_begin) ++si;
+    while (si + 1 < tab.n && it >= tab.s[si + 1].item_begin) ++si;
     const Segment3& S = tab.s[si];
-    const int item = gid - S.item_begin;
+    const int item = it - S.item_begin;
     int bx, by, bz;
     decode3(S, item, bx, by, bz);
     const double z0 = *z0p;
+    const float iz0 = 1.0f / (float)z0;
     if (S.octet) {
-        for (int k = 0; k < 8; ++k) {
-            const long long z = ((long long)(2 * bz + (k >> 2)) * lay.ny + 2 * by + ((k >> 1) & 1)) * lay.nx +
-                                2 * bx + (k & 1);
-            beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, k), 0.0f, z0, clamp);
-        }
+        const long long z = ((long long)(2 * bz + (k >> 2)) * lay.ny + 2 * by + ((k >> 1) & 1)) * lay.nx +
+                            2 * bx + (k & 1);
+        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, k), 0.0f, z0, iz0, clamp);
         return;
     }
-    int slot = 0;
-    if (S.has_approx) {
+    if (k == 0) {
+        if (!S.has_approx) return;
         const long long z = approx3(lay, bx, by, bz);
-        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, 0), 0.0f, z0, clamp);
-        slot = 1;
+        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, 0), 0.0f, z0, iz0, clamp);
+        return;
     }
-    if (S.has_details) {
-        const int ndet = lay.z3 ? 7 : 3;
-        for (int t = 1; t <= ndet; ++t) {
-            const long long z = detail3(lay, S.level, t, bx, by, bz);
-            beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, slot + 2 * (t - 1)),
-                                  sum_slot3(S, part, item, slot + 2 * (t - 1) + 1), z0, clamp);
-        }
-    }
+    if (!S.has_details || k > (lay.z3 ? 7 : 3)) return;
+    const int slot = (S.has_approx ? 1 : 0) + 2 * (k - 1);
+    const long long z = detail3(lay, S.level, k, bx, by, bz);
+    beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, slot), sum_slot3(S, part, item, slot + 1), z0, iz0,
+                          clamp);
 }
 
 cudaError_t launch_update3(const SegTable3& tab, const Layout3& lay, const float* part, const double* b,
@@ -539,7 +549,7 @@ cudaError_t launch_update3(const SegTable3& tab, const Layout3& lay, const float
 {
     if (tab.total_items == 0) return cudaSuccess;
     count_launch();
-    k_update3<<<nb(tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    k_update3<<<nb(8LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
     return cudaGetLastError();
 }
 

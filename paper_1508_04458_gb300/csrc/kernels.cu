@@ -332,13 +332,13 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
                 umin = fmin(umin, uu);
                 umax = fmax(umax, uu);
             }
-            // a margin of 1e-4 bin covers the fast division's rounding
-            const int blo = max(0, (int)floor(umin * ipitch + g.ucen - T(1e-4)));
-            const int bhi = min(g.B - 1, (int)ceil(umax * ipitch + g.ucen + T(1e-4)));
+            // the rays through the shadow (umin, umax); a margin of 1e-3 bin
+            // covers the fast division's rounding (~1e-4 bin at the detector edge)
+            const int blo = max(0, (int)ceil(umin * ipitch + g.ucen - T(1e-3)));
+            const int bhi = min(g.B - 1, (int)floor(umax * ipitch + g.ucen + T(1e-3)));
             const T kappa = fan ? (g.sod - ac) * isdd : T(1);
             const T* row = sino + (size_t)v * g.B;
             const typename Vec4<T>::type* drow = dirtab ? dirtab + (size_t)v * g.B : nullptr;
-            evals += (unsigned)max(0, bhi - blo + 1);
             T fb = T(blo);
             for (int bb = blo; bb <= bhi; ++bb, fb += T(1)) {
                 const T ub = fb * g.pitch + u0;
@@ -360,44 +360,40 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
                     dd.y = -c * dd.w;
                 }
                 const T a = delta * dd.x, b = delta * dd.y;
-                const T Ax = hx * fabs(dd.z), Ay = hy * fabs(dd.w);
                 const T q = __ldg(row + bb);
-                if (quad) {
-                    // pixel basis: the four pixels' chords in physical order (sums of
-                    // non-negative terms); the half crossed first is the lower one
-                    // when the direction along that axis is positive
-                    T cFF, cFS, cSF, cSS;
-                    child_chords_ab(a, b, Ax, Ay, cFF, cFS, cSF, cSS);
-                    const bool px = dd.z > T(0), py = dd.w > T(0);
-                    const T xlyl = px ? (py ? cFF : cFS) : (py ? cSF : cSS);
-                    const T xhyl = px ? (py ? cSF : cSS) : (py ? cFF : cFS);
-                    const T xlyh = px ? (py ? cFS : cFF) : (py ? cSS : cSF);
-                    const T xhyh = px ? (py ? cSS : cSF) : (py ? cFS : cFF);
-                    aA += q * xlyl;
-                    hP += q * xhyl;
-                    hM += q * xlyh;
-                    vP += q * xhyh;
-                } else if (four) {
-                    T cFF, cFS, cSF, cSS;
-                    child_chords_ab(a, b, Ax, Ay, cFF, cFS, cSF, cSS);
-                    const T qs = q * scale;
-                    const T xF = cFF + cFS, xS = cSF + cSS;      // first / second x half
-                    const T yF = cFF + cSF, yS = cFS + cSS;
-                    aA += qs * (xF + xS);
-                    // lower half minus upper half, by the travel direction's signs
-                    const T ph = qs * flip(yF - yS, dd.w);
-                    const T pv = qs * flip(xF - xS, dd.z);
-                    const T pd = qs * flip2((cFF + cSS) - (cFS + cSF), dd.z, dd.w);
-                    if (ph > T(0)) hP += ph; else hM += ph;
-                    if (pv > T(0)) vP += pv; else vM += pv;
-                    if (pd > T(0)) dP += pd; else dM += pd;
+                if (four) {
+                    // chords of the four children (pixels of a quad) in physical order
+                    T cll, chl, clh, chh;
+                    child_chords_phys(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
+                    if (work) evals += (cll > T(0)) + (chl > T(0)) + (clh > T(0)) + (chh > T(0));
+                    if (quad) {
+                        // pixel basis: pixel (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) sums
+                        aA += q * cll;
+                        hP += q * chl;
+                        hM += q * clh;
+                        vP += q * chh;
+                    } else {
+                        // Haar split: lower half minus upper half along y (h), x (v),
+                        // and the diagonal pair minus the anti-diagonal pair (d)
+                        const T qs = q * scale;
+                        const T yl = cll + chl, yh = clh + chh;
+                        aA += qs * (yl + yh);
+                        const T ph = qs * (yl - yh);
+                        const T pv = qs * ((cll + clh) - (chl + chh));
+                        const T pd = qs * ((cll + chh) - (chl + clh));
+                        if (ph > T(0)) hP += ph; else hM += ph;
+                        if (pv > T(0)) vP += pv; else vM += pv;
+                        if (pd > T(0)) dP += pd; else dM += pd;
+                    }
                 } else {
-                    aA += q * scale * block_chord_ab(a, b, Ax, Ay);
+                    const T ch = block_chord_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w));
+                    aA += q * scale * ch;
+                    if (work) evals += ch > T(0);
                 }
             }
         }
     }
-    add_work(work, four ? 4u * evals : evals);
+    add_work(work, evals);
     // fixed-order sum of the 8 view lanes, one partial per (item, view range)
     red[wv][0][lane] = aA;
     red[wv][1][lane] = hP; red[wv][2][lane] = hM;
@@ -497,10 +493,10 @@ __device__ __forceinline__ double am_delta(double b, double bp, double bm, doubl
     return t / z0;
 }
 
-// The same root in FP32.  Where the counts are near zero (the data weight b
-// is below 1e-3 of the model weight bp - bm, e.g. rays behind metal) the log
-// ratio is taken in FP64 instead.
-__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, double clamp)
+// The same root in FP32 (iz0 = 1 / Z0 in FP32).  Where the counts are near
+// zero (the data weight b is below 1e-3 of the model weight bp - bm, e.g.
+// rays behind metal) the log ratio is taken in FP64 instead.
+__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp)
 {
     const float bf = (float)b;
     if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta(b, (double)bp, (double)bm, z0, clamp);
@@ -515,54 +511,52 @@ __device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, dou
         t = 0.0f;
     }
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
-    return (double)t / z0;
+    return (double)(t * iz0);
 }
 
-__device__ __forceinline__ double am_step(double b, float bp, float bm, double z0, double clamp)
+__device__ __forceinline__ double am_step(double b, float bp, float bm, double z0, float iz0, double clamp)
 {
-    return am_delta_f32(b, bp, bm, z0, clamp);
+    return am_delta_f32(b, bp, bm, z0, iz0, clamp);
 }
 
-__device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, double clamp)
+__device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, float, double clamp)
 {
     return am_delta(b, bp, bm, z0, clamp);
 }
 
-// a6: reduce the partials of each item and apply the AM update to beta.
+// a6: reduce the partials of each item and apply the AM update to beta.  One
+// thread per coefficient: thread 4 i + k of item i takes pixel k of a quad,
+// or (k = 0) the approximation and (k = 1..3) detail type k of a block.
 template <typename T>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= tab.total_items) return;
-    const Segment& S = tab.s[find_item_segment(tab, gid)];
-    const int item = gid - S.item_begin;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 4LL * tab.total_items) return;
+    const int it = (int)(gid >> 2), k = (int)(gid & 3);
+    const Segment& S = tab.s[find_item_segment(tab, it)];
+    const int item = it - S.item_begin;
     int bx, by;
     item_block(S, item, bx, by);
     const double z0 = *z0p;
+    const float iz0 = 1.0f / (float)z0;
     if (S.quad) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
-            beta[z] += am_step(bvec[z], sum_slot(S, part, item, k), T(0), z0, clamp);
-        }
+        const long long z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
+        beta[z] += am_step(bvec[z], sum_slot(S, part, item, k), T(0), z0, iz0, clamp);
         return;
     }
-    int slot = 0;
-    if (S.has_approx) {
+    if (k == 0) {
+        if (!S.has_approx) return;
         const long long z = approx_index(lay, S.level, bx, by);
-        beta[z] += am_step(bvec[z], sum_slot(S, part, item, 0), T(0), z0, clamp);
-        slot = 1;
+        beta[z] += am_step(bvec[z], sum_slot(S, part, item, 0), T(0), z0, iz0, clamp);
+        return;
     }
-    if (S.has_details) {
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const long long z = detail_index(lay, S.level, t, bx, by);
-            const T bp = sum_slot(S, part, item, slot + 2 * t);
-            const T bm = sum_slot(S, part, item, slot + 2 * t + 1);
-            beta[z] += am_step(bvec[z], bp, bm, z0, clamp);
-        }
-    }
+    if (!S.has_details) return;
+    const int t = k - 1, slot = (S.has_approx ? 1 : 0) + 2 * t;
+    const long long z = detail_index(lay, S.level, t, bx, by);
+    const T bp = sum_slot(S, part, item, slot);
+    const T bm = sum_slot(S, part, item, slot + 1);
+    beta[z] += am_step(bvec[z], bp, bm, z0, iz0, clamp);
 }
 
 // Scatter the reduced bhat+ / bhat- of each item into coefficient layout.
@@ -900,7 +894,7 @@ cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part,
 {
     if (tab.total_items == 0) return cudaSuccess;
     COUNT_LAUNCH();
-    k_update<T><<<nblk(tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    k_update<T><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
     return cudaGetLastError();
 }
 

@@ -337,6 +337,26 @@ __device__ __forceinline__ T block_chord_ab(T a, T b, T Ax, T Ay)
     return fmax(fmin(a + Ax, b + Ay) - fmax(a - Ax, b - Ay), T(0));
 }
 
+// Chords of a ray through the four children of a block in physical order
+// (l/h: lower/upper half along x, then y).  a, b: the ray parameters where it
+// crosses the block's centre lines x = cx, y = cy; ix = 1/dx, iy = 1/dy
+// (signed); Hx, Hy: half the block's half-sizes.  The child on the lower-x
+// side spans the parameters between the lines x = cx - 2 Hx and x = cx, i.e.
+// [a - Hx (|ix| + ix), a + Hx (|ix| - ix)] whatever the sign of dx, so no
+// selects are needed.
+template <typename T>
+__device__ __forceinline__ void child_chords_phys(T a, T b, T Hx, T Hy, T ix, T iy, T& cll, T& chl, T& clh,
+                                                  T& chh)
+{
+    const T ux = fabs(ix) + ix, wx = fabs(ix) - ix, uy = fabs(iy) + iy, wy = fabs(iy) - iy;
+    const T xl0 = fma(-Hx, ux, a), xl1 = fma(Hx, wx, a), xh0 = fma(-Hx, wx, a), xh1 = fma(Hx, ux, a);
+    const T yl0 = fma(-Hy, uy, b), yl1 = fma(Hy, wy, b), yh0 = fma(-Hy, wy, b), yh1 = fma(Hy, uy, b);
+    cll = fmax(fmin(xl1, yl1) - fmax(xl0, yl0), T(0));
+    chl = fmax(fmin(xh1, yl1) - fmax(xh0, yl0), T(0));
+    clh = fmax(fmin(xl1, yh1) - fmax(xl0, yh0), T(0));
+    chh = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
+}
+
 template <typename T>
 __device__ __forceinline__ void child_chords_ab(T a, T b, T Ax, T Ay, T& cFF, T& cFS, T& cSF, T& cSS)
 {
