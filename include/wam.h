@@ -73,6 +73,7 @@ typedef enum {
     WAM_ERR_CUDA = -3,     /* a CUDA call failed */
     WAM_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
     WAM_ERR_STATE = -5,    /* call order violated (e.g. no data set) */
+    WAM_ERR_IO = -6,       /* a checkpoint file could not be written, read or verified */
     WAM_WARN_NONMONOTONE = 1 /* reconstruction finished, but the cost rose
                                 by more than the rounding band at least once */
 } wam_status;
@@ -178,6 +179,43 @@ wam_status wam_reconstruct(wam_ctx* ctx, const wam_schedule* sched, void* mu_out
 wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule* sched,
                                  void* const* mu_out, double* const* hist, int on_device,
                                  int use_graph, void* stream);
+
+/* ---- checkpoint / resume ------------------------------------------------- */
+
+/* Algorithm 1 is a fixed-point iteration whose whole state after iteration j
+ * is the coefficient vector beta^(j), the tree of active coefficients and the
+ * expansions applied so far (b = Phi^T d and Z0 follow from the data and the
+ * tree).  wam_checkpoint writes that state for the context's last finished
+ * wam_reconstruct (2-D or cone beam): beta (FP64), the tree masks, the cost
+ * history I(d || qhat^(0..j)), the schedule it ran, the geometry, CRC-32
+ * fingerprints of d and I0, and the back-projector tuning value; the file ends
+ * with a CRC-32 of its contents and is written to "<path>.tmp" and renamed.
+ * Format (little endian): "WAMCKPT1", u32 version 1, u32 0; 20 int64 (kind,
+ * nx, ny, nz, n_views, n_bins, n_rows, levels, dims, zsum_criterion,
+ * precision, full_am, n_expand, iterations done, expansions done, N,
+ * mask bytes, history length, crc(d), crc(I0)); 11 double (vx, vy, vz,
+ * angle0, angle_span, bin_pitch, row_pitch, sod, sdd, dmax_clamp, tuning);
+ * int64 expand_at[n_expand]; double tau[n_expand]; double beta[N];
+ * u8 masks[mask bytes]; double history[iterations done + 1]; u32 crc.
+ * Errors: WAM_ERR_STATE if no reconstruction has finished on ctx since its
+ * data were set; WAM_ERR_IO if the file cannot be written. */
+wam_status wam_checkpoint(wam_ctx* ctx, const char* path);
+
+/* Load a checkpoint into ctx; the next wam_reconstruct on ctx continues from
+ * it: it runs iterations j..n_iters - 1 (j = iterations done) and applies the
+ * schedule's remaining expansions, and its outputs (image, the full cost
+ * history 0..n_iters, tree) equal those of one uninterrupted run bit for bit.
+ * The context's back-projector tuning is set to the checkpoint's.  Requires
+ * data set (wam_set_data) equal to the checkpoint's (CRC-32 of d and I0) and
+ * an equal geometry; the continuing schedule must have the same levels, dims,
+ * zsum_criterion, precision, full_am and dmax_clamp, n_iters >= j, and the
+ * same first expansions (those applied so far) with no other expansion at or
+ * before j, else that wam_reconstruct returns WAM_ERR_STATE and the loaded
+ * state stays pending.  wam_set_data discards a pending state.
+ * wam_reconstruct_batch refuses contexts with a pending state (WAM_ERR_STATE).
+ * Errors: WAM_ERR_IO for an unreadable, truncated or corrupt file (bad magic,
+ * version or CRC); WAM_ERR_STATE for no data or a geometry or data mismatch. */
+wam_status wam_resume(wam_ctx* ctx, const char* path);
 
 /* Tuning knobs (set by the caller or by an autotuner that times them). */
 enum {

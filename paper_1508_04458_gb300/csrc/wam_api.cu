@@ -37,8 +37,24 @@ struct ProfPending {
     cudaEvent_t a, b;
 };
 
+// Algorithm 1's state after a run (for wam_checkpoint) or loaded from a file
+// (wam_resume, consumed by the next wam_reconstruct).
+struct RunRecord {
+    bool valid = false;
+    int levels = 0, dims = 2, zsum = 0, precision = 32, full_am = 0;
+    double clamp = 30.0;
+    std::vector<int> expand_at;
+    std::vector<double> tau;
+    int iters_done = 0, expansions_done = 0;
+    double tuning = 32.0;
+    std::vector<double> beta, hist;     // host copies (loaded state only)
+    std::vector<uint8_t> mask;
+};
+
 struct wam_ctx {
     wam_geometry g{};
+    RunRecord last;                        // last finished reconstruction (device buffers hold its arrays)
+    RunRecord pending;                     // state loaded by wam_resume
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -111,6 +127,55 @@ wam_status ensure_t(wam_ctx* c, BufId id, size_t count, P** out)
 size_t pad_elems(const wam_ctx* c)
 {
     return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2);
+}
+
+// --- run state ---------------------------------------------------------------
+double eff_clamp(const wam_schedule* sc) { return sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0; }
+
+int eff_dims(const wam_ctx* c, const wam_schedule* sc)
+{
+    return c->g.kind == WAM_CONE3D_FLAT_CIRCULAR ? sc->dims : 2;
+}
+
+void record_run(wam_ctx* c, const wam_schedule* sc, int iters, int expansions)
+{
+    RunRecord& r = c->last;
+    r = RunRecord{};
+    r.valid = true;
+    r.levels = sc->full_am ? 0 : sc->levels;
+    r.dims = eff_dims(c, sc);
+    r.zsum = sc->zsum_criterion;
+    r.precision = sc->precision;
+    r.full_am = sc->full_am;
+    r.clamp = eff_clamp(sc);
+    r.expand_at.assign(sc->expand_at, sc->expand_at + sc->n_expand);
+    r.tau.assign(sc->tau, sc->tau + sc->n_expand);
+    r.iters_done = iters;
+    r.expansions_done = expansions;
+    r.tuning = c->back_ctas_per_sm;
+    c->pending = RunRecord{};
+}
+
+// A schedule may continue the pending state when it ran the same method and
+// the same expansions up to the iterations done.
+wam_status check_resume(wam_ctx* c, const wam_schedule* sc)
+{
+    const RunRecord& r = c->pending;
+    if (!r.valid) return WAM_OK;
+    const int L = sc->full_am ? 0 : sc->levels;
+    if (L != r.levels || sc->full_am != r.full_am || sc->precision != r.precision || eff_dims(c, sc) != r.dims ||
+        sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp)
+        return fail(c, WAM_ERR_STATE, "resume: the schedule's method differs from the checkpoint's");
+    if (sc->n_iters < r.iters_done) return fail(c, WAM_ERR_STATE, "resume: n_iters is below the iterations done");
+    if (L > 0) {
+        if (sc->n_expand < r.expansions_done) return fail(c, WAM_ERR_STATE, "resume: fewer expansions than done");
+        for (int k = 0; k < r.expansions_done; ++k)
+            if (sc->expand_at[k] != r.expand_at[k] || sc->tau[k] != r.tau[k])
+                return fail(c, WAM_ERR_STATE, "resume: the expansions done differ from the schedule's");
+        if (sc->n_expand > r.expansions_done && sc->expand_at[r.expansions_done] <= r.iters_done)
+            return fail(c, WAM_ERR_STATE, "resume: the schedule expands at or before the iterations done");
+    }
+    return WAM_OK;
 }
 
 // --- profiling ---------------------------------------------------------------
@@ -489,6 +554,7 @@ struct Run {
     const uint8_t* fwd_leaf = nullptr;
     std::vector<int> exp_at;
     size_t next_exp = 0;
+    int j0 = 0;                 // first iteration to run (> 0 when resuming)
 
     // The leaf walk pays per leaf what the pixel walk pays per pixel, about
     // 2.5 times over; once leaves average fewer than 4 pixels the image mu
@@ -567,6 +633,30 @@ struct Run {
         exp_at.assign(sc->n_expand > 0 ? sc->expand_at : nullptr,
                       sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
         next_exp = 0;
+        j0 = 0;
+        if (c->pending.valid) WST(load_pending(st));
+        return WAM_OK;
+    }
+
+    // continue from the state of wam_resume: beta, the tree (its block lists
+    // and Z0 rebuilt), the cost history so far and the expansions done
+    wam_status load_pending(cudaStream_t st)
+    {
+        const RunRecord& r = c->pending;
+        if (r.beta.size() != (size_t)N || r.hist.size() != (size_t)r.iters_done + 1 ||
+            r.mask.size() != (L > 0 ? (size_t)lay.mask_bytes : 0))
+            return fail(c, WAM_ERR_STATE, "resume: the checkpoint's sizes do not fit this schedule");
+        WCK(c, cudaMemcpyAsync(beta, r.beta.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        WCK(c, cudaMemcpyAsync(costs, r.hist.data(), r.hist.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (L > 0) {
+            WCK(c, cudaMemcpyAsync(mask, r.mask.data(), lay.mask_bytes, cudaMemcpyHostToDevice, st));
+            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
+            fwd_leaf = pick_leaf();
+            PROF(WAM_K_Z0);
+            WST(compute_z0<T>(c, g, lay, leaf, z0, st));
+        }
+        next_exp = (size_t)r.expansions_done;
+        j0 = r.iters_done;
         return WAM_OK;
     }
 
@@ -665,9 +755,11 @@ template <typename T>
 wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
                             int on_device, cudaStream_t st)
 {
+    WST(check_resume(c, sc));
+    c->last.valid = false;
     Run<T> run;
     WST(run.setup(c, sc, st));
-    for (int j = 0; j < run.J; ++j) {
+    for (int j = run.j0; j < run.J; ++j) {
         WST(run.iteration(j, st, false));
         if (run.expands_after(j)) WST(run.expand(st));
     }
@@ -676,6 +768,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     WST(run.copy_out(mu_out, hist, mask_out, on_device, &h, st));
     WCK(c, cudaStreamSynchronize(st));
     if (c->prof) WST(prof_resolve(c));
+    record_run(c, sc, run.J, (int)run.next_exp);
     return run.monotone(h);
 }
 
@@ -941,6 +1034,8 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
                              unsigned char* mask_out, int on_device, cudaStream_t st)
 {
     if (sc->precision != 32) return fail(c, WAM_ERR_ARG, "cone beam: precision 32 only");
+    WST(check_resume(c, sc));
+    c->last.valid = false;
     const int L = sc->full_am ? 0 : sc->levels;
     int z3 = 1;
     if (!sc->full_am && L > 0) {
@@ -1012,7 +1107,26 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
     std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
                             sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
     size_t next_exp = 0;
-    for (int j = 0; j <= J; ++j) {
+    int j0 = 0;
+    if (c->pending.valid) {
+        // continue from the state of wam_resume (as in the 2-D driver)
+        const RunRecord& r = c->pending;
+        if (r.beta.size() != (size_t)N || r.hist.size() != (size_t)r.iters_done + 1 ||
+            r.mask.size() != (L > 0 ? (size_t)lay.mask_bytes : 0))
+            return fail(c, WAM_ERR_STATE, "resume: the checkpoint's sizes do not fit this schedule");
+        WCK(c, cudaMemcpyAsync(beta, r.beta.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        WCK(c, cudaMemcpyAsync(costs, r.hist.data(), r.hist.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (L > 0) {
+            WCK(c, cudaMemcpyAsync(mask, r.mask.data(), lay.mask_bytes, cudaMemcpyHostToDevice, st));
+            WST(plan_tree3(c, lay, mask, leaf, &tab, &part, &leaves, st));
+            fleaf = pick();
+            PROF(WAM_K_Z0);
+            WST(compute_z03(c, g, lay, leaf, z0, st));
+        }
+        next_exp = (size_t)r.expansions_done;
+        j0 = r.iters_done;
+    }
+    for (int j = j0; j <= J; ++j) {
         {
             PROF(WAM_K_SYNTH);
             WCK(c, launch_synth3(lay, leaf, beta, mu, st));
@@ -1059,10 +1173,80 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
     if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
     WCK(c, cudaStreamSynchronize(st));
     if (c->prof) WST(prof_resolve(c));
+    record_run(c, sc, J, (int)next_exp);
     for (int j = 0; j < J; ++j)
         if (h[j + 1] > h[j] + 1e-6 * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
     return WAM_OK;
 }
+
+// ---- checkpoint files ----------------------------------------------------------
+// CRC-32 (the reflected IEEE 802.3 polynomial 0xEDB88320, initial value and
+// final xor 0xFFFFFFFF), byte-wise with a 256-entry table.
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n)
+{
+    static uint32_t table[256];
+    static bool ready = false;
+    if (!ready) {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t r = i;
+            for (int k = 0; k < 8; ++k) r = (r & 1u) ? (r >> 1) ^ 0xEDB88320u : r >> 1;
+            table[i] = r;
+        }
+        ready = true;
+    }
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xffu] ^ (crc >> 8);
+    return ~crc;
+}
+
+// CRC-32 of the context's d and I0 (device copies read back)
+wam_status data_crc(wam_ctx* c, uint32_t* cd, uint32_t* ci)
+{
+    std::vector<float> h((size_t)c->M);
+    WCK(c, cudaMemcpy(h.data(), c->buf[B_D].p, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    *cd = crc32_update(0, h.data(), h.size() * sizeof(float));
+    WCK(c, cudaMemcpy(h.data(), c->buf[B_I0].p, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    *ci = crc32_update(0, h.data(), h.size() * sizeof(float));
+    return WAM_OK;
+}
+
+struct CkptWriter {
+    std::vector<unsigned char> b;
+    void raw(const void* p, size_t n)
+    {
+        const unsigned char* q = static_cast<const unsigned char*>(p);
+        b.insert(b.end(), q, q + n);
+    }
+    void i64(long long v)
+    {
+        const int64_t x = v;
+        raw(&x, 8);
+    }
+    void f64(double v) { raw(&v, 8); }
+};
+
+struct CkptReader {
+    const unsigned char* p;
+    size_t n, at = 0;
+    bool raw(void* dst, size_t k)
+    {
+        if (k > n - at) return false;
+        std::memcpy(dst, p + at, k);
+        at += k;
+        return true;
+    }
+    bool i64(long long* v)
+    {
+        int64_t x;
+        if (!raw(&x, 8)) return false;
+        *v = x;
+        return true;
+    }
+    bool f64(double* v) { return raw(v, 8); }
+};
+
+const char kCkptMagic[8] = {'W', 'A', 'M', 'C', 'K', 'P', 'T', '1'};
 
 }  // namespace
 
@@ -1168,6 +1352,8 @@ wam_status wam_set_data(wam_ctx* c, const float* d, const float* I0, int I0_is_s
         WCK(c, launch_dterm(dd, ii, M, dt, st));
         WCK(c, cudaStreamSynchronize(st));
         c->has_data = true;
+        c->last = RunRecord{};
+        c->pending = RunRecord{};
         return WAM_OK;
     } catch (...) {
         return fail(c, WAM_ERR_OOM, "host allocation failed");
@@ -1195,6 +1381,143 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
             return reconstruct3_impl(c, sc, mu_out, hist, mask_out, on_device, st);
         if (sc->precision == 32) return reconstruct_impl<float>(c, sc, mu_out, hist, mask_out, on_device, st);
         return reconstruct_impl<double>(c, sc, mu_out, hist, mask_out, on_device, st);
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+// ---- checkpoint / resume ----------------------------------------------------
+
+wam_status wam_checkpoint(wam_ctx* c, const char* path)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!path || !*path) return fail(c, WAM_ERR_ARG, "path is empty");
+    if (!c->last.valid || !c->has_data) return fail(c, WAM_ERR_STATE, "no finished reconstruction to checkpoint");
+    try {
+        const RunRecord& r = c->last;
+        const size_t mb = r.levels > 0 ? wam_mask_bytes_dims(c, r.levels, r.dims) : 0;
+        std::vector<double> beta((size_t)c->N), hist((size_t)r.iters_done + 1);
+        std::vector<unsigned char> mask(mb);
+        WCK(c, cudaMemcpy(beta.data(), c->buf[B_BETA].p, beta.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        WCK(c, cudaMemcpy(hist.data(), c->buf[B_COSTS].p, hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        if (mb) WCK(c, cudaMemcpy(mask.data(), c->buf[B_MASK_A].p, mb, cudaMemcpyDeviceToHost));
+        uint32_t cd = 0, ci = 0;
+        WST(data_crc(c, &cd, &ci));
+        const wam_geometry& g = c->g;
+        CkptWriter w;
+        w.raw(kCkptMagic, 8);
+        const uint32_t version = 1, zero = 0;
+        w.raw(&version, 4);
+        w.raw(&zero, 4);
+        const long long ints[20] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
+                                    r.zsum, r.precision, r.full_am, (long long)r.expand_at.size(), r.iters_done,
+                                    r.expansions_done, c->N, (long long)mb, (long long)hist.size(), cd, ci};
+        for (long long v : ints) w.i64(v);
+        const double dbl[11] = {g.vx, g.vy, g.vz, g.angle0, g.angle_span, g.bin_pitch, g.row_pitch, g.sod, g.sdd,
+                                r.clamp, r.tuning};
+        for (double v : dbl) w.f64(v);
+        for (int v : r.expand_at) w.i64(v);
+        for (double v : r.tau) w.f64(v);
+        w.raw(beta.data(), beta.size() * sizeof(double));
+        w.raw(mask.data(), mask.size());
+        w.raw(hist.data(), hist.size() * sizeof(double));
+        const uint32_t crc = crc32_update(0, w.b.data(), w.b.size());
+        w.raw(&crc, 4);
+        const std::string tmp = std::string(path) + ".tmp";
+        std::FILE* f = std::fopen(tmp.c_str(), "wb");
+        if (!f) return fail(c, WAM_ERR_IO, "cannot open " + tmp + " for writing");
+        const bool ok = std::fwrite(w.b.data(), 1, w.b.size(), f) == w.b.size() && std::fflush(f) == 0;
+        if (std::fclose(f) != 0 || !ok) {
+            std::remove(tmp.c_str());
+            return fail(c, WAM_ERR_IO, "writing " + tmp + " failed");
+        }
+        if (std::rename(tmp.c_str(), path) != 0) {
+            std::remove(tmp.c_str());
+            return fail(c, WAM_ERR_IO, std::string("renaming to ") + path + " failed");
+        }
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_resume(wam_ctx* c, const char* path)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (!path || !*path) return fail(c, WAM_ERR_ARG, "path is empty");
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    try {
+        std::FILE* f = std::fopen(path, "rb");
+        if (!f) return fail(c, WAM_ERR_IO, std::string("cannot open ") + path);
+        std::vector<unsigned char> buf;
+        unsigned char chunk[1 << 16];
+        size_t k;
+        while ((k = std::fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + k);
+        const bool rerr = std::ferror(f) != 0;
+        std::fclose(f);
+        if (rerr) return fail(c, WAM_ERR_IO, std::string("reading ") + path + " failed");
+        if (buf.size() < 16 + 4 || std::memcmp(buf.data(), kCkptMagic, 8) != 0)
+            return fail(c, WAM_ERR_IO, "not a checkpoint file (magic)");
+        uint32_t crc_file;
+        std::memcpy(&crc_file, buf.data() + buf.size() - 4, 4);
+        if (crc32_update(0, buf.data(), buf.size() - 4) != crc_file)
+            return fail(c, WAM_ERR_IO, "checkpoint file is corrupt (CRC mismatch)");
+        CkptReader rd{buf.data(), buf.size() - 4};
+        rd.at = 8;
+        uint32_t version = 0, zero = 0;
+        if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || version != 1)
+            return fail(c, WAM_ERR_IO, "unsupported checkpoint version");
+        long long v[20];
+        double d[11];
+        for (long long& x : v)
+            if (!rd.i64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
+        for (double& x : d)
+            if (!rd.f64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
+        const wam_geometry& g = c->g;
+        const bool same_geom = v[0] == g.kind && v[1] == g.nx && v[2] == g.ny && v[3] == g.nz && v[4] == g.n_views &&
+                               v[5] == g.n_bins && v[6] == g.n_rows && d[0] == g.vx && d[1] == g.vy &&
+                               d[2] == g.vz && d[3] == g.angle0 && d[4] == g.angle_span && d[5] == g.bin_pitch &&
+                               d[6] == g.row_pitch && d[7] == g.sod && d[8] == g.sdd;
+        if (!same_geom) return fail(c, WAM_ERR_STATE, "checkpoint geometry differs from the context's");
+        uint32_t cd = 0, ci = 0;
+        WST(data_crc(c, &cd, &ci));
+        if (v[18] != (long long)cd || v[19] != (long long)ci)
+            return fail(c, WAM_ERR_STATE, "checkpoint data (d, I0) differ from the context's");
+        RunRecord r;
+        r.levels = (int)v[7];
+        r.dims = (int)v[8];
+        r.zsum = (int)v[9];
+        r.precision = (int)v[10];
+        r.full_am = (int)v[11];
+        const long long n_expand = v[12];
+        r.iters_done = (int)v[13];
+        r.expansions_done = (int)v[14];
+        r.clamp = d[9];
+        r.tuning = d[10];
+        const size_t mb = r.levels > 0 ? wam_mask_bytes_dims(c, r.levels, r.dims) : 0;
+        if (r.levels < 0 || r.levels > WAM_MAX_LEVELS || n_expand < 0 || n_expand > 4096 || r.iters_done < 0 ||
+            r.expansions_done < 0 || r.expansions_done > n_expand || v[15] != c->N || v[16] != (long long)mb ||
+            v[17] != (long long)r.iters_done + 1 || !(r.tuning >= 0.25 && r.tuning <= 256.0))
+            return fail(c, WAM_ERR_IO, "checkpoint header is inconsistent with this context");
+        r.expand_at.resize((size_t)n_expand);
+        r.tau.resize((size_t)n_expand);
+        for (int& x : r.expand_at) {
+            long long t;
+            if (!rd.i64(&t)) return fail(c, WAM_ERR_IO, "checkpoint truncated");
+            x = (int)t;
+        }
+        for (double& x : r.tau)
+            if (!rd.f64(&x)) return fail(c, WAM_ERR_IO, "checkpoint truncated");
+        r.beta.resize((size_t)c->N);
+        r.mask.resize(mb);
+        r.hist.resize((size_t)r.iters_done + 1);
+        if (!rd.raw(r.beta.data(), r.beta.size() * sizeof(double)) || !rd.raw(r.mask.data(), mb) ||
+            !rd.raw(r.hist.data(), r.hist.size() * sizeof(double)) || rd.at != rd.n)
+            return fail(c, WAM_ERR_IO, "checkpoint size does not match its header");
+        r.valid = true;
+        c->back_ctas_per_sm = r.tuning;
+        c->pending = std::move(r);
+        return WAM_OK;
     } catch (...) {
         return fail(c, WAM_ERR_OOM, "host allocation failed");
     }
@@ -1416,6 +1739,8 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
         if (!ctxs[i]) return WAM_ERR_ARG;
         if (ctxs[i]->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(ctxs[i], WAM_ERR_ARG, "2-D contexts only");
         if (!ctxs[i]->has_data) return fail(ctxs[i], WAM_ERR_STATE, "wam_set_data must be called first");
+        if (ctxs[i]->pending.valid)
+            return fail(ctxs[i], WAM_ERR_STATE, "a resumed state is pending: continue it with wam_reconstruct");
         for (int k = 0; k < i; ++k)
             if (ctxs[k] == ctxs[i]) return fail(ctxs[i], WAM_ERR_ARG, "a context appears twice in the batch");
     }
@@ -1456,7 +1781,10 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
     }
     try {
         std::vector<Run<float>> runs(n);
-        for (int i = 0; i < n; ++i) ctxs[i]->prof = false;
+        for (int i = 0; i < n; ++i) {
+            ctxs[i]->prof = false;
+            ctxs[i]->last.valid = false;
+        }
         for (int i = 0; i < n; ++i) {
             wam_status s = runs[i].setup(ctxs[i], sc, st);
             if (s != WAM_OK) { cleanup(); return s; }
@@ -1543,8 +1871,10 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             cleanup();
             return fail(c0, WAM_ERR_CUDA, "synchronisation failed");
         }
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            record_run(ctxs[i], sc, J, (int)runs[i].next_exp);
             if (runs[i].monotone(hs[i]) != WAM_OK) ret = WAM_WARN_NONMONOTONE;
+        }
     } catch (...) {
         cleanup();
         return fail(c0, WAM_ERR_OOM, "host allocation failed");

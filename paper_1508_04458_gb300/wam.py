@@ -31,6 +31,7 @@ WAM_ERR_OOM = -2
 WAM_ERR_CUDA = -3
 WAM_ERR_TIMEOUT = -4
 WAM_ERR_STATE = -5
+WAM_ERR_IO = -6
 WAM_WARN_NONMONOTONE = 1
 WAM_MAX_LEVELS = 8
 WAM_TUNE_BACK_CTAS_PER_SM = 1
@@ -97,6 +98,8 @@ _PROTOS = {
     "wam_reconstruct_batch": (_S, [ctypes.POINTER(_P), _I, ctypes.POINTER(wam_schedule), ctypes.POINTER(_P),
                                    ctypes.POINTER(_P), _I, _I, _P]),
     "wam_set_tuning": (_S, [_P, _I, _D]),
+    "wam_checkpoint": (_S, [_P, ctypes.c_char_p]),
+    "wam_resume": (_S, [_P, ctypes.c_char_p]),
     "wam_profile": (_S, [_P, _I]),
     "wam_get_stats": (_S, [_P, _P]),
     "wam_kernel_launches": (ctypes.c_ulonglong, []),
@@ -226,6 +229,14 @@ class Context:
         del keep
         self.check(st, allow=(WAM_OK, WAM_WARN_NONMONOTONE))
         return mu, hist, masks[: self.mask_bytes(L, dims)], st
+
+    def checkpoint(self, path: str):
+        """Write the state of the last finished reconstruct() to path."""
+        return self.check(wam_checkpoint(self.h, os.fsencode(path)))
+
+    def resume(self, path: str):
+        """Load a checkpoint; the next reconstruct() continues from it."""
+        return self.check(wam_resume(self.h, os.fsencode(path)))
 
     def profile(self, enable: bool = True):
         """Reset and enable (or stop) per-kernel event timing of reconstruct()."""
