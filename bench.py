@@ -190,8 +190,9 @@ def run_wam(args, problem, world, rank, local_rank):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K complete reconstructions, L2 flushed between them
-    ctx.profile(True)
+    # ---- timed region: K complete reconstructions, L2 flushed between them;
+    # CUDA events bracket every kernel (no work counters in the kernels)
+    ctx.profile(mode=wam.WAM_PROFILE_TIME)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
@@ -211,7 +212,14 @@ def run_wam(args, problem, world, rank, local_rank):
         dist.barrier()
     launches = wam.kernel_launches() - launches0
     stats = ctx.stats()
+    # the same step once more with the kernels' work counters (outside the
+    # timed region: counting adds instructions); the work is deterministic
+    ctx.profile(mode=wam.WAM_PROFILE_WORK)
+    step()
+    work1 = ctx.stats()
     ctx.profile(False)
+    for k in stats:
+        stats[k]["work"] = work1[k]["work"] * args.steps
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = float(sum(step_ms))
     t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
@@ -399,10 +407,17 @@ def run_cone256(args):
                      ("multires_3d_haar", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=3)),
                      ("multires_per_slice", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=2, zsum=True))):
         ctx.reconstruct(**kw, device_out=True)
-        ctx.profile(True)
         (mu, hist, _, st), ms = _timed(lambda: ctx.reconstruct(**kw, device_out=True))
+        # the kernel split (events only) and the work (counters only) in two more runs
+        ctx.profile(mode=wam.WAM_PROFILE_TIME)
+        ctx.reconstruct(**kw, device_out=True)
         k = ctx.stats()
+        ctx.profile(mode=wam.WAM_PROFILE_WORK)
+        ctx.reconstruct(**kw, device_out=True)
+        kw_work = ctx.stats()
         ctx.profile(False)
+        for n in k:
+            k[n]["work"] = kw_work[n]["work"]
         h = hist.cpu().numpy()
         res[name] = {"ms": ms, "iters_per_s": J / (ms / 1e3), "status": st, "idiv0": float(h[0]),
                      "idiv_final": float(h[-1]),

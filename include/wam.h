@@ -379,9 +379,19 @@ typedef struct {
     unsigned long long work[WAM_NKERNEL];
 } wam_stats;
 
-/* enable = 1: reset the statistics and, from now on, bracket every kernel
- * launch of wam_reconstruct with CUDA events on its stream and count its
- * work; enable = 0 stops.  Adds two event records per launch. */
+/* Profiling modes of wam_profile. */
+enum {
+    WAM_PROFILE_OFF = 0,
+    WAM_PROFILE_ALL = 1,   /* events and work counters */
+    WAM_PROFILE_TIME = 2,  /* events only: the kernels run as unprofiled */
+    WAM_PROFILE_WORK = 3   /* work counters only (they add instructions to the kernels) */
+};
+
+/* A mode other than WAM_PROFILE_OFF resets the statistics; from then on every
+ * kernel launch of wam_reconstruct is bracketed with CUDA events on its
+ * stream (ALL, TIME; two event records per launch) and/or counts its work
+ * (ALL, WORK: ray-cell intersections with a nonzero chord); WAM_PROFILE_OFF
+ * stops.  Errors: WAM_ERR_ARG for an unknown mode. */
 wam_status wam_profile(wam_ctx* ctx, int enable);
 
 /* Statistics gathered since wam_profile(ctx, 1); synchronises the stream

@@ -33,7 +33,7 @@ def measure(ctx: "wam.Context", value: float, levels: int, n_iters: int, expand_
     """k_backproject ms per launch with the knob at `value`."""
     ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_BACK_CTAS_PER_SM, float(value)))
     ctx.reconstruct(levels, n_iters, expand_at, tau, device_out=True)      # warm-up
-    ctx.profile(True)
+    ctx.profile(mode=wam.WAM_PROFILE_TIME)
     ctx.reconstruct(levels, n_iters, expand_at, tau, device_out=True)
     st = ctx.stats()["backproject"]
     ctx.profile(False)

@@ -5,6 +5,8 @@
 // under one shared tree (the paper's own 3-D setting).  All sums run in a
 // fixed order.
 #include "cone3d.cuh"
+
+#include <cmath>
 #include "wam_kernels.h"
 
 #include <math.h>
@@ -47,10 +49,22 @@ __device__ __forceinline__ float flipf(float x, float sgn)
     return __int_as_float(__float_as_int(x) ^ (__float_as_int(sgn) & 0x80000000));
 }
 
-// 2^(-3l/2) (3-D Haar) or 2^-l (2-D Haar per slice)
+// 2^-k exactly
+__host__ __device__ __forceinline__ double exp2m(int k)
+{
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((1023 - k) << 20, 0);
+#else
+    return std::ldexp(1.0, -k);
+#endif
+}
+
+// 2^(-3l/2) (3-D Haar) or 2^-l (2-D Haar per slice), without a division:
+// for odd l, 2^(-3l/2) = 2^(-(3l-1)/2) / sqrt(2)
 __host__ __device__ __forceinline__ double basis_scale(int z3, int l)
 {
-    return z3 ? 1.0 / ((double)(1 << l) * sqrt((double)(1 << l))) : 1.0 / (double)(1 << l);
+    if (!z3) return exp2m(l);
+    return (l & 1) ? exp2m((3 * l - 1) / 2) * (1.0 / sqrt(2.0)) : exp2m(3 * l / 2);
 }
 
 // ---------------------------------------------------------------------------

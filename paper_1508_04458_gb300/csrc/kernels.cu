@@ -47,6 +47,9 @@ __device__ __forceinline__ void add_work(unsigned long long* work, unsigned cnt)
     if ((threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicAdd(work, (unsigned long long)tot);
 }
 
+// 2^-l exactly (l = 0..1022), built from its exponent bits
+__device__ __forceinline__ double pow2m(int l) { return __hiloint2double((1023 - l) << 20, 0); }
+
 struct OpSum {
     template <typename V> __device__ V operator()(V a, V b) const { return a + b; }
 };
@@ -59,19 +62,23 @@ struct OpMax {
 // Beer's law and the I-divergence terms (Sec. II and its footnote).
 // One thread per ray; CTA = (bin tile, view).
 // ---------------------------------------------------------------------------
-// The two apron-padded copies the pixel walk reads: py = mu with a zero
-// border ((ny + 2) rows of nx + 2), px = its transpose with a zero border
-// ((nx + 2) rows of ny + 2).  One thread per padded pixel (x, y) in
-// [-1, nx] x [-1, ny]; both writes coalesced through a 32x32 shared tile.
+// The two apron-padded copies the pixel walk reads, on the grid of cells of
+// 2^lam x 2^lam pixels (mu constant on each cell; lam = 0: the pixels):
+// py = the cell values with a zero border ((ny + 2) rows of nx + 2, nx, ny
+// counted in cells), px = its transpose with a zero border ((nx + 2) rows of
+// ny + 2).  A cell's value is read at its first pixel; nxf is mu's row
+// length.  One thread per padded cell (x, y) in [-1, nx] x [-1, ny]; both
+// writes coalesced through a 32x32 shared tile.
 template <typename T>
-__global__ void k_pad2(const T* __restrict__ mu, int nx, int ny, T* __restrict__ py, T* __restrict__ px)
+__global__ void k_pad2(const T* __restrict__ mu, int nxf, int lam, int nx, int ny, T* __restrict__ py,
+                       T* __restrict__ px)
 {
     __shared__ T tile[32][33];
     const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int x = x0 + threadIdx.x, y = y0 + k;
         T v = T(0);
-        if (x >= 0 && x < nx && y >= 0 && y < ny) v = mu[(size_t)y * nx + x];
+        if (x >= 0 && x < nx && y >= 0 && y < ny) v = mu[((size_t)y << lam) * nxf + ((size_t)x << lam)];
         tile[k][threadIdx.x] = v;
         if (x <= nx && y <= ny) py[(size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
     }
@@ -222,7 +229,7 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
             });
 #pragma unroll
             for (int li = 0; li < kMaxLevels; ++li) flush(li);
-            rowsum = (double)rs + (double)total / (double)(1 << L);
+            rowsum = (double)rs + (double)total * pow2m(L);
         }
     }
     rowsum = warp_reduce(rowsum, OpMax());
@@ -276,6 +283,125 @@ __device__ __forceinline__ double flip2(double x, double s1, double s2)
 // dirtab[v][b] = (s/dx, -c/dy, 1/dx, 1/dy) of ray (v, b), c, s = cos, sin of
 // the view: with delta the ray's offset from a block centre along u, the
 // centre-line crossings are a = delta s/dx and b = -delta c/dy.
+// Item kinds of a back-projection segment.
+enum { kBpBlock = 0, kBpSplit = 1, kBpQuad = 2 };
+
+// The view and bin loops of one item (block bx, by of segment S) over the
+// views of its chunk taken by this warp, specialised by item kind, by the
+// direction table's presence and by work counting, so that the inner loop
+// carries no run-time switch.  acc: A, h+, h-, v+, v-, d+, d- of the Haar
+// split; a pixel quad keeps its four pixel sums in the first four.
+template <typename T, int MODE, bool TABLE, bool WORK>
+__device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int bx, int by, int chunk, int wv,
+                                        const T* __restrict__ sino,
+                                        const typename Vec4<T>::type* __restrict__ dirtab, T (&acc)[7],
+                                        unsigned& evals)
+{
+    const int bsz = 1 << S.level;
+    const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
+    const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
+    const T scale = MODE == kBpQuad ? T(1) : T(1) / T(bsz);
+    const int v0 = chunk * S.vpc;
+    const int v1 = min(g.V, v0 + S.vpc);
+    const bool fan = g.kind != 0;
+    const T isdd = T(1) / g.sdd, ipitch = T(1) / g.pitch;
+    const T u0 = -g.ucen * g.pitch;
+    for (int v = v0 + wv; v < v1; v += kViewLanes) {
+        const T c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
+        const T ac = cx * c + cy * s;        // block centre along e
+        const T wc = -cx * s + cy * c;       // ... along u
+        // shadow of the block: detector coordinates of its four corners
+        T umin = T(1e30), umax = T(-1e30);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy;
+            const T wu = wc - ox * s + oy * c;
+            const T uu = fan ? fast_div(g.sdd * wu, g.sod - (ac + ox * c + oy * s)) : wu;
+            umin = fmin(umin, uu);
+            umax = fmax(umax, uu);
+        }
+        // the rays through the shadow (umin, umax); a margin of 1e-3 bin
+        // covers the fast division's rounding (~1e-4 bin at the detector edge)
+        const int blo = max(0, (int)ceil(umin * ipitch + g.ucen - T(1e-3)));
+        const int bhi = min(g.B - 1, (int)floor(umax * ipitch + g.ucen + T(1e-3)));
+        const T kappa = fan ? (g.sod - ac) * isdd : T(1);
+        // ray offset from the block centre along u, linear in the bin
+        const T delta0 = (T(blo) * g.pitch + u0) * kappa - wc, dstep = g.pitch * kappa;
+        const T* row = sino + (size_t)v * g.B;
+        const typename Vec4<T>::type* drow = TABLE ? dirtab + (size_t)v * g.B : nullptr;
+        T fk = T(0);
+#pragma unroll 1
+        for (int bb = blo; bb <= bhi; ++bb, fk += T(1)) {
+            const T delta = fma(fk, dstep, delta0);
+            typename Vec4<T>::type dd;
+            if (TABLE) {
+                dd = ld4(drow + bb);
+            } else {
+                // no table: the same four numbers from the ray's direction
+                const T ub = T(bb) * g.pitch + u0;
+                T dx = c, dy = s;
+                if (fan) {
+                    const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
+                    dx = (-g.sdd * c - ub * s) * rn;
+                    dy = (-g.sdd * s + ub * c) * rn;
+                }
+                dd.z = safe_rcp(dx);
+                dd.w = safe_rcp(dy);
+                dd.x = s * dd.z;
+                dd.y = -c * dd.w;
+            }
+            const T a = delta * dd.x, b = delta * dd.y;
+            const T q = __ldg(row + bb);
+            if (MODE == kBpQuad) {
+                // pixel basis: the four pixels' chords in physical order, select-free:
+                // pixel (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) sums
+                T cll, chl, clh, chh;
+                child_chords_phys(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
+                acc[0] += q * cll;
+                acc[1] += q * chl;
+                acc[2] += q * clh;
+                acc[3] += q * chh;
+                if (WORK) evals += (cll > T(0)) + (chl > T(0)) + (clh > T(0)) + (chh > T(0));
+            } else if (MODE == kBpSplit) {
+                // Haar split from the crossing-ordered child chords (first / second
+                // half along the travel direction), the halves' order fixed by signs
+                T cFF, cFS, cSF, cSS;
+                child_chords_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w), cFF, cFS, cSF, cSS);
+                const T qs = q * scale;
+                const T xF = cFF + cFS, xS = cSF + cSS;      // first / second x half
+                const T yF = cFF + cSF, yS = cFS + cSS;
+                acc[0] += qs * (xF + xS);
+                // lower half minus upper half, by the travel direction's signs
+                const T ph = qs * flip(yF - yS, dd.w);
+                const T pv = qs * flip(xF - xS, dd.z);
+                const T pd = qs * flip2((cFF + cSS) - (cFS + cSF), dd.z, dd.w);
+                if (ph > T(0)) acc[1] += ph; else acc[2] += ph;
+                if (pv > T(0)) acc[3] += pv; else acc[4] += pv;
+                if (pd > T(0)) acc[5] += pd; else acc[6] += pd;
+                if (WORK) evals += (cFF > T(0)) + (cFS > T(0)) + (cSF > T(0)) + (cSS > T(0));
+            } else {
+                const T ch = block_chord_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w));
+                acc[0] += q * scale * ch;
+                if (WORK) evals += ch > T(0);
+            }
+        }
+    }
+}
+
+template <typename T, bool TABLE, bool WORK>
+__device__ __forceinline__ void bp_dispatch(const Geom<T>& g, const Segment& S, int bx, int by, int chunk, int wv,
+                                            const T* sino, const typename Vec4<T>::type* dirtab, T (&acc)[7],
+                                            unsigned& evals)
+{
+    if (S.quad) bp_item<T, kBpQuad, TABLE, WORK>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+    else if (S.has_details) bp_item<T, kBpSplit, TABLE, WORK>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+    else bp_item<T, kBpBlock, TABLE, WORK>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+}
+
+// a4 (Eq. 1.10) and a0: one CTA = kItemsPerCta items (lanes) x kViewLanes
+// warps, each warp taking every kViewLanes-th view of the CTA's view chunk;
+// the warps' sums meet in shared memory in a fixed order and leave one
+// partial per (item, chunk, slot).
 template <typename T>
 __global__ void __launch_bounds__(kBackTPB)
 k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
@@ -291,15 +417,11 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
     const int chunk = local / S.tiles, tile = local - chunk * S.tiles;
     const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
     const int item = tile * kItemsPerCta + lane;
-    const bool valid = item < S.n_items;
-    const bool det = S.has_details != 0;
     const bool quad = S.quad != 0;
-    const bool four = det || quad;       // chords through the four children
-    // accumulators: Haar split (A, h+, h-, v+, v-, d+, d-); a pixel quad keeps
-    // its four pixel sums in the first four
-    T aA = 0, hP = 0, hM = 0, vP = 0, vM = 0, dP = 0, dM = 0;
+    const bool det = S.has_details != 0;
+    T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     unsigned evals = 0;
-    if (valid) {
+    if (item < S.n_items) {
         int bx, by;
         if (S.items) {
             const uint32_t w = S.items[item];
@@ -309,90 +431,15 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
             bx = item % S.gw;
             by = item / S.gw;
         }
-        const int bsz = 1 << S.level;
-        const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
-        const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
-        const T scale = quad ? T(1) : T(1) / T(bsz);
-        const int v0 = chunk * S.vpc;
-        const int v1 = min(g.V, v0 + S.vpc);
-        const bool fan = g.kind != 0;
-        const T isdd = T(1) / g.sdd, ipitch = T(1) / g.pitch;
-        const T u0 = -g.ucen * g.pitch;
-        for (int v = v0 + wv; v < v1; v += kViewLanes) {
-            const T c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
-            const T ac = cx * c + cy * s;        // block centre along e
-            const T wc = -cx * s + cy * c;       // ... along u
-            // shadow of the block: detector coordinates of its four corners
-            T umin = T(1e30), umax = T(-1e30);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const T ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy;
-                const T wu = wc - ox * s + oy * c;
-                const T uu = fan ? fast_div(g.sdd * wu, g.sod - (ac + ox * c + oy * s)) : wu;
-                umin = fmin(umin, uu);
-                umax = fmax(umax, uu);
-            }
-            // the rays through the shadow (umin, umax); a margin of 1e-3 bin
-            // covers the fast division's rounding (~1e-4 bin at the detector edge)
-            const int blo = max(0, (int)ceil(umin * ipitch + g.ucen - T(1e-3)));
-            const int bhi = min(g.B - 1, (int)floor(umax * ipitch + g.ucen + T(1e-3)));
-            const T kappa = fan ? (g.sod - ac) * isdd : T(1);
-            const T* row = sino + (size_t)v * g.B;
-            const typename Vec4<T>::type* drow = dirtab ? dirtab + (size_t)v * g.B : nullptr;
-            T fb = T(blo);
-            for (int bb = blo; bb <= bhi; ++bb, fb += T(1)) {
-                const T ub = fb * g.pitch + u0;
-                const T delta = ub * kappa - wc;     // ray offset from the centre along u
-                typename Vec4<T>::type dd;
-                if (drow) {
-                    dd = ld4(drow + bb);
-                } else {
-                    // no table: the same four numbers from the ray's direction
-                    T dx = c, dy = s;
-                    if (fan) {
-                        const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
-                        dx = (-g.sdd * c - ub * s) * rn;
-                        dy = (-g.sdd * s + ub * c) * rn;
-                    }
-                    dd.z = safe_rcp(dx);
-                    dd.w = safe_rcp(dy);
-                    dd.x = s * dd.z;
-                    dd.y = -c * dd.w;
-                }
-                const T a = delta * dd.x, b = delta * dd.y;
-                const T q = __ldg(row + bb);
-                if (four) {
-                    // chords of the four children (pixels of a quad) in physical order
-                    T cll, chl, clh, chh;
-                    child_chords_phys(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
-                    if (work) evals += (cll > T(0)) + (chl > T(0)) + (clh > T(0)) + (chh > T(0));
-                    if (quad) {
-                        // pixel basis: pixel (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) sums
-                        aA += q * cll;
-                        hP += q * chl;
-                        hM += q * clh;
-                        vP += q * chh;
-                    } else {
-                        // Haar split: lower half minus upper half along y (h), x (v),
-                        // and the diagonal pair minus the anti-diagonal pair (d)
-                        const T qs = q * scale;
-                        const T yl = cll + chl, yh = clh + chh;
-                        aA += qs * (yl + yh);
-                        const T ph = qs * (yl - yh);
-                        const T pv = qs * ((cll + clh) - (chl + chh));
-                        const T pd = qs * ((cll + chh) - (chl + clh));
-                        if (ph > T(0)) hP += ph; else hM += ph;
-                        if (pv > T(0)) vP += pv; else vM += pv;
-                        if (pd > T(0)) dP += pd; else dM += pd;
-                    }
-                } else {
-                    const T ch = block_chord_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w));
-                    aA += q * scale * ch;
-                    if (work) evals += ch > T(0);
-                }
-            }
+        if (dirtab) {
+            if (work) bp_dispatch<T, true, true>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+            else bp_dispatch<T, true, false>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+        } else {
+            if (work) bp_dispatch<T, false, true>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
+            else bp_dispatch<T, false, false>(g, S, bx, by, chunk, wv, sino, dirtab, acc, evals);
         }
     }
+    const T aA = acc[0], hP = acc[1], hM = acc[2], vP = acc[3], vM = acc[4], dP = acc[5], dM = acc[6];
     add_work(work, evals);
     // fixed-order sum of the 8 view lanes, one partial per (item, view range)
     red[wv][0][lane] = aA;
@@ -615,29 +662,64 @@ __global__ void k_reduce_pixels(SegTable tab, int nx, long long npix, const T* _
 // a1, Eq. 1.2: mu = Omega beta over the tree.  Per pixel, only the levels
 // above its leaf carry active details; below they are inactive (zero).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
-                        T* __restrict__ mu)
+// a1, Eq. 1.2: mu at pixel (ix, iy) = the sum over the active coefficients
+// whose support holds it, i.e. the level-L approximation and the details of
+// the expanded ancestors above its leaf level lam, in FP64.
+__device__ __forceinline__ double synth_at(const Layout& lay, const double* __restrict__ beta, int ix, int iy,
+                                           int lam)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= lay.nx * lay.ny) return;
-    const int ix = p % lay.nx, iy = p / lay.nx;
     const int L = lay.L;
-    if (L == 0) {
-        mu[p] = (T)beta[p];
-        return;
-    }
-    const int lam = leaf ? (int)leaf[p] : 0;
-    double v = beta[(long long)(iy >> L) * lay.gw[L] + (ix >> L)] / (double)(1 << L);
+    double v = beta[(long long)(iy >> L) * lay.gw[L] + (ix >> L)] * pow2m(L);
     for (int l = L; l > lam; --l) {
         const int bx = ix >> l, by = iy >> l;
         const double sh = ((iy >> (l - 1)) & 1) ? -1.0 : 1.0;
         const double sv = ((ix >> (l - 1)) & 1) ? -1.0 : 1.0;
         const long long n = (long long)lay.gw[l] * lay.gh[l];
         const long long z = lay.coff[l] + (long long)by * lay.gw[l] + bx;
-        v += (sh * beta[z] + sv * beta[z + n] + sh * sv * beta[z + 2 * n]) / (double)(1 << l);
+        v += (sh * beta[z] + sv * beta[z + n] + sh * sv * beta[z + 2 * n]) * pow2m(l);
     }
-    mu[p] = (T)v;
+    return v;
+}
+
+template <typename T>
+__global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
+                        T* __restrict__ mu)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= lay.nx * lay.ny) return;
+    if (lay.L == 0) {
+        mu[p] = (T)beta[p];
+        return;
+    }
+    const int ix = p % lay.nx, iy = p / lay.nx;
+    mu[p] = (T)synth_at(lay, beta, ix, iy, leaf ? (int)leaf[p] : 0);
+}
+
+// a1 fused with the strip walk's input: the apron-padded copies of k_pad2
+// (cells of 2^lam pixels, row-major and transposed) filled straight from the
+// coefficients; a cell's value is mu at its first pixel.
+template <typename T>
+__global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
+                             int lam, int nx, int ny, T* __restrict__ py, T* __restrict__ px)
+{
+    __shared__ T tile[32][33];
+    const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int x = x0 + threadIdx.x, y = y0 + k;
+        T v = T(0);
+        if (x >= 0 && x < nx && y >= 0 && y < ny) {
+            const int ix = x << lam, iy = y << lam;
+            v = lay.L == 0 ? (T)beta[(long long)iy * lay.nx + ix]
+                           : (T)synth_at(lay, beta, ix, iy, leaf ? (int)leaf[(long long)iy * lay.nx + ix] : 0);
+        }
+        tile[k][threadIdx.x] = v;
+        if (x <= nx && y <= ny) py[(size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int y = y0 + threadIdx.x, x = x0 + k;
+        if (x <= nx && y <= ny) px[(size_t)(x + 1) * (ny + 2) + (y + 1)] = tile[threadIdx.x][k];
+    }
 }
 
 // Leaf level of every pixel from the masks.
@@ -824,7 +906,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 template <typename T>
-cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, const float* d,
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d,
                            const double* dterm, const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st)
 {
@@ -834,14 +916,46 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
         k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, d, dterm, I0, qhat, p_out, resid,
                                                       cost_part, work);
     } else {
-        if (!pad) return cudaErrorInvalidValue;
+        if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
+            return cudaErrorInvalidValue;
+        // the grid of 2^lam-pixel cells: same box, cells 2^lam times larger
+        Geom<T> gc = g;
+        gc.nx = g.nx >> lam;
+        gc.ny = g.ny >> lam;
+        gc.vx = g.vx * T(1 << lam);
+        gc.vy = g.vy * T(1 << lam);
+        gc.ivx = g.ivx / T(1 << lam);
+        gc.ivy = g.ivy / T(1 << lam);
         COUNT_LAUNCH();
-        k_pad2<T><<<dim3(nblk(g.nx + 2, 32), nblk(g.ny + 2, 32)), dim3(32, 8), 0, st>>>(
-            mu, g.nx, g.ny, pad, pad + (size_t)(g.nx + 2) * (g.ny + 2));
+        k_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
+            mu, g.nx, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
         COUNT_LAUNCH();
-        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(g, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
+        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
                                                      cost_part, work);
     }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, const double* beta,
+                                int lam, T* pad, const float* d, const double* dterm, const float* I0, T* qhat,
+                                T* p_out, T* resid, double* cost_part, unsigned long long* work, cudaStream_t st)
+{
+    if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
+        return cudaErrorInvalidValue;
+    Geom<T> gc = g;
+    gc.nx = g.nx >> lam;
+    gc.ny = g.ny >> lam;
+    gc.vx = g.vx * T(1 << lam);
+    gc.vy = g.vy * T(1 << lam);
+    gc.ivx = g.ivx / T(1 << lam);
+    gc.ivy = g.ivy / T(1 << lam);
+    COUNT_LAUNCH();
+    k_synth_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
+        lay, leaf, beta, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
+    COUNT_LAUNCH();
+    k_forward<T, true><<<dim3(nblk(g.B, kFwdTPB), g.V), kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0,
+                                                                          qhat, p_out, resid, cost_part, work);
     return cudaGetLastError();
 }
 
@@ -1039,7 +1153,10 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
 
 // explicit instantiations
 #define WAM_INST(T)                                                                                              \
-    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, T*, const uint8_t*, const float*, const double*, \
+    template cudaError_t launch_forward_tree<T>(const Geom<T>&, const Layout&, const uint8_t*, const double*, int, T*, \
+                                                const float*, const double*, const float*, T*, T*, T*, double*,       \
+                                                unsigned long long*, cudaStream_t);                                   \
+    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, T*, const uint8_t*, int, const float*, const double*, \
                                            const float*, T*, T*, T*, double*, unsigned long long*, cudaStream_t); \
     template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \

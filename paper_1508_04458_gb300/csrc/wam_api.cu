@@ -56,12 +56,14 @@ struct wam_ctx {
     RunRecord last;                        // last finished reconstruction (device buffers hold its arrays)
     RunRecord pending;                     // state loaded by wam_resume
     // profiling
-    bool prof = false;
+    bool prof = false;                     // CUDA events around each kernel
+    bool prof_work = false;                // work counters in the kernels
     std::vector<cudaEvent_t> ev_pool;
     std::vector<ProfPending> pend;
     wam_stats stats{};
     unsigned long long* dwork = nullptr;   // device [WAM_NKERNEL]
     long long last_leaves = 0;             // leaves of the tree last planned
+    int last_lmin = 0;                     // ... and its finest leaf level
     // tuning
     double back_ctas_per_sm = 32.0;        // back-projector work split: CTAs per SM per launch
     cudaStream_t prof_stream = nullptr;
@@ -221,7 +223,7 @@ struct ProfScope {
     }
 };
 
-unsigned long long* work_ptr(wam_ctx* c, int k) { return c->prof && c->dwork ? c->dwork + k : nullptr; }
+unsigned long long* work_ptr(wam_ctx* c, int k) { return c->prof_work && c->dwork ? c->dwork + k : nullptr; }
 
 wam_status prof_resolve(wam_ctx* c)
 {
@@ -465,6 +467,11 @@ wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t
     long long leaves = (long long)lay.gw[L] * lay.gh[L];
     for (int k = 1; k <= L; ++k) leaves += 3LL * h[k];
     c->last_leaves = leaves;
+    // h[k] counts the expanded blocks of level L - k + 1, whose children are
+    // leaves of level L - k (or finer)
+    c->last_lmin = L;
+    for (int k = 1; k <= L; ++k)
+        if (h[k] > 0) c->last_lmin = L - k;
     std::vector<ListInfo> li;
     li.push_back({L, 1, 0, h[0], lists, lay.gw[L]});
     li.push_back({L, 1, 1, h[1], lists + stride, lay.gw[L]});
@@ -552,14 +559,27 @@ struct Run {
     const void* dirt = nullptr;
     SegTable tab{};
     const uint8_t* fwd_leaf = nullptr;
+    int fwd_lam = 0;
     std::vector<int> exp_at;
     size_t next_exp = 0;
     int j0 = 0;                 // first iteration to run (> 0 when resuming)
 
-    // The leaf walk pays per leaf what the pixel walk pays per pixel, about
-    // 2.5 times over; once leaves average fewer than 4 pixels the image mu
-    // (constant on leaves) is projected pixel by pixel instead.
-    const uint8_t* pick_leaf() const { return (L > 0 && 4 * c->last_leaves < N) ? leaf : nullptr; }
+    // How a2 walks the tree's image mu, which is constant on the leaves and
+    // so on the cells of the finest leaf level lam: the strip walk over the
+    // grid of those cells (exact for such an image), unless the tree is so
+    // uneven that the leaves are fewer than a ninth of the cells.  A ray then
+    // meets about 3 times fewer leaves than cells, which pays for the leaf
+    // walk's dearer steps (a leaf-map read and a division per leaf).
+    const uint8_t* pick_leaf()
+    {
+        fwd_lam = L > 0 ? c->last_lmin : 0;
+        const long long cells = N >> (2 * fwd_lam);
+        if (L > 0 && cells > 9 * c->last_leaves) {
+            fwd_lam = 0;
+            return leaf;
+        }
+        return nullptr;
+    }
 
     wam_status setup(wam_ctx* ctx, const wam_schedule* sched, cudaStream_t st)
     {
@@ -664,14 +684,18 @@ struct Run {
     // costs[*counter] (then counter + 1) instead of costs[j]
     wam_status iteration(int j, cudaStream_t st, bool use_counter)
     {
-        {
+        if (fwd_leaf) {
             PROF(WAM_K_SYNTH);
             WCK(c, launch_synth(lay, leaf, beta, mu, st));                                  // a1
         }
         {
-            PROF(WAM_K_FORWARD);                                                            // a2, a3
-            WCK(c, launch_forward(g, mu, mut, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
-                                  work_ptr(c, WAM_K_FORWARD), st));
+            PROF(WAM_K_FORWARD);                                                            // (a1,) a2, a3
+            if (fwd_leaf)
+                WCK(c, launch_forward(g, mu, mut, fwd_leaf, 0, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+                                      work_ptr(c, WAM_K_FORWARD), st));
+            else
+                WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, beta, fwd_lam, mut, dsino, dterm, I0, q,
+                                           (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, np, costs + j, st));
         }
@@ -721,7 +745,7 @@ struct Run {
         }
         {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_forward(g, mu, mut, fwd_leaf, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+            WCK(c, launch_forward(g, mu, mut, fwd_leaf, fwd_lam, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, np, costs + J, st));
@@ -767,7 +791,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     std::vector<double> h;
     WST(run.copy_out(mu_out, hist, mask_out, on_device, &h, st));
     WCK(c, cudaStreamSynchronize(st));
-    if (c->prof) WST(prof_resolve(c));
+    if (c->prof || c->prof_work) WST(prof_resolve(c));
     record_run(c, sc, run.J, (int)run.next_exp);
     return run.monotone(h);
 }
@@ -782,7 +806,7 @@ wam_status project_impl(wam_ctx* c, const T* mu, T* p, void* stream)
     WST(make_geom<T>(c, &g));
     T* mut = nullptr;
     WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
-    WCK(c, launch_forward<T>(g, mu, mut, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, nullptr,
+    WCK(c, launch_forward<T>(g, mu, mut, nullptr, 0, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, nullptr,
                              as_stream(stream)));
     return WAM_OK;
 }
@@ -840,7 +864,7 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
     WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
     T* mut = nullptr;
     WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
-    WCK(c, launch_forward<T>(g, mu, mut, leaf, static_cast<const float*>(c->buf[B_D].p),
+    WCK(c, launch_forward<T>(g, mu, mut, leaf, 0, static_cast<const float*>(c->buf[B_D].p),
                              static_cast<const double*>(c->buf[B_DTERM].p),
                              static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr, cpart, nullptr,
                              st));
@@ -1172,7 +1196,7 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
     WCK(c, cudaMemcpyAsync(h.data(), costs, (J + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (hist) WCK(c, cudaMemcpyAsync(hist, costs, (J + 1) * sizeof(double), k2, st));
     WCK(c, cudaStreamSynchronize(st));
-    if (c->prof) WST(prof_resolve(c));
+    if (c->prof || c->prof_work) WST(prof_resolve(c));
     record_run(c, sc, J, (int)next_exp);
     for (int j = 0; j < J; ++j)
         if (h[j + 1] > h[j] + 1e-6 * std::fabs(h[j])) return WAM_WARN_NONMONOTONE;
@@ -1689,6 +1713,7 @@ wam_status wam_expand(wam_ctx* c, int levels, const float* S, double tau, const 
 wam_status wam_profile(wam_ctx* c, int enable)
 {
     if (!c) return WAM_ERR_ARG;
+    if (enable < WAM_PROFILE_OFF || enable > WAM_PROFILE_WORK) return fail(c, WAM_ERR_ARG, "unknown profile mode");
     if (enable) {
         if (!c->dwork) {
             if (cudaMalloc(&c->dwork, sizeof(unsigned long long) * WAM_NKERNEL) != cudaSuccess) {
@@ -1706,7 +1731,8 @@ wam_status wam_profile(wam_ctx* c, int enable)
         WCK(c, cudaMemset(c->dwork, 0, sizeof(unsigned long long) * WAM_NKERNEL));
         std::memset(&c->stats, 0, sizeof(c->stats));
     }
-    c->prof = enable != 0;
+    c->prof = enable == WAM_PROFILE_ALL || enable == WAM_PROFILE_TIME;
+    c->prof_work = enable == WAM_PROFILE_ALL || enable == WAM_PROFILE_WORK;
     return WAM_OK;
 }
 
@@ -1940,7 +1966,7 @@ wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p,
         WST(make_geom<float>(c, &g));
         float* mut = nullptr;
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
-        WCK(c, launch_forward<float>(g, mu, mut, nullptr, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+        WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
                                      nullptr, st));
         return WAM_OK;
     } catch (...) {
@@ -1989,7 +2015,7 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
         WST(ensure_t(c, B_GRES, (size_t)c->M, &res));
         float* mut = nullptr;
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
-        WCK(c, launch_forward<float>(g, mu, mut, nullptr, static_cast<const float*>(c->buf[B_D].p),
+        WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, static_cast<const float*>(c->buf[B_D].p),
                                      static_cast<const double*>(c->buf[B_DTERM].p),
                                      static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, res, cpart, nullptr,
                                      st));

@@ -278,7 +278,7 @@ __device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& 
     T fj = T(j0 + 1);
     strip(fmax(fma(fj, vm, M0) - s_lo, T(0)) * sec, fma(fj, D, A));
     const T full = vm * sec;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = j1 - j0 - 1; k > 0; --k) {
         fj += T(1);
         strip(full, fma(fj, D, A));

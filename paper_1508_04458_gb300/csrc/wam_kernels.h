@@ -6,11 +6,20 @@
 namespace wam {
 
 template <typename T>
+// leaf: the leaf walk over the tree's leaf map; null: the strip walk over the
+// grid of 2^lam-pixel cells (mu must be constant on them; lam = 0: pixels).
 // pad: scratch of 2 (nx + 2)(ny + 2) elements, required when leaf is null
-// (the pixel walk reads apron-padded copies of mu written there).
-cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, const float* d, const double* dterm,
+// (the strip walk reads apron-padded copies of the cell values written there).
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d, const double* dterm,
                            const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st);
+// a1 + a2 + a3 for the strip walk: the padded cell images of 2^lam pixels
+// synthesised from the coefficients beta over the tree (leaf map; null when
+// L = 0) straight into pad, then the forward pass.
+template <typename T>
+cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, const double* beta,
+                                int lam, T* pad, const float* d, const double* dterm, const float* I0, T* qhat,
+                                T* p_out, T* resid, double* cost_part, unsigned long long* work, cudaStream_t st);
 int forward_parts(int V, int B);
 cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st);
 cudaError_t launch_max_final(const double* part, int n, double* out, cudaStream_t st);

@@ -35,6 +35,7 @@ WAM_ERR_IO = -6
 WAM_WARN_NONMONOTONE = 1
 WAM_MAX_LEVELS = 8
 WAM_TUNE_BACK_CTAS_PER_SM = 1
+WAM_PROFILE_OFF, WAM_PROFILE_ALL, WAM_PROFILE_TIME, WAM_PROFILE_WORK = 0, 1, 2, 3
 
 
 class wam_geometry(ctypes.Structure):
@@ -238,9 +239,11 @@ class Context:
         """Load a checkpoint; the next reconstruct() continues from it."""
         return self.check(wam_resume(self.h, os.fsencode(path)))
 
-    def profile(self, enable: bool = True):
-        """Reset and enable (or stop) per-kernel event timing of reconstruct()."""
-        self.check(wam_profile(self.h, 1 if enable else 0))
+    def profile(self, enable: bool = True, mode: Optional[int] = None):
+        """Reset and enable (or stop) per-kernel event timing and work counting
+        of reconstruct(); mode = WAM_PROFILE_TIME / _WORK selects one of them."""
+        m = mode if mode is not None else (WAM_PROFILE_ALL if enable else WAM_PROFILE_OFF)
+        self.check(wam_profile(self.h, m))
 
     def stats(self) -> dict:
         st = wam_stats()
