@@ -229,6 +229,65 @@ def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None) -> AMResult:
 
 
 # ---------------------------------------------------------------------------
+# ordered subsets (the paper's Conclusion combines the method with ordered
+# subsets; the combination is read here as: a sub-iteration is one step of
+# Algorithm 1 on the rays of one subset of views)
+# ---------------------------------------------------------------------------
+
+def view_subsets(n_views: int, n_subsets: int) -> List[np.ndarray]:
+    """Subset s holds the views k with k mod S = s (interleaved, so every
+    subset spans the whole angular range)."""
+    return [np.arange(s, n_views, n_subsets) for s in range(n_subsets)]
+
+
+@dataclasses.dataclass
+class OSResult:
+    beta: np.ndarray
+    mu: np.ndarray
+    cost: np.ndarray                  # full I(d||qhat) at the start of each outer iteration, and at the end
+    z0: np.ndarray                    # [n_iter, S]: Z0 of each sub-iteration (max over its subset's rays)
+    sub_cost: np.ndarray              # [n_iter, S, 2]: the subset's own I-divergence before / after its step
+    tree: Optional[List[np.ndarray]]
+
+
+def os_wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int, n_subsets: int, n_bins: int,
+                  expand_at: Sequence[int] = (), taus: Sequence[float] = ()) -> OSResult:
+    """Algorithm 1 with ordered subsets of views.  Each outer iteration visits
+    the subsets in order s = 0..S-1; sub-iteration s is one step of Algorithm 1
+    restricted to the rays y of subset s: b_s(z) = sum_{y in s} d(y) phi(y|z)
+    (Eq. 1.6 on the subset), qhat and bhat+- over those rays (Eq. 1.10), and
+    Z0_s = max over those rays of sum_{z in Zs} |phi(y|z)| (Eq. 1.61), which
+    keeps the convex decomposition valid for the subset's surrogate.  The tree
+    grows after the listed outer iterations.  S = 1 is Algorithm 1."""
+    d = np.asarray(d, dtype=np.float64).ravel()
+    I0a = np.broadcast_to(np.asarray(I0, dtype=np.float64), d.shape)
+    Omega = haar.basis_matrix(nx, ny, L)
+    Phi = (H @ Omega).tocsr()
+    n_views = Phi.shape[0] // n_bins
+    rows = [(k[:, None] * n_bins + np.arange(n_bins)[None, :]).ravel() for k in view_subsets(n_views, n_subsets)]
+    Phis = [Phi[r].tocsc() for r in rows]
+    bs = [P.T @ d[r] for P, r in zip(Phis, rows)]
+    beta = np.zeros(nx * ny)
+    tree = empty_tree(nx, ny, L)
+    sched = dict(zip(expand_at, taus))
+    costs, z0s, subc = [], np.zeros((n_iter, n_subsets)), np.zeros((n_iter, n_subsets, 2))
+    for j in range(n_iter):
+        costs.append(idiv(d, I0a, Phi @ beta))
+        act = active_mask(tree, nx, ny, L)
+        for s_ in range(n_subsets):
+            Ps = Phis[s_][:, act]
+            ds, Is = d[rows[s_]], I0a[rows[s_]]
+            delta, c_before, Z0 = am_step(Ps, bs[s_][act], beta[act], ds, Is)
+            beta[act] += delta
+            z0s[j, s_] = Z0
+            subc[j, s_] = (c_before, idiv(ds, Is, Ps @ beta[act]))
+        if (j + 1) in sched:
+            tree = expand(tree, (Omega @ beta).reshape(ny, nx), sched[j + 1])
+    costs.append(idiv(d, I0a, Phi @ beta))
+    return OSResult(beta, (Omega @ beta).reshape(ny, nx), np.array(costs), z0s, subc, tree)
+
+
+# ---------------------------------------------------------------------------
 # 3-D Haar trees (volume blocks of 2^l voxels per side, seven details each)
 # ---------------------------------------------------------------------------
 

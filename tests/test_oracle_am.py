@@ -270,3 +270,47 @@ def test_phi_equals_child_chords():
             else:
                 want = (c[0] - c[1] - c[2] + c[3]) / s
             assert col[y] == pytest.approx(want, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# ordered subsets
+# ---------------------------------------------------------------------------
+
+def test_view_subsets_partition_interleaved():
+    subs = am.view_subsets(10, 3)
+    assert [list(x) for x in subs] == [[0, 3, 6, 9], [1, 4, 7], [2, 5, 8]]
+    assert sorted(np.concatenate(am.view_subsets(37, 4)).tolist()) == list(range(37))
+
+
+def test_one_subset_is_algorithm_1():
+    p = I.small_problem(16, 16, 12, 25, seed=81)
+    H = smx.system_matrix(p.geom)
+    kw = dict(expand_at=(2, 4), taus=(0.1, -1.0))
+    ref = am.wavelet_am(H, p.d, p.I0, 16, 16, 2, 6, **kw)
+    os1 = am.os_wavelet_am(H, p.d, p.I0, 16, 16, 2, 6, 1, p.geom.n_bins, **kw)
+    np.testing.assert_allclose(os1.beta, ref.beta, rtol=0, atol=1e-14 * np.abs(ref.beta).max())
+    np.testing.assert_allclose(os1.cost, ref.cost, rtol=1e-14)
+    for t1, t2 in zip(os1.tree, ref.tree):
+        np.testing.assert_array_equal(t1, t2)
+
+
+def test_each_subset_step_decreases_its_own_cost_and_subset_z0_is_bounded():
+    p = I.small_problem(16, 16, 12, 25, seed=82)
+    H = smx.system_matrix(p.geom)
+    r = am.os_wavelet_am(H, p.d, p.I0, 16, 16, 2, 5, 4, p.geom.n_bins, expand_at=(2,), taus=(0.05,))
+    # a sub-step minimises a majoriser of the subset's own I-divergence (Eq. 1.8 on the subset)
+    assert np.all(r.sub_cost[:, :, 1] <= r.sub_cost[:, :, 0] * (1 + 1e-12))
+    # Z0 of a subset is a max over fewer rays than the full Z0 of the same tree
+    Phi = (H @ haar.basis_matrix(16, 16, 2)).tocsr()
+    act = am.active_mask(am.empty_tree(16, 16, 2), 16, 16, 2)
+    z_full = np.max(np.asarray(abs(Phi[:, act]).sum(axis=1)).ravel())
+    assert np.all(r.z0[0] <= z_full * (1 + 1e-15)) and np.isclose(r.z0[0].max(), z_full, rtol=1e-15)
+
+
+def test_os_single_pixel_reaches_the_fixed_point_in_one_sub_step():
+    # one pixel, every ray of the same length h and the same counts: the first
+    # sub-step lands on mu* = ln(I0 / d) / h, later sub-steps stay there
+    h, I0, dv, n = 3.0, 1e4, 2500.0, 12
+    H = sp.csr_matrix(np.full((n, 1), h))
+    r = am.os_wavelet_am(H, np.full(n, dv), I0, 1, 1, 0, 3, 3, 1)
+    assert abs(r.beta[0] - np.log(I0 / dv) / h) <= 1e-14
