@@ -104,6 +104,13 @@ typedef struct {
     int precision;            /* 32 (FP32 bulk) or 64 (FP64 everywhere) */
     int full_am;              /* 1: plain AM, Omega = I, every pixel active */
     double dmax_clamp;        /* clamp on |Z0 * delta|; <= 0 means 30 */
+    int n_subsets;            /* ordered subsets of views (the Conclusion's combination with
+                                 ordered subsets): 0 or 1 = none; S > 1: subset s holds the views
+                                 k with k mod S = s, and each iteration runs S sub-iterations in
+                                 order, each one step of Algorithm 1 on its subset's rays with
+                                 that subset's b = Phi_s^T d_s, bhat+- and Z0 (max over its rays).
+                                 2-D contexts, wam_reconstruct only; idiv_hist still holds the
+                                 full I-divergence at the start of every iteration. */
 } wam_schedule;
 
 typedef struct wam_ctx wam_ctx;
@@ -190,10 +197,10 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
  * history I(d || qhat^(0..j)), the schedule it ran, the geometry, CRC-32
  * fingerprints of d and I0, and the back-projector tuning value; the file ends
  * with a CRC-32 of its contents and is written to "<path>.tmp" and renamed.
- * Format (little endian): "WAMCKPT1", u32 version 1, u32 0; 20 int64 (kind,
+ * Format (little endian): "WAMCKPT1", u32 version 1, u32 0; 21 int64 (kind,
  * nx, ny, nz, n_views, n_bins, n_rows, levels, dims, zsum_criterion,
  * precision, full_am, n_expand, iterations done, expansions done, N,
- * mask bytes, history length, crc(d), crc(I0)); 11 double (vx, vy, vz,
+ * mask bytes, history length, crc(d), crc(I0), n_subsets); 11 double (vx, vy, vz,
  * angle0, angle_span, bin_pitch, row_pitch, sod, sdd, dmax_clamp, tuning);
  * int64 expand_at[n_expand]; double tau[n_expand]; double beta[N];
  * u8 masks[mask bytes]; double history[iterations done + 1]; u32 crc.
@@ -208,7 +215,7 @@ wam_status wam_checkpoint(wam_ctx* ctx, const char* path);
  * The context's back-projector tuning is set to the checkpoint's.  Requires
  * data set (wam_set_data) equal to the checkpoint's (CRC-32 of d and I0) and
  * an equal geometry; the continuing schedule must have the same levels, dims,
- * zsum_criterion, precision, full_am and dmax_clamp, n_iters >= j, and the
+ * zsum_criterion, precision, full_am, dmax_clamp and n_subsets, n_iters >= j, and the
  * same first expansions (those applied so far) with no other expansion at or
  * before j, else that wam_reconstruct returns WAM_ERR_STATE and the loaded
  * state stays pending.  wam_set_data discards a pending state.

@@ -13,7 +13,7 @@ import numpy as np
 MAGIC = b"WAMCKPT1"
 INT_FIELDS = ("kind", "nx", "ny", "nz", "n_views", "n_bins", "n_rows", "levels", "dims", "zsum_criterion",
               "precision", "full_am", "n_expand", "iters_done", "expansions_done", "n_coef", "mask_bytes",
-              "n_hist", "crc_d", "crc_I0")
+              "n_hist", "crc_d", "crc_I0", "n_subsets")
 DBL_FIELDS = ("vx", "vy", "vz", "angle0", "angle_span", "bin_pitch", "row_pitch", "sod", "sdd", "dmax_clamp",
               "tuning")
 

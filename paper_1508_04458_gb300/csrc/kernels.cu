@@ -252,14 +252,19 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
 // ---------------------------------------------------------------------------
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_16a; };
 
 __device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
-__device__ __forceinline__ double4 ld4(const double4* p)
+__device__ __forceinline__ double4_16a ld4(const double4_16a* p)
 {
     const double2 lo = __ldg(reinterpret_cast<const double2*>(p));
     const double2 hi = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    return make_double4(lo.x, lo.y, hi.x, hi.y);
+    double4_16a r;
+    r.x = lo.x;
+    r.y = lo.y;
+    r.z = hi.x;
+    r.w = hi.y;
+    return r;
 }
 
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
@@ -898,12 +903,35 @@ __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// dst row k = src row perm[k] (rows of B elements): a scan's views in
+// another order
+template <typename E>
+__global__ void k_permute_rows(const E* __restrict__ src, E* __restrict__ dst, const int* __restrict__ perm,
+                               int V, int B)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)V * B) return;
+    const int k = (int)(i / B), b = (int)(i - (long long)k * B);
+    dst[i] = src[(long long)perm[k] * B + b];
+}
+
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
+
+template <typename E>
+cudaError_t launch_permute_rows(const E* src, E* dst, const int* perm, int V, int B, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_permute_rows<E><<<nblk((long long)V * B, 256), 256, 0, st>>>(src, dst, perm, V, B);
+    return cudaGetLastError();
+}
+template cudaError_t launch_permute_rows<float>(const float*, float*, const int*, int, int, cudaStream_t);
+template cudaError_t launch_permute_rows<double>(const double*, double*, const int*, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d,

@@ -27,6 +27,7 @@ enum BufId {
     B_PART, B_COSTPART, B_COSTS, B_Z0, B_SCRATCH, B_TMPA, B_TMPB, B_GIMG, B_SINO,
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
     B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER, B_MUT,
+    B_PERM, B_CSP32, B_CSP64, B_DIRP32, B_DIRP64, B_DP, B_I0P, B_DTP, B_BSUB, B_Z0SUB, B_SINOP,
     B_NBUF
 };
 
@@ -45,7 +46,7 @@ struct RunRecord {
     double clamp = 30.0;
     std::vector<int> expand_at;
     std::vector<double> tau;
-    int iters_done = 0, expansions_done = 0;
+    int iters_done = 0, expansions_done = 0, n_subsets = 1;
     double tuning = 32.0;
     std::vector<double> beta, hist;     // host copies (loaded state only)
     std::vector<uint8_t> mask;
@@ -83,17 +84,19 @@ wam_status fail(wam_ctx* c, wam_status s, const std::string& msg)
     return s;
 }
 
+// Return the status of a failing CUDA call (WCK) or library step (WST).  The
+// locals carry names no caller uses, so a macro argument can never see them.
 #define WCK(ctx, call)                                                                              \
     do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess)                                                                      \
-            return fail(ctx, WAM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+        cudaError_t wck_err_local = (call);                                                         \
+        if (wck_err_local != cudaSuccess)                                                           \
+            return fail(ctx, WAM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(wck_err_local)); \
     } while (0)
 
-#define WST(call)                       \
-    do {                                \
-        wam_status s_ = (call);         \
-        if (s_ != WAM_OK) return s_;    \
+#define WST(call)                                                    \
+    do {                                                             \
+        wam_status wst_status_local = (call);                        \
+        if (wst_status_local != WAM_OK) return wst_status_local;     \
     } while (0)
 
 // Grow-only device buffer.
@@ -154,6 +157,7 @@ void record_run(wam_ctx* c, const wam_schedule* sc, int iters, int expansions)
     r.tau.assign(sc->tau, sc->tau + sc->n_expand);
     r.iters_done = iters;
     r.expansions_done = expansions;
+    r.n_subsets = std::max(1, sc->n_subsets);
     r.tuning = c->back_ctas_per_sm;
     c->pending = RunRecord{};
 }
@@ -166,7 +170,7 @@ wam_status check_resume(wam_ctx* c, const wam_schedule* sc)
     if (!r.valid) return WAM_OK;
     const int L = sc->full_am ? 0 : sc->levels;
     if (L != r.levels || sc->full_am != r.full_am || sc->precision != r.precision || eff_dims(c, sc) != r.dims ||
-        sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp)
+        sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp || std::max(1, sc->n_subsets) != r.n_subsets)
         return fail(c, WAM_ERR_STATE, "resume: the schedule's method differs from the checkpoint's");
     if (sc->n_iters < r.iters_done) return fail(c, WAM_ERR_STATE, "resume: n_iters is below the iterations done");
     if (L > 0) {
@@ -333,9 +337,10 @@ struct ListInfo {
 // Split every list into view ranges so that the grid is about one full wave
 // of 256-thread CTAs (8 per SM) with similar work (chord evaluations) each.
 template <typename T>
-wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTable* tab, T** part_out)
+wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTable* tab, T** part_out, int nv = 0)
 {
     const wam_geometry& w = c->g;
+    const int V = nv > 0 ? nv : w.n_views;     // views of the scan (or view subset) back-projected
     std::memset(tab, 0, sizeof(*tab));
     const double mag = (w.kind == WAM_FAN2D_FLAT) ? 1.2 * w.sdd / w.sod : 1.0;
     const double diag = std::sqrt(w.vx * w.vx + w.vy * w.vy);
@@ -344,11 +349,11 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
     for (size_t i = 0; i < lists.size(); ++i) {
         const double shadow = (double)(1 << lists[i].level) * diag * mag / w.bin_pitch + 1.0;
         cost[i] = shadow * ((lists[i].has_details || lists[i].quad) ? 3.0 : 1.0);
-        total += (double)lists[i].n * w.n_views * cost[i];
+        total += (double)lists[i].n * V * cost[i];
     }
     const double target_ctas = (double)c->num_sms * c->back_ctas_per_sm;
     const double per_cta = std::max(total / target_ctas, 1.0);
-    const int max_chunks = std::max(1, w.n_views / kViewLanes);
+    const int max_chunks = std::max(1, V / kViewLanes);
     int cta = 0, items = 0;
     long long part = 0;
     for (size_t i = 0; i < lists.size(); ++i) {
@@ -363,11 +368,11 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         s.n_items = li.n;
         s.items = li.items;
         s.gw = li.gw;
-        const double full = (double)kItemsPerCta * w.n_views * cost[i];
+        const double full = (double)kItemsPerCta * V * cost[i];
         int chunks = (int)std::ceil(full / per_cta);
         chunks = std::max(1, std::min(chunks, max_chunks));
-        s.vpc = (w.n_views + chunks - 1) / chunks;
-        s.n_chunks = (w.n_views + s.vpc - 1) / s.vpc;
+        s.vpc = (V + chunks - 1) / chunks;
+        s.n_chunks = (V + s.vpc - 1) / s.vpc;
         s.tiles = (li.n + kItemsPerCta - 1) / kItemsPerCta;
         s.cta_begin = cta;
         s.item_begin = items;
@@ -386,12 +391,12 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
 // products with the view's sin and -cos, computed in FP64 on the host once
 // per context and precision.
 template <typename T>
-wam_status dir_table(wam_ctx* c, const void** out)
+wam_status dir_table(wam_ctx* c, const void** out, const std::vector<int>* order = nullptr)
 {
-    const BufId id = sizeof(T) == 4 ? B_DIR32 : B_DIR64;
+    const BufId id = order ? (sizeof(T) == 4 ? B_DIRP32 : B_DIRP64) : (sizeof(T) == 4 ? B_DIR32 : B_DIR64);
     const wam_geometry& w = c->g;
     const size_t n = (size_t)w.n_views * w.n_bins;
-    if (c->buf[id].p && c->buf[id].bytes >= n * 4 * sizeof(T)) {
+    if (!order && c->buf[id].p && c->buf[id].bytes >= n * 4 * sizeof(T)) {
         *out = c->buf[id].p;
         return WAM_OK;
     }
@@ -403,7 +408,8 @@ wam_status dir_table(wam_ctx* c, const void** out)
         return std::signbit(d) ? -1.0 / a : 1.0 / a;
     };
     for (int k = 0; k < w.n_views; ++k) {
-        const double th = w.angle0 + k * (w.angle_span / w.n_views);
+        const int view = order ? (*order)[k] : k;     // row k of the table holds this view
+        const double th = w.angle0 + view * (w.angle_span / w.n_views);
         const double cs = std::cos(th), sn = std::sin(th);
         for (int b = 0; b < w.n_bins; ++b) {
             double dx = cs, dy = sn;
@@ -431,7 +437,7 @@ wam_status dir_table(wam_ctx* c, const void** out)
 // Pixel basis (Omega = I): items are 2x2 pixel quads when both sides are
 // even (one shadow per quad, four chords per ray), else single pixels.
 template <typename T>
-wam_status plan_pixels(wam_ctx* c, SegTable* tab, T** part)
+wam_status plan_pixels(wam_ctx* c, SegTable* tab, T** part, int nv = 0)
 {
     const int nx = c->g.nx, ny = c->g.ny;
     std::vector<ListInfo> lists;
@@ -442,14 +448,14 @@ wam_status plan_pixels(wam_ctx* c, SegTable* tab, T** part)
     } else {
         lists.push_back({0, 1, 0, (int)c->N, nullptr, nx});
     }
-    return plan_segments<T>(c, lists, tab, part);
+    return plan_segments<T>(c, lists, tab, part, nv);
 }
 
 // Rebuild leaf map, block lists and work plan from the mask (device); reads
 // the list lengths back (one small synchronous copy).
 template <typename T>
 wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t* leaf, SegTable* tab, T** part,
-                     cudaStream_t st)
+                     cudaStream_t st, int nv = 0)
 {
     PROF(WAM_K_TREE);
     WCK(c, launch_leafmap(lay, mask, leaf, st));
@@ -476,7 +482,7 @@ wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t
     li.push_back({L, 1, 0, h[0], lists, lay.gw[L]});
     li.push_back({L, 1, 1, h[1], lists + stride, lay.gw[L]});
     for (int k = 1; k < L; ++k) li.push_back({L - k, 0, 1, h[k + 1], lists + stride * (k + 1), lay.gw[L - k]});
-    return plan_segments<T>(c, li, tab, part);
+    return plan_segments<T>(c, li, tab, part, nv);
 }
 
 template <typename T>
@@ -563,6 +569,16 @@ struct Run {
     std::vector<int> exp_at;
     size_t next_exp = 0;
     int j0 = 0;                 // first iteration to run (> 0 when resuming)
+    // ordered subsets of views: the scan is held in subset-major view order
+    // (subset s = views k with k mod S = s, rows sv0[s] .. sv0[s] + svn[s] - 1)
+    int S = 1;
+    std::vector<int> sv0, svn;
+    std::vector<Geom<T>> gsub;  // each subset as a scan of its own
+    Geom<T> gperm{};            // the whole scan in subset-major order
+    const float *dP = nullptr, *I0P = nullptr;
+    const double* dtP = nullptr;
+    const void* dirP = nullptr;
+    double *bsub = nullptr, *z0sub = nullptr;   // per subset: b (Eq. 1.6 on its rays), Z0
 
     // How a2 walks the tree's image mu, which is constant on the leaves and
     // so on the cells of the finest leaf level lam: the strip walk over the
@@ -654,7 +670,159 @@ struct Run {
                       sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
         next_exp = 0;
         j0 = 0;
+        S = std::max(1, sc->n_subsets);
+        if (S > 1) WST(setup_subsets(st));
         if (c->pending.valid) WST(load_pending(st));
+        return WAM_OK;
+    }
+
+    // The views in subset-major order (cos/sin, direction table, d, I0, the
+    // cost constants), each subset's b and the block plan for a subset's
+    // view count; then the subsets' Z0.
+    wam_status setup_subsets(cudaStream_t st)
+    {
+        const wam_geometry& w = c->g;
+        const int V = w.n_views, B = w.n_bins;
+        std::vector<int> perm;
+        perm.reserve(V);
+        sv0.assign(S, 0);
+        svn.assign(S, 0);
+        for (int ss = 0; ss < S; ++ss) {
+            sv0[ss] = (int)perm.size();
+            for (int k = ss; k < V; k += S) perm.push_back(k);
+            svn[ss] = (int)perm.size() - sv0[ss];
+        }
+        int* dperm = nullptr;
+        WST(ensure_t(c, B_PERM, (size_t)V, &dperm));
+        WCK(c, cudaMemcpyAsync(dperm, perm.data(), V * sizeof(int), cudaMemcpyHostToDevice, st));
+        std::vector<T> csh(2 * (size_t)V);
+        for (int k = 0; k < V; ++k) {
+            const double th = w.angle0 + perm[k] * (w.angle_span / V);
+            csh[2 * k] = (T)std::cos(th);
+            csh[2 * k + 1] = (T)std::sin(th);
+        }
+        T* csp = nullptr;
+        WST(ensure_t(c, sizeof(T) == 4 ? B_CSP32 : B_CSP64, csh.size(), &csp));
+        WCK(c, cudaMemcpyAsync(csp, csh.data(), csh.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+        float *dp = nullptr, *ip = nullptr;
+        double* dtp = nullptr;
+        WST(ensure_t(c, B_DP, (size_t)M, &dp));
+        WST(ensure_t(c, B_I0P, (size_t)M, &ip));
+        WST(ensure_t(c, B_DTP, (size_t)M, &dtp));
+        WCK(c, launch_permute_rows<float>(dsino, dp, dperm, V, B, st));
+        WCK(c, launch_permute_rows<float>(I0, ip, dperm, V, B, st));
+        WCK(c, launch_permute_rows<double>(dterm, dtp, dperm, V, B, st));
+        dP = dp;
+        I0P = ip;
+        dtP = dtp;
+        WST(dir_table<T>(c, &dirP, &perm));
+        gperm = g;
+        gperm.cs = csp;
+        gsub.assign(S, g);
+        for (int ss = 0; ss < S; ++ss) {
+            gsub[ss].V = svn[ss];
+            gsub[ss].cs = csp + 2 * (size_t)sv0[ss];
+        }
+        // b_s = Phi_s^T d_s = Omega^T (H_s^T d_s) for every coefficient
+        WST(ensure_t(c, B_BSUB, (size_t)S * N, &bsub));
+        WST(ensure_t(c, B_Z0SUB, (size_t)S, &z0sub));
+        const T* dTP;
+        if (sizeof(T) == sizeof(float)) {
+            dTP = reinterpret_cast<const T*>(dp);
+        } else {
+            T* sp = nullptr;
+            WST(ensure_t(c, B_SINOP, (size_t)M, &sp));
+            WCK(c, launch_permute_rows<T>(sino, sp, dperm, V, B, st));
+            dTP = sp;
+        }
+        SegTable pix;
+        T* ppart = nullptr;
+        WST(plan_pixels<T>(c, &pix, &ppart, svn[0]));
+        for (int ss = 0; ss < S; ++ss) {
+            const size_t off = (size_t)sv0[ss] * B;
+            {
+                PROF(WAM_K_BACKPROJECT);
+                WCK(c, launch_backproject(gsub[ss], pix, dTP + off, dir_rows(off), ppart,
+                                          work_ptr(c, WAM_K_BACKPROJECT), st));
+            }
+            PROF(WAM_K_TREE);
+            WCK(c, (launch_reduce_pixels<T, double>(pix, c->g.nx, N, ppart, gimg, st)));
+            WCK(c, launch_haar(lay, gimg, bsub + (size_t)ss * N, 0, tmpa, tmpb, st));
+        }
+        if (L == 0) {
+            WST(plan_pixels<T>(c, &tab, &part, svn[0]));
+            PROF(WAM_K_Z0);
+            for (int ss = 0; ss < S; ++ss) WST(compute_z0<T>(c, gsub[ss], lay, leaf, z0sub + ss, st));
+            return WAM_OK;
+        }
+        return replan(st);
+    }
+
+    // direction-table rows from ray `off` of the subset-major table
+    const void* dir_rows(size_t off) const
+    {
+        return static_cast<const void*>(static_cast<const T*>(dirP) + 4 * off);
+    }
+
+    // block plan, forward walk and Z0 (per subset) for the current tree
+    wam_status replan(cudaStream_t st)
+    {
+        if (L > 0) {
+            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st, S > 1 ? svn[0] : 0));
+            fwd_leaf = pick_leaf();
+        }
+        PROF(WAM_K_Z0);
+        if (S > 1) {
+            for (int ss = 0; ss < S; ++ss) WST(compute_z0<T>(c, gsub[ss], lay, leaf, z0sub + ss, st));
+        } else {
+            WST(compute_z0<T>(c, g, lay, leaf, z0, st));                                  // a5
+        }
+        return WAM_OK;
+    }
+
+    // a1 + a2 + a3 on a scan (the whole one or a subset): qhat into qq and,
+    // with cp, the cost partials
+    wam_status fwd(const Geom<T>& gg, const float* dd, const double* dt, const float* ii, T* qq, double* cp,
+                   cudaStream_t st)
+    {
+        if (fwd_leaf) {
+            {
+                PROF(WAM_K_SYNTH);
+                WCK(c, launch_synth(lay, leaf, beta, mu, st));
+            }
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_forward(gg, mu, mut, fwd_leaf, 0, dd, dt, ii, qq, (T*)nullptr, (T*)nullptr, cp,
+                                  work_ptr(c, WAM_K_FORWARD), st));
+        } else {
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_forward_tree(gg, lay, L > 0 ? leaf : nullptr, beta, fwd_lam, mut, dd, dt, ii, qq,
+                                       (T*)nullptr, (T*)nullptr, cp, work_ptr(c, WAM_K_FORWARD), st));
+        }
+        return WAM_OK;
+    }
+
+    // one iteration with ordered subsets: the full cost at beta^(j) (its qhat
+    // rows of subset 0 serve the first sub-iteration), then per subset a2-a4
+    // on its rays and a6 with its b and Z0
+    wam_status iteration_os(int j, cudaStream_t st)
+    {
+        const int B = c->g.n_bins;
+        WST(fwd(gperm, dP, dtP, I0P, q, cpart, st));
+        {
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_sum_final(cpart, np, costs + j, st));
+        }
+        for (int ss = 0; ss < S; ++ss) {
+            const size_t off = (size_t)sv0[ss] * B;
+            if (ss > 0) WST(fwd(gsub[ss], dP + off, dtP + off, I0P + off, q + off, nullptr, st));
+            {
+                PROF(WAM_K_BACKPROJECT);
+                WCK(c, launch_backproject(gsub[ss], tab, q + off, dir_rows(off), part,
+                                          work_ptr(c, WAM_K_BACKPROJECT), st));
+            }
+            PROF(WAM_K_UPDATE);
+            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, st));
+        }
         return WAM_OK;
     }
 
@@ -670,10 +838,7 @@ struct Run {
         WCK(c, cudaMemcpyAsync(costs, r.hist.data(), r.hist.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         if (L > 0) {
             WCK(c, cudaMemcpyAsync(mask, r.mask.data(), lay.mask_bytes, cudaMemcpyHostToDevice, st));
-            WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
-            fwd_leaf = pick_leaf();
-            PROF(WAM_K_Z0);
-            WST(compute_z0<T>(c, g, lay, leaf, z0, st));
+            WST(replan(st));
         }
         next_exp = (size_t)r.expansions_done;
         j0 = r.iters_done;
@@ -684,6 +849,7 @@ struct Run {
     // costs[*counter] (then counter + 1) instead of costs[j]
     wam_status iteration(int j, cudaStream_t st, bool use_counter)
     {
+        if (S > 1) return iteration_os(j, st);
         if (fwd_leaf) {
             PROF(WAM_K_SYNTH);
             WCK(c, launch_synth(lay, leaf, beta, mu, st));                                  // a1
@@ -728,13 +894,7 @@ struct Run {
         }
         std::swap(mask, mask2);
         std::swap(c->buf[B_MASK_A], c->buf[B_MASK_B]);
-        WST(plan_tree<T>(c, lay, mask, leaf, &tab, &part, st));
-        fwd_leaf = pick_leaf();
-        {
-            PROF(WAM_K_Z0);
-            WST(compute_z0<T>(c, g, lay, leaf, z0, st));                                  // a5
-        }
-        return WAM_OK;
+        return replan(st);
     }
 
     wam_status final_cost(cudaStream_t st, bool use_counter)
@@ -1392,6 +1552,10 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
     if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
     if (sc->n_iters < 0) return fail(c, WAM_ERR_ARG, "n_iters must be >= 0");
     if (sc->precision != 32 && sc->precision != 64) return fail(c, WAM_ERR_ARG, "precision must be 32 or 64");
+    if (sc->n_subsets < 0 || sc->n_subsets > c->g.n_views)
+        return fail(c, WAM_ERR_ARG, "n_subsets must be in 0..n_views");
+    if (sc->n_subsets > 1 && c->g.kind == WAM_CONE3D_FLAT_CIRCULAR)
+        return fail(c, WAM_ERR_ARG, "ordered subsets: 2-D contexts only");
     if (sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c, WAM_ERR_ARG, "expand_at/tau missing");
     for (int k = 0; k < sc->n_expand; ++k) {
@@ -1433,9 +1597,10 @@ wam_status wam_checkpoint(wam_ctx* c, const char* path)
         const uint32_t version = 1, zero = 0;
         w.raw(&version, 4);
         w.raw(&zero, 4);
-        const long long ints[20] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
+        const long long ints[21] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
                                     r.zsum, r.precision, r.full_am, (long long)r.expand_at.size(), r.iters_done,
-                                    r.expansions_done, c->N, (long long)mb, (long long)hist.size(), cd, ci};
+                                    r.expansions_done, c->N, (long long)mb, (long long)hist.size(), cd, ci,
+                                    r.n_subsets};
         for (long long v : ints) w.i64(v);
         const double dbl[11] = {g.vx, g.vy, g.vz, g.angle0, g.angle_span, g.bin_pitch, g.row_pitch, g.sod, g.sdd,
                                 r.clamp, r.tuning};
@@ -1491,7 +1656,7 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         uint32_t version = 0, zero = 0;
         if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || version != 1)
             return fail(c, WAM_ERR_IO, "unsupported checkpoint version");
-        long long v[20];
+        long long v[21];
         double d[11];
         for (long long& x : v)
             if (!rd.i64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
@@ -1516,12 +1681,14 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         const long long n_expand = v[12];
         r.iters_done = (int)v[13];
         r.expansions_done = (int)v[14];
+        r.n_subsets = (int)v[20];
         r.clamp = d[9];
         r.tuning = d[10];
         const size_t mb = r.levels > 0 ? wam_mask_bytes_dims(c, r.levels, r.dims) : 0;
         if (r.levels < 0 || r.levels > WAM_MAX_LEVELS || n_expand < 0 || n_expand > 4096 || r.iters_done < 0 ||
             r.expansions_done < 0 || r.expansions_done > n_expand || v[15] != c->N || v[16] != (long long)mb ||
-            v[17] != (long long)r.iters_done + 1 || !(r.tuning >= 0.25 && r.tuning <= 256.0))
+            v[17] != (long long)r.iters_done + 1 || !(r.tuning >= 0.25 && r.tuning <= 256.0) || r.n_subsets < 1 ||
+            r.n_subsets > c->g.n_views)
             return fail(c, WAM_ERR_IO, "checkpoint header is inconsistent with this context");
         r.expand_at.resize((size_t)n_expand);
         r.tau.resize((size_t)n_expand);
@@ -1772,6 +1939,7 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
     }
     wam_ctx* c0 = ctxs[0];
     if (sc->precision != 32) return fail(c0, WAM_ERR_ARG, "batched reconstruction runs in precision 32");
+    if (sc->n_subsets > 1) return fail(c0, WAM_ERR_ARG, "batched reconstruction has no ordered subsets");
     if (sc->n_iters < 0 || sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c0, WAM_ERR_ARG, "bad schedule");
     for (int k = 0; k < sc->n_expand; ++k)
