@@ -180,9 +180,9 @@ def run_wam(args, problem, world, rank, local_rank):
     d_dev = torch.from_numpy(problem.d.astype(np.float32).ravel()).to(dev)
     ctx.set_data(d_dev, problem.I0)
 
-    def step(n_iters=N_ITERS, levels=L_LEVELS, full=False):
+    def step(n_iters=N_ITERS, levels=L_LEVELS, full=False, n_subsets=1):
         return ctx.reconstruct(levels, n_iters, () if full else EXPAND_AT, () if full else TAU,
-                               precision=32, full_am=full, device_out=True)
+                               precision=32, full_am=full, device_out=True, n_subsets=n_subsets)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
@@ -267,6 +267,28 @@ def run_wam(args, problem, world, rank, local_rank):
         curve.append({"full_am_iters": k, "target_idiv": tgt, "full_am_ms": t_full,
                       "multires_iters": int(jh[0]) if jh.size else None, "multires_ms": t_mr})
 
+    # ---- ordered subsets of views (the Conclusion's combination with ordered
+    # subsets): the same schedules with S interleaved view subsets, time to
+    # plain AM's final cost (+1e-3)
+    def os_run(full, n_sub, n_max):
+        step(n_iters=N_ITERS, full=full, levels=0 if full else L_LEVELS, n_subsets=n_sub)
+        (_, h100, _, _), ms100 = timed(lambda: step(n_iters=N_ITERS, full=full, levels=0 if full else L_LEVELS,
+                                                    n_subsets=n_sub))
+        h = h100.cpu().numpy()
+        if n_max > N_ITERS:
+            (_, hl, _, _), _ = timed(lambda: step(n_iters=n_max, full=full, levels=0 if full else L_LEVELS,
+                                                  n_subsets=n_sub))
+            h = hl.cpu().numpy()
+        jh = np.nonzero(h <= target)[0]
+        t_hit = None
+        if jh.size:
+            _, t_hit = timed(lambda: step(n_iters=int(jh[0]), full=full, levels=0 if full else L_LEVELS,
+                                          n_subsets=n_sub))
+        return {"n_subsets": n_sub, "iters_per_s": N_ITERS / (ms100 / 1e3),
+                "idiv_after_%d" % N_ITERS: float(h100.cpu().numpy()[-1]),
+                "iters_to_target": int(jh[0]) if jh.size else None, "time_to_target_ms": t_hit}
+    ordered = {"multires": os_run(False, 16, TTT_MAX_ITERS), "full_am": os_run(True, 8, N_ITERS)}
+
     # ---- e2e through the C-ABI from host buffers
     d_host = np.ascontiguousarray(problem.d.astype(np.float32).ravel())
     torch.cuda.synchronize()
@@ -338,6 +360,7 @@ def run_wam(args, problem, world, rank, local_rank):
                         "ms_per_iter": full_ms2 / N_ITERS, "time_to_target_ms": full_ms2},
             "target_idiv": target,
             "time_to_equal_objective": curve,
+            "ordered_subsets": ordered,
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "work": v["work"]}
                         for k, v in stats.items()},
             "wall_s_timed": wall,
