@@ -140,10 +140,19 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
     }
     add_work(work, steps);
     if (cost_part) {
-        // one partial per warp: no CTA barrier behind the longest ray
+        // one partial per CTA: warp sums, then the warps in a fixed order (a
+        // CTA's slot frees only when its last warp ends, so the barrier costs
+        // no occupancy)
+        __shared__ double wsum[kFwdTPB / 32];
         term = warp_reduce(term, OpSum());
-        if ((threadIdx.x & 31) == 0)
-            cost_part[(blockIdx.y * gridDim.x + blockIdx.x) * (kFwdTPB / 32) + (threadIdx.x >> 5)] = term;
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = term;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = wsum[0];
+#pragma unroll
+            for (int w = 1; w < kFwdTPB / 32; ++w) t += wsum[w];
+            cost_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
     }
 }
 
@@ -183,25 +192,27 @@ __global__ void k_max_final(const double* __restrict__ part, int n, double* __re
 // convex block is crossed in one contiguous run of leaves, so an ancestor's
 // |phi| terms are final when the next ancestor of that level appears.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int LM>
 __global__ void __launch_bounds__(kFwdTPB)
 k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict__ part)
 {
+    // LM = the tree's level count (0..kMaxLevels): the per-level loops unroll
+    // exactly, with compile-time bounds
     const int v = blockIdx.y;
     const int b = blockIdx.x * kFwdTPB + threadIdx.x;
     double rowsum = 0.0;
     if (b < g.B) {
         Ray<T> r;
         if (make_ray(g, v, b, r)) {
-            T acc[kMaxLevels][4];
-            int cur[kMaxLevels];
+            T acc[LM > 0 ? LM : 1][4];
+            int cur[LM > 0 ? LM : 1];
 #pragma unroll
-            for (int l = 0; l < kMaxLevels; ++l) {
+            for (int l = 0; l < LM; ++l) {
                 cur[l] = -1;
                 acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = T(0);
             }
             T total = T(0), rs = T(0);
-            const int L = lay.L;
+            const int L = LM;
             auto flush = [&](int li) {
                 if (cur[li] >= 0) {
                     const T* a = acc[li];
@@ -214,9 +225,9 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
             traverse(g, leaf, r, [&](int ix, int iy, int lam, int bx0, int by0, T c) {
                 total += c;
 #pragma unroll
-                for (int li = 0; li < kMaxLevels; ++li) {
+                for (int li = 0; li < LM; ++li) {
                     const int l = li + 1;
-                    if (l > lam && l <= L) {
+                    if (l > lam) {
                         const int id = ((iy >> l) << 16) | (ix >> l);
                         if (id != cur[li]) { flush(li); cur[li] = id; }
                         const int q = (((by0 >> li) & 1) << 1) | ((bx0 >> li) & 1);
@@ -228,7 +239,7 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
                 }
             });
 #pragma unroll
-            for (int li = 0; li < kMaxLevels; ++li) flush(li);
+            for (int li = 0; li < LM; ++li) flush(li);
             rowsum = (double)rs + (double)total * pow2m(L);
         }
     }
@@ -576,38 +587,69 @@ __device__ __forceinline__ double am_step(double b, double bp, double bm, double
     return am_delta(b, bp, bm, z0, clamp);
 }
 
+// Sum of one slot of an item over the view chunks c = lane, lane + 8, ... of
+// one lane of a group of 8 (fixed order within the lane).
+template <int G, typename T>
+__device__ __forceinline__ T sum_slot_lane(const Segment& S, const T* __restrict__ part, int item, int slot, int lane)
+{
+    T s = T(0);
+    const T* p = part + S.part_off + (size_t)slot * S.n_items + item;
+    const size_t stride = (size_t)S.n_slots * S.n_items;
+    for (int c = lane; c < S.n_chunks; c += G) s += p[c * stride];
+    return s;
+}
+
+// The G lanes' sums of a group added by a fixed butterfly (every lane gets
+// the same total).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T x)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 // a6: reduce the partials of each item and apply the AM update to beta.  One
-// thread per coefficient: thread 4 i + k of item i takes pixel k of a quad,
-// or (k = 0) the approximation and (k = 1..3) detail type k of a block.
-template <typename T>
+// group of G lanes per coefficient: coefficient 4 i + k of item i is pixel k
+// of a quad, or (k = 0) the approximation and (k = 1..3) detail type k of a
+// block; the lanes split the item's view-chunk partials, a fixed butterfly
+// adds them, and lane 0 applies the update.  G = 8 when the items are few
+// (coarse trees, whose items carry many view chunks), else 1.
+template <typename T, int G>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= 4LL * tab.total_items) return;
-    const int it = (int)(gid >> 2), k = (int)(gid & 3);
-    const Segment& S = tab.s[find_item_segment(tab, it)];
-    const int item = it - S.item_begin;
-    int bx, by;
-    item_block(S, item, bx, by);
+    const long long cf = gid / G;
+    const int lane8 = (int)(gid % G);
+    long long z = -1;
+    T bp = T(0), bm = T(0);
+    if (cf < 4LL * tab.total_items) {      // every lane reaches the shuffles below
+        const int it = (int)(cf >> 2), k = (int)(cf & 3);
+        const Segment& S = tab.s[find_item_segment(tab, it)];
+        const int item = it - S.item_begin;
+        int bx, by;
+        item_block(S, item, bx, by);
+        if (S.quad) {
+            z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
+            bp = sum_slot_lane<G>(S, part, item, k, lane8);
+        } else if (k == 0) {
+            if (S.has_approx) {
+                z = approx_index(lay, S.level, bx, by);
+                bp = sum_slot_lane<G>(S, part, item, 0, lane8);
+            }
+        } else if (S.has_details) {
+            const int t = k - 1, slot = (S.has_approx ? 1 : 0) + 2 * t;
+            z = detail_index(lay, S.level, t, bx, by);
+            bp = sum_slot_lane<G>(S, part, item, slot, lane8);
+            bm = sum_slot_lane<G>(S, part, item, slot + 1, lane8);
+        }
+    }
+    bp = group_sum<G>(bp);
+    bm = group_sum<G>(bm);
+    if (z < 0 || lane8 != 0) return;
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
-    if (S.quad) {
-        const long long z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
-        beta[z] += am_step(bvec[z], sum_slot(S, part, item, k), T(0), z0, iz0, clamp);
-        return;
-    }
-    if (k == 0) {
-        if (!S.has_approx) return;
-        const long long z = approx_index(lay, S.level, bx, by);
-        beta[z] += am_step(bvec[z], sum_slot(S, part, item, 0), T(0), z0, iz0, clamp);
-        return;
-    }
-    if (!S.has_details) return;
-    const int t = k - 1, slot = (S.has_approx ? 1 : 0) + 2 * t;
-    const long long z = detail_index(lay, S.level, t, bx, by);
-    const T bp = sum_slot(S, part, item, slot);
-    const T bm = sum_slot(S, part, item, slot + 1);
     beta[z] += am_step(bvec[z], bp, bm, z0, iz0, clamp);
 }
 
@@ -988,6 +1030,7 @@ cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8
 }
 
 int forward_parts(int V, int B) { return (int)nblk(B, kFwdTPB) * V * (kFwdTPB / 32); }
+int forward_cost_parts(int V, int B) { return (int)nblk(B, kFwdTPB) * V; }
 
 cudaError_t launch_sum_final(const double* part, int n, double* out, cudaStream_t st)
 {
@@ -1015,7 +1058,18 @@ cudaError_t launch_z0(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, 
 {
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
     COUNT_LAUNCH();
-    k_z0<T><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
+    switch (lay.L) {
+    case 0: k_z0<T, 0><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 1: k_z0<T, 1><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 2: k_z0<T, 2><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 3: k_z0<T, 3><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 4: k_z0<T, 4><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 5: k_z0<T, 5><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 6: k_z0<T, 6><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 7: k_z0<T, 7><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    case 8: k_z0<T, 8><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -1036,7 +1090,10 @@ cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part,
 {
     if (tab.total_items == 0) return cudaSuccess;
     COUNT_LAUNCH();
-    k_update<T><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    if (tab.total_items < 16384)
+        k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    else
+        k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
     return cudaGetLastError();
 }
 

@@ -550,7 +550,7 @@ template <typename T>
 struct Run {
     wam_ctx* c = nullptr;
     const wam_schedule* sc = nullptr;
-    int L = 0, J = 0, np = 0;
+    int L = 0, J = 0, np = 0, npc = 0;   // partial buffer size; cost partials of one forward
     double clamp = 30.0;
     long long N = 0, M = 0;
     Layout lay{};
@@ -621,6 +621,7 @@ struct Run {
         WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
         WST(ensure_t(c, B_COUNTER, 1, &counter));
         np = forward_parts(g.V, g.B);
+        npc = forward_cost_parts(g.V, g.B);
         WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
         if (L > 0) {
             WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
@@ -810,7 +811,7 @@ struct Run {
         WST(fwd(gperm, dP, dtP, I0P, q, cpart, st));
         {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_sum_final(cpart, np, costs + j, st));
+            WCK(c, launch_sum_final(cpart, npc, costs + j, st));
         }
         for (int ss = 0; ss < S; ++ss) {
             const size_t off = (size_t)sv0[ss] * B;
@@ -862,8 +863,8 @@ struct Run {
             else
                 WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, beta, fwd_lam, mut, dsino, dterm, I0, q,
                                            (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
-            if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
-            else WCK(c, launch_sum_final(cpart, np, costs + j, st));
+            if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
+            else WCK(c, launch_sum_final(cpart, npc, costs + j, st));
         }
         {
             PROF(WAM_K_BACKPROJECT);                                                        // a4
@@ -907,8 +908,8 @@ struct Run {
             PROF(WAM_K_FORWARD);
             WCK(c, launch_forward(g, mu, mut, fwd_leaf, fwd_lam, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                   work_ptr(c, WAM_K_FORWARD), st));
-            if (use_counter) WCK(c, launch_sum_at(cpart, np, costs, counter, st));
-            else WCK(c, launch_sum_final(cpart, np, costs + J, st));
+            if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
+            else WCK(c, launch_sum_final(cpart, npc, costs + J, st));
         }
         return WAM_OK;
     }
@@ -1028,7 +1029,7 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
                              static_cast<const double*>(c->buf[B_DTERM].p),
                              static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr, cpart, nullptr,
                              st));
-    WCK(c, launch_sum_final(cpart, np, cost, st));
+    WCK(c, launch_sum_final(cpart, forward_cost_parts(g.V, g.B), cost, st));
     return WAM_OK;
 }
 
@@ -2191,11 +2192,12 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
         WST(sino_to_coef(c, lay, res, &coef, st));
         const int nl1 = (int)((c->N + 255) / 256);
         double* l1 = nullptr;
-        WST(ensure_t(c, B_L1PART, (size_t)nl1 + np, &l1));
+        const int npc = forward_cost_parts(g.V, g.B);
+        WST(ensure_t(c, B_L1PART, (size_t)nl1 + npc, &l1));
         WCK(c, launch_l1(lay, beta, coef, lambda, grad, l1, nl1, st));
         // loss = sum of the cost partials and the L1 partials, fixed order
-        WCK(c, cudaMemcpyAsync(l1 + nl1, cpart, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        WCK(c, launch_sum_final(l1, nl1 + np, loss, st));
+        WCK(c, cudaMemcpyAsync(l1 + nl1, cpart, npc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        WCK(c, launch_sum_final(l1, nl1 + npc, loss, st));
         return WAM_OK;
     } catch (...) {
         return fail(c, WAM_ERR_OOM, "host allocation failed");

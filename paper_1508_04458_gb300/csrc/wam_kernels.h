@@ -21,6 +21,7 @@ cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8
                                 int lam, T* pad, const float* d, const double* dterm, const float* I0, T* qhat,
                                 T* p_out, T* resid, double* cost_part, unsigned long long* work, cudaStream_t st);
 int forward_parts(int V, int B);
+int forward_cost_parts(int V, int B);   // cost partials a forward launch writes (one per CTA)
 // dst row k = src row perm[k], rows of B elements (views of a scan reordered)
 template <typename E>
 cudaError_t launch_permute_rows(const E* src, E* dst, const int* perm, int V, int B, cudaStream_t st);
