@@ -157,14 +157,120 @@ __device__ __forceinline__ void walk3(const Geom3& g, const uint8_t* __restrict_
     }
 }
 
+// Exact voxel walk by in-plane strips: the 2-D strip walk with z as a second
+// minor axis.  The major axis is the in-plane one whose grid lines the ray
+// crosses most often per unit length; when z's lines are crossed no more often
+// (strip3_ok), a strip holds at most one crossing of the in-plane minor axis
+// and one of z, so one to three voxels, visited in travel order: the crossing
+// with the longer piece beyond it comes first.  Both minor positions are
+// tracked in oriented voxel units from the entry voxel's edges; the two end
+// strips are peeled.  Voxels are addressed in a volume with a one-voxel zero
+// apron on every side, (nz + 2) slabs of (nm + 2) strips of (nn + 2):
+// lin = ((k + 1)(nm + 2) + (j + 1))(nn + 2) + (c + 1), j the strip, c the minor
+// index, k the slice; x-major rays read a copy with x and y exchanged.  A step
+// across a face of the volume (only in the exit strip) lands on the apron
+// and reads 0, so no range test is needed.  visit(la, ca, lb, cb, lc, cc)
+// once per strip.
+__device__ __forceinline__ bool strip3_ok(const Geom3& g, const Ray3& r, bool& ymaj)
+{
+    const float ax = fabsf(r.dx) * g.ivx, ay = fabsf(r.dy) * g.ivy, az = fabsf(r.dz) * g.ivz;
+    ymaj = ay >= ax;
+    return az <= fmaxf(ax, ay);
+}
+
+template <typename F>
+__device__ __forceinline__ void traverse_strips3(const Geom3& g, const Ray3& r, bool ymaj, F&& visit)
+{
+    const float pm = ymaj ? r.py : r.px, pn = ymaj ? r.px : r.py;
+    const float dm = ymaj ? r.dy : r.dx, dn = ymaj ? r.dx : r.dy;
+    const float vm = ymaj ? g.vy : g.vx, vn = ymaj ? g.vx : g.vy;
+    const float ivm = ymaj ? g.ivy : g.ivx, ivn = ymaj ? g.ivx : g.ivy;
+    const float M0 = ymaj ? g.Y0 : g.X0, N0 = ymaj ? g.X0 : g.Y0;
+    const int nm = ymaj ? g.ny : g.nx, nn = ymaj ? g.nx : g.ny;
+    const float idm = ymaj ? r.idy : r.idx, idn = ymaj ? r.idx : r.idy;
+    const float sec = fabsf(idm);                      // length per unit of major coordinate
+    const float vkn = vn * fabsf(idn), vkz = g.vz * fabsf(r.idz);
+    const float sn = dn * idm, sz = r.dz * idm;        // dn / dm, dz / dm
+    const float s_in = pm + r.tin * dm, s_out = pm + r.tout * dm;
+    const float s_lo = fminf(s_in, s_out), s_hi = fmaxf(s_in, s_out);
+    const float n0 = pn - pm * sn, z0 = r.pz - pm * sz;   // minor and z coordinates at major 0
+    const bool upn = sn >= 0.0f, upz = sz >= 0.0f;
+    const int j0 = clampi((int)floorf((s_lo - M0) * ivm), 0, nm - 1);
+    const int j1 = clampi((int)floorf((s_hi - M0) * ivm), 0, nm - 1);
+    const int c0 = clampi((int)floorf((fmaf(s_lo, sn, n0) - N0) * ivn), 0, nn - 1);
+    const int k0 = clampi((int)floorf((fmaf(s_lo, sz, z0) - g.Z0) * g.ivz), 0, g.nz - 1);
+    const float Nc = fmaf((float)c0, vn, N0), Zc = fmaf((float)k0, g.vz, g.Z0);
+    const float Gn = fabsf(sn) * ivn, Gz = fabsf(sz) * g.ivz;
+    const float Un = (upn ? n0 - Nc : Nc - n0) * ivn, Uz = (upz ? z0 - Zc : Zc - z0) * g.ivz;
+    const int sM = nn + 2, sZ = (nm + 2) * (nn + 2);
+    const int dln = upn ? 1 : -1, dlz = upz ? sZ : -sZ;
+    float fn = upn ? 1.0f : 0.0f, fz = upz ? 1.0f : 0.0f;   // next grid lines, oriented
+    int lin = ((k0 + 1) * (nm + 2) + (j0 + 1)) * sM + c0 + 1;
+    auto strip = [&](float chord, float un, float uz) {
+        const float en = un - fn, ez = uz - fz;
+        const bool cn = en >= 0.0f, cz = ez >= 0.0f;
+        const float ln = cn ? fminf(en * vkn, chord) : 0.0f;    // piece beyond the minor line
+        const float lz = cz ? fminf(ez * vkz, chord) : 0.0f;    // piece beyond the z plane
+        const float hi = fmaxf(ln, lz), lo = fminf(ln, lz);
+        const int lb = ln > lz ? lin + dln : (cz ? lin + dlz : lin);
+        const int lc = lin + (cn ? dln : 0) + (cz ? dlz : 0);
+        visit(lin, chord - hi, lb, hi - lo, lc, lo);
+        fn = cn ? fn + 1.0f : fn;
+        fz = cz ? fz + 1.0f : fz;
+        lin = lc + sM;
+    };
+    if (j1 == j0) {
+        strip((s_hi - s_lo) * sec, fmaf(s_hi, Gn, Un), fmaf(s_hi, Gz, Uz));
+        return;
+    }
+    const float An = fmaf(Gn, M0, Un), Dn = Gn * vm, Az = fmaf(Gz, M0, Uz), Dz = Gz * vm;
+    float fj = (float)(j0 + 1);
+    strip(fmaxf(fmaf(fj, vm, M0) - s_lo, 0.0f) * sec, fmaf(fj, Dn, An), fmaf(fj, Dz, Az));
+    const float full = vm * sec;
+#pragma unroll 4
+    for (int k = j1 - j0 - 1; k > 0; --k) {
+        fj += 1.0f;
+        strip(full, fmaf(fj, Dn, An), fmaf(fj, Dz, Az));
+    }
+    strip(fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec, fmaf(s_hi, Gn, Un), fmaf(s_hi, Gz, Uz));
+}
+
 }  // namespace
+
+// The strip walk's two apron-padded volumes: py (z, y, x) and px (z, x, y),
+// each (nz + 2)(ny + 2)(nx + 2) with a zero border.  One thread per padded
+// voxel; the x-y transposition goes through a 32x32 shared tile per slice.
+// Cells of 2^lam x 2^lam x 2^lamz voxels (mu constant on them; lam = 0:
+// voxels): nx, ny, nz count cells, nxf, nyf are mu's row and slice sizes, and
+// a cell's value is read at its first voxel.
+__global__ void k_pad3(const float* __restrict__ mu, int nxf, int nyf, int lam, int lamz, int nx, int ny, int nz,
+                       float* __restrict__ py, float* __restrict__ px)
+{
+    __shared__ float tile[32][33];
+    const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1, z = (int)blockIdx.z - 1;
+    const size_t slab = (size_t)(nx + 2) * (ny + 2);
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int x = x0 + threadIdx.x, y = y0 + k;
+        float v = 0.0f;
+        if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
+            v = mu[(((size_t)z << lamz) * nyf + ((size_t)y << lam)) * nxf + ((size_t)x << lam)];
+        tile[k][threadIdx.x] = v;
+        if (x <= nx && y <= ny) py[(size_t)(z + 1) * slab + (size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int y = y0 + threadIdx.x, x = x0 + k;
+        if (x <= nx && y <= ny) px[(size_t)(z + 1) * slab + (size_t)(x + 1) * (ny + 2) + (y + 1)] = tile[threadIdx.x][k];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // a2 + a3: projection (leaf or voxel walk), Beer's law, FP64 cost terms
 // ---------------------------------------------------------------------------
+template <bool STRIP>
 __global__ void __launch_bounds__(kFwdTPB)
-k_forward3(Geom3 g, const float* __restrict__ mu, const uint8_t* __restrict__ leaf, int z3,
-           const float* __restrict__ d, const double* __restrict__ dterm, const float* __restrict__ I0,
+k_forward3(Geom3 g, const float* __restrict__ mu, const float* __restrict__ pad, const uint8_t* __restrict__ leaf,
+           int z3, const float* __restrict__ d, const double* __restrict__ dterm, const float* __restrict__ I0,
            float* __restrict__ qhat, float* __restrict__ p_out, double* __restrict__ cost_part,
            unsigned long long* __restrict__ work)
 {
@@ -175,11 +281,39 @@ k_forward3(Geom3 g, const float* __restrict__ mu, const uint8_t* __restrict__ le
     if (b < g.B) {
         Ray3 ray;
         float acc = 0.0f;
+        bool ymaj = false;
         if (make_ray3(g, v, r, b, ray)) {
-            walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
-                acc += c * __ldg(mu + ((size_t)iz * g.ny + iy) * g.nx + ix);
-                ++steps;
-            });
+            if (STRIP && strip3_ok(g, ray, ymaj)) {
+                // padded volumes: loads run one strip ahead of their use; the
+                // sum keeps the walk's order
+                const float* img = ymaj ? pad : pad + (size_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+                float pa = 0.0f, va = 0.0f, pb = 0.0f, vb = 0.0f, pc = 0.0f, vc = 0.0f;
+                traverse_strips3(g, ray, ymaj, [&](int la, float ca, int lb, float cb, int lc, float cc) {
+                    const float wa = __ldg(img + la), wb = __ldg(img + lb), wc = __ldg(img + lc);
+                    acc += pa * va;
+                    acc += pb * vb;
+                    acc += pc * vc;
+                    pa = ca; va = wa;
+                    pb = cb; vb = wb;
+                    pc = cc; vc = wc;
+                    steps += (ca > 0.0f) + (cb > 0.0f) + (cc > 0.0f);
+                });
+                acc += pa * va;
+                acc += pb * vb;
+                acc += pc * vc;
+            } else if (STRIP) {
+                // a ray steeper in z than the strip walk allows: the cell walk on
+                // the same (possibly coarse) grid, reading the padded row-major copy
+                walk3(g, nullptr, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
+                    acc += c * __ldg(pad + (((size_t)iz + 1) * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1);
+                    ++steps;
+                });
+            } else {
+                walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
+                    acc += c * __ldg(mu + ((size_t)iz * g.ny + iy) * g.nx + ix);
+                    ++steps;
+                });
+            }
         }
         const size_t y = ((size_t)v * g.R + r) * g.B + b;
         if (p_out) p_out[y] = acc;
@@ -199,13 +333,39 @@ k_forward3(Geom3 g, const float* __restrict__ mu, const uint8_t* __restrict__ le
 
 int forward3_parts(const Geom3& g) { return (int)nb(g.B, kFwdTPB) * g.V * g.R * (kFwdTPB / 32); }
 
-cudaError_t launch_forward3(const Geom3& g, const float* mu, const uint8_t* leaf, int z3, const float* d,
-                            const double* dterm, const float* I0, float* qhat, float* p_out, double* cost_part,
-                            unsigned long long* work, cudaStream_t st)
+cudaError_t launch_forward3(const Geom3& g, const float* mu, float* pad, const uint8_t* leaf, int lam, int z3,
+                            const float* d, const double* dterm, const float* I0, float* qhat, float* p_out,
+                            double* cost_part, unsigned long long* work, cudaStream_t st)
 {
-    count_launch();
     dim3 grid(nb(g.B, kFwdTPB), g.R, g.V);
-    k_forward3<<<grid, kFwdTPB, 0, st>>>(g, mu, leaf, z3, d, dterm, I0, qhat, p_out, cost_part, work);
+    if (!leaf && pad) {
+        // the strip walk over the padded cells of 2^lam voxels (2^lam x 2^lam x 1
+        // per slice when z3 = 0): same box, larger cells
+        const int lamz = z3 ? lam : 0;
+        if (lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny ||
+            (g.nz >> lamz) << lamz != g.nz)
+            return cudaErrorInvalidValue;
+        Geom3 gc = g;
+        gc.nx = g.nx >> lam;
+        gc.ny = g.ny >> lam;
+        gc.nz = g.nz >> lamz;
+        gc.vx = g.vx * (float)(1 << lam);
+        gc.vy = g.vy * (float)(1 << lam);
+        gc.vz = g.vz * (float)(1 << lamz);
+        gc.ivx = g.ivx / (float)(1 << lam);
+        gc.ivy = g.ivy / (float)(1 << lam);
+        gc.ivz = g.ivz / (float)(1 << lamz);
+        count_launch();
+        k_pad3<<<dim3(nb(gc.nx + 2, 32), nb(gc.ny + 2, 32), gc.nz + 2), dim3(32, 8), 0, st>>>(
+            mu, g.nx, g.ny, lam, lamz, gc.nx, gc.ny, gc.nz, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2) * (gc.nz + 2));
+        count_launch();
+        k_forward3<true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, z3, d, dterm, I0, qhat, p_out, cost_part,
+                                                    work);
+    } else {
+        count_launch();
+        k_forward3<false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, z3, d, dterm, I0, qhat, p_out,
+                                                     cost_part, work);
+    }
     return cudaGetLastError();
 }
 

@@ -48,9 +48,13 @@ struct SegTable3 {
 constexpr int kSlots3 = 15;           // approximation + 7 details x (+, -)
 
 // launchers (cone3d.cu)
-cudaError_t launch_forward3(const Geom3& g, const float* mu, const uint8_t* leaf, int z3, const float* d,
-                            const double* dterm, const float* I0, float* qhat, float* p_out, double* cost_part,
-                            unsigned long long* work, cudaStream_t st);
+// leaf null and pad non-null: the strip walk over apron-padded copies of the
+// cells of 2^lam voxels (2^lam x 2^lam x 1 when z3 = 0; mu must be constant on
+// them) written to pad (2 (nx + 2)(ny + 2)(nz + 2) floats at most); else the
+// leaf / voxel walk.
+cudaError_t launch_forward3(const Geom3& g, const float* mu, float* pad, const uint8_t* leaf, int lam, int z3,
+                            const float* d, const double* dterm, const float* I0, float* qhat, float* p_out,
+                            double* cost_part, unsigned long long* work, cudaStream_t st);
 int forward3_parts(const Geom3& g);
 cudaError_t launch_backproject3(const Geom3& g, const SegTable3& tab, int z3, const float* sino, float* part,
                                 unsigned long long* work, cudaStream_t st);

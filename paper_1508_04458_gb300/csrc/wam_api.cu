@@ -128,10 +128,12 @@ wam_status ensure_t(wam_ctx* c, BufId id, size_t count, P** out)
     return WAM_OK;
 }
 
-// Elements of the pixel walk's two apron-padded image copies.
+// Elements of the strip walk's two apron-padded image (2-D) or volume
+// (cone beam) copies.
 size_t pad_elems(const wam_ctx* c)
 {
-    return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2);
+    const size_t nz2 = c->g.kind == WAM_CONE3D_FLAT_CIRCULAR ? (size_t)(c->g.nz + 2) : 1;
+    return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2) * nz2;
 }
 
 // --- run state ---------------------------------------------------------------
@@ -1195,6 +1197,10 @@ wam_status plan_tree3(wam_ctx* c, const Layout3& lay, const uint8_t* mask, uint8
     long long lv = (long long)lay.gw[L] * lay.gh[L] * (lay.z3 ? lay.gd[L] : 1);
     for (int k = 1; k <= L; ++k) lv += (long long)nd * h[k];
     *leaves = lv * nzr;
+    // finest leaf level: h[k] counts the expanded blocks of level L - k + 1
+    c->last_lmin = L;
+    for (int k = 1; k <= L; ++k)
+        if (h[k] > 0) c->last_lmin = L - k;
     std::vector<ListInfo3> li;
     li.push_back({L, 1, 0, 0, h[0] * nzr, lists, rep ? h[0] : 0, lay.gw[L], lay.gh[L]});
     li.push_back({L, 1, 1, 0, h[1] * nzr, lists + stride, rep ? h[1] : 0, lay.gw[L], lay.gh[L]});
@@ -1250,6 +1256,8 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
     WST(ensure_t(c, B_TMPB, (size_t)N, &tmpb));
     WST(ensure_t(c, B_GIMG, (size_t)N, &gimg));
     WST(ensure_t(c, B_S2D, (size_t)lay.nslice, &s2d));
+    float* pad3 = nullptr;
+    WST(ensure_t(c, B_MUT, pad_elems(c), &pad3));
     const int np = forward3_parts(g);
     WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
     if (L > 0) {
@@ -1287,7 +1295,20 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
         PROF(WAM_K_Z0);
         WST(compute_z03(c, g, lay, leaf, z0, st));
     }
-    auto pick = [&]() -> const uint8_t* { return (L > 0 && 4 * leaves < N) ? leaf : nullptr; };
+    // a2 walks the volume mu, constant on the leaves and so on the cells of the
+    // finest leaf level lam (2^lam cubes for the 3-D tree, 2^lam x 2^lam x 1
+    // per slice): the strip walk over those cells, unless the leaves are fewer
+    // than a ninth of the cells (then the leaf walk meets fewer boundaries)
+    int flam = 0;
+    auto pick = [&]() -> const uint8_t* {
+        flam = L > 0 ? c->last_lmin : 0;
+        const long long cells = N >> ((z3 ? 3 : 2) * flam);
+        if (L > 0 && cells > 9 * leaves) {
+            flam = 0;
+            return leaf;
+        }
+        return nullptr;
+    };
     const uint8_t* fleaf = pick();
     std::vector<int> exp_at(sc->n_expand > 0 ? sc->expand_at : nullptr,
                             sc->n_expand > 0 ? sc->expand_at + sc->n_expand : nullptr);
@@ -1318,7 +1339,7 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
         }
         {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_forward3(g, mu, fleaf, z3, dsino, dterm, I0, q, nullptr, cpart, work_ptr(c, WAM_K_FORWARD),
+            WCK(c, launch_forward3(g, mu, pad3, fleaf, flam, z3, dsino, dterm, I0, q, nullptr, cpart, work_ptr(c, WAM_K_FORWARD),
                                    st));
             WCK(c, launch_sum_final(cpart, np, costs + j, st));
         }
@@ -1723,7 +1744,9 @@ wam_status wam_project(wam_ctx* c, const float* mu, float* p, void* s)
         if (!mu || !p) return fail(c, WAM_ERR_ARG, "null pointer");
         Geom3 g;
         WST(make_geom3(c, &g));
-        WCK(c, launch_forward3(g, mu, nullptr, 1, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
+        float* pad3 = nullptr;
+        WST(ensure_t(c, B_MUT, pad_elems(c), &pad3));
+        WCK(c, launch_forward3(g, mu, pad3, nullptr, 0, 1, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
                                as_stream(s)));
         return WAM_OK;
     }
