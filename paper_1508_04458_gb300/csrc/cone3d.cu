@@ -396,6 +396,196 @@ __device__ __forceinline__ void decode3(const Segment3& S, int item, int& bx, in
     }
 }
 
+// Item kinds of a cone-beam back-projection segment.
+enum { kBp3Block = 0, kBp3Oct = 1, kBp3Quad = 2, kBp3Octet = 3 };
+
+// The view, row and bin loops of one item, specialised by item kind and work
+// counting (no run-time switch in the inner loop; the bin loop is not
+// unrolled and the ray offset from the block centre is linear in the bin).
+template <int MODE, bool WORK>
+__device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int z3, int bx, int by, int bz,
+                                         int chunk, int wv, const float* __restrict__ sino, float (&acc)[kSlots3],
+                                         unsigned& evals)
+{
+    const bool oct = MODE == kBp3Octet;
+    const int l = S.level;
+    const int bs = 1 << l;
+    const int bsz = oct ? 2 : (z3 ? bs : 1);
+    const float hx = 0.5f * bs * g.vx, hy = 0.5f * bs * g.vy, hz = 0.5f * bsz * g.vz;
+    const float cx = g.X0 + (2 * bx + 1) * hx, cy = g.Y0 + (2 * by + 1) * hy;
+    const float cz = g.Z0 + (2 * bz + 1) * hz;
+    const float scale = oct ? 1.0f : (float)basis_scale(z3, l);
+    const int v0 = chunk * S.vpc, v1 = min(g.V, v0 + S.vpc);
+    const float isdd = 1.0f / g.sdd, ipitch = 1.0f / g.pitch, irp = 1.0f / g.rpitch;
+    for (int v = v0 + wv; v < v1; v += kViewLanes) {
+        const float c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
+        const float ac = cx * c + cy * s, wc = -cx * s + cy * c;
+        float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy, oz = (k & 4) ? hz : -hz;
+            const float den = __fdividef(g.sdd, g.sod - (ac + ox * c + oy * s));
+            const float uu = (wc - ox * s + oy * c) * den, vv = (cz + oz) * den;
+            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+            vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+        }
+        // the bins and rows whose rays pass through the shadow; a margin of
+        // 1e-3 bin (row) covers the fast division's rounding
+        const int blo = max(0, (int)ceilf(umin * ipitch + g.ucen - 1e-3f));
+        const int bhi = min(g.B - 1, (int)floorf(umax * ipitch + g.ucen + 1e-3f));
+        const int rlo = max(0, (int)ceilf(vmin * irp + g.rcen - 1e-3f));
+        const int rhi = min(g.R - 1, (int)floorf(vmax * irp + g.rcen + 1e-3f));
+        if (blo > bhi || rlo > rhi) continue;
+        const float kappa = (g.sod - ac) * isdd;
+        const float dw0 = (((float)blo - g.ucen) * g.pitch) * kappa - wc, dstep = g.pitch * kappa;
+        const float4* drow = g.dirt + (size_t)v * g.B;
+        for (int rr = rlo; rr <= rhi; ++rr) {
+            const float vr = ((float)rr - g.rcen) * g.rpitch;
+            const float ri = __ldg(g.rowinv + rr);
+            // z intervals (in tau) of the first / second z half and of the whole
+            // block; for voxel octets the lower / upper half in physical order
+            float z0l, z0h, z1l, z1h, zsl, zsh;
+            if (vr != 0.0f) {
+                const float cc = -(vr * kappa - cz) * ri;      // z centre-plane crossing
+                if (oct) {
+                    const float Hz = 0.5f * hz, uz = fabsf(ri) + ri, wz = fabsf(ri) - ri;
+                    z0l = fmaf(-Hz, uz, cc); z0h = fmaf(Hz, wz, cc);      // lower z half
+                    z1l = fmaf(-Hz, wz, cc); z1h = fmaf(Hz, uz, cc);      // upper z half
+                    zsl = zsh = 0.0f;
+                } else {
+                    const float Az = hz * fabsf(ri);
+                    z0l = cc - Az; z0h = cc; z1l = cc; z1h = cc + Az; zsl = cc - Az; zsh = cc + Az;
+                }
+            } else {
+                // the ray stays in the plane z = 0: it belongs to the half (block)
+                // whose half-open z range [lo, hi) holds 0; 1/v_r = +inf, so the
+                // first half is the lower one
+                const float B = 1e30f;
+                const bool lo = (cz - hz <= 0.0f) && (0.0f < cz), hi = (cz <= 0.0f) && (0.0f < cz + hz);
+                const bool in = (cz - hz <= 0.0f) && (0.0f < cz + hz);
+                z0l = lo ? -B : B; z0h = lo ? B : -B;
+                z1l = hi ? -B : B; z1h = hi ? B : -B;
+                zsl = in ? -B : B; zsh = in ? B : -B;
+            }
+            const float* row = sino + ((size_t)v * g.R + rr) * g.B;
+            const float* dl = g.dlen + (size_t)rr * g.B;
+            float fk = 0.0f;
+#pragma unroll 1
+            for (int bb = blo; bb <= bhi; ++bb, fk += 1.0f) {
+                const float dw = fmaf(fk, dstep, dw0);
+                const float4 T = __ldg(drow + bb);
+                const float a = dw * T.x, b = dw * T.y;
+                const float q = __ldg(row + bb) * __ldg(dl + bb) * scale;
+                if (MODE == kBp3Block) {
+                    const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
+                    const float ch = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh) -
+                                           fmaxf(fmaxf(a - Ax, b - Ay), zsl), 0.0f);
+                    acc[0] += q * ch;
+                    if (WORK) evals += ch > 0.0f;
+                } else if (MODE == kBp3Quad) {
+                    // quadrants of the block within the slice's z slab
+                    const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
+                    const float zl = zsl, zh = zsh;
+                    const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                    const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
+                    float w[4];   // index i + 2 j: i x half, j y half (0 first)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            w[i + 2 * j] = fmaxf(fminf(fminf(xh[i], yh[j]), zh) - fmaxf(fmaxf(xl[i], yl[j]), zl),
+                                                 0.0f);
+                    if (WORK) evals += (w[0] > 0.0f) + (w[1] > 0.0f) + (w[2] > 0.0f) + (w[3] > 0.0f);
+                    // Walsh-Hadamard over (x, y): t = 1 x, 2 y, 3 xy; + on the lower halves
+                    const float s1 = w[0] + w[1], s2 = w[2] + w[3], d1 = w[0] - w[1], d2 = w[2] - w[3];
+                    acc[0] += q * (s1 + s2);
+                    const float W[3] = {flipf(d1 + d2, T.z), flipf(s1 - s2, T.w), flipf(flipf(d1 - d2, T.z), T.w)};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        const float ph = q * W[t];
+                        if (ph > 0.0f) acc[1 + 2 * t] += ph; else acc[2 + 2 * t] += ph;
+                    }
+                } else if (MODE == kBp3Octet) {
+                    // voxel basis: chords of the 8 voxels in physical order (index
+                    // x + 2 y + 4 z, 0 = lower half), select-free: the lower-x voxel
+                    // spans [a - H(|1/Dx| + 1/Dx), a + H(|1/Dx| - 1/Dx)], H half its size
+                    const float Hx = 0.5f * hx, Hy = 0.5f * hy;
+                    const float ux = fabsf(T.z) + T.z, wx = fabsf(T.z) - T.z;
+                    const float uy = fabsf(T.w) + T.w, wy = fabsf(T.w) - T.w;
+                    const float xl[2] = {fmaf(-Hx, ux, a), fmaf(-Hx, wx, a)};
+                    const float xh[2] = {fmaf(Hx, wx, a), fmaf(Hx, ux, a)};
+                    const float yl[2] = {fmaf(-Hy, uy, b), fmaf(-Hy, wy, b)};
+                    const float yh[2] = {fmaf(Hy, wy, b), fmaf(Hy, uy, b)};
+                    const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                const float ch = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                                acc[i + 2 * j + 4 * k] += q * ch;
+                                if (WORK) evals += ch > 0.0f;
+                            }
+                        }
+                } else {
+                    const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
+                    const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                    const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
+                    const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
+                    float w[8];   // index i + 2 j + 4 k
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
+#pragma unroll
+                            for (int k = 0; k < 2; ++k)
+                                w[i + 2 * j + 4 * k] = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
+                        }
+                    if (WORK) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) evals += w[i] > 0.0f;
+                    }
+                    // in-place Walsh-Hadamard transform over (x, y, z)
+#pragma unroll
+                    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (!(i & h)) {
+                                const float u0 = w[i], u1 = w[i + h];
+                                w[i] = u0 + u1;
+                                w[i + h] = u0 - u1;
+                            }
+                    acc[0] += q * w[0];
+#pragma unroll
+                    for (int t = 1; t < 8; ++t) {
+                        float wt = w[t];
+                        if (t & 1) wt = flipf(wt, T.z);
+                        if (t & 2) wt = flipf(wt, T.w);
+                        if (t & 4) wt = flipf(wt, ri);
+                        const float ph = q * wt;
+                        if (ph > 0.0f) acc[2 * t - 1] += ph; else acc[2 * t] += ph;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <bool WORK>
+__device__ __forceinline__ void bp3_dispatch(const Geom3& g, const Segment3& S, int z3, int bx, int by, int bz,
+                                             int chunk, int wv, const float* sino, float (&acc)[kSlots3],
+                                             unsigned& evals)
+{
+    const bool det = S.has_details != 0;
+    if (S.octet) bp3_item<kBp3Octet, WORK>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
+    else if (det && z3) bp3_item<kBp3Oct, WORK>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
+    else if (det) bp3_item<kBp3Quad, WORK>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
+    else bp3_item<kBp3Block, WORK>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
+}
+
 __global__ void __launch_bounds__(kBackTPB)
 k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, float* __restrict__ part,
                unsigned long long* __restrict__ work)
@@ -409,169 +599,16 @@ k_backproject3(Geom3 g, SegTable3 tab, int z3, const float* __restrict__ sino, f
     const int chunk = local / S.tiles, tile = local - chunk * S.tiles;
     const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
     const int item = tile * kItemsPerCta + lane;
-    const bool valid = item < S.n_items;
     const bool oct = S.octet != 0, det = S.has_details != 0;
-    // 0: single chord; 1: 8 octant chords; 2: 4 quadrant chords within the slice
-    const int mode = (oct || (det && z3)) ? 1 : (det ? 2 : 0);   // oct handled inside mode 1
     float acc[kSlots3];
 #pragma unroll
     for (int k = 0; k < kSlots3; ++k) acc[k] = 0.0f;
     unsigned evals = 0;
-    if (valid) {
+    if (item < S.n_items) {
         int bx, by, bz;
         decode3(S, item, bx, by, bz);
-        const int l = S.level;
-        const int bs = 1 << l;
-        const int bsz = oct ? 2 : (z3 ? bs : 1);
-        const float hx = 0.5f * bs * g.vx, hy = 0.5f * bs * g.vy, hz = 0.5f * bsz * g.vz;
-        const float cx = g.X0 + (2 * bx + 1) * hx, cy = g.Y0 + (2 * by + 1) * hy;
-        const float cz = g.Z0 + (2 * bz + 1) * hz;
-        const float scale = oct ? 1.0f : (float)basis_scale(z3, l);
-        const int v0 = chunk * S.vpc, v1 = min(g.V, v0 + S.vpc);
-        const float isdd = 1.0f / g.sdd, ipitch = 1.0f / g.pitch, irp = 1.0f / g.rpitch;
-        for (int v = v0 + wv; v < v1; v += kViewLanes) {
-            const float c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
-            const float ac = cx * c + cy * s, wc = -cx * s + cy * c;
-            float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy, oz = (k & 4) ? hz : -hz;
-                const float den = __fdividef(g.sdd, g.sod - (ac + ox * c + oy * s));
-                const float uu = (wc - ox * s + oy * c) * den, vv = (cz + oz) * den;
-                umin = fminf(umin, uu); umax = fmaxf(umax, uu);
-                vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
-            }
-            // the bins and rows whose rays pass through the shadow; a margin of
-            // 1e-3 bin (row) covers the fast division's rounding
-            const int blo = max(0, (int)ceilf(umin * ipitch + g.ucen - 1e-3f));
-            const int bhi = min(g.B - 1, (int)floorf(umax * ipitch + g.ucen + 1e-3f));
-            const int rlo = max(0, (int)ceilf(vmin * irp + g.rcen - 1e-3f));
-            const int rhi = min(g.R - 1, (int)floorf(vmax * irp + g.rcen + 1e-3f));
-            if (blo > bhi || rlo > rhi) continue;
-            const float kappa = (g.sod - ac) * isdd;
-            const float4* drow = g.dirt + (size_t)v * g.B;
-            for (int rr = rlo; rr <= rhi; ++rr) {
-                const float vr = ((float)rr - g.rcen) * g.rpitch;
-                const float ri = __ldg(g.rowinv + rr);
-                // z intervals (in tau) of the first / second z half and of the whole block
-                float z0l, z0h, z1l, z1h, zsl, zsh;
-                if (vr != 0.0f) {
-                    const float cc = -(vr * kappa - cz) * ri;      // z centre-plane crossing
-                    const float Az = hz * fabsf(ri);
-                    z0l = cc - Az; z0h = cc; z1l = cc; z1h = cc + Az; zsl = cc - Az; zsh = cc + Az;
-                } else {
-                    // the ray stays in the plane z = 0: it belongs to the half (block)
-                    // whose half-open z range [lo, hi) holds 0; 1/v_r = +inf, so the
-                    // first half is the lower one
-                    const float B = 1e30f;
-                    const bool lo = (cz - hz <= 0.0f) && (0.0f < cz), hi = (cz <= 0.0f) && (0.0f < cz + hz);
-                    const bool in = (cz - hz <= 0.0f) && (0.0f < cz + hz);
-                    z0l = lo ? -B : B; z0h = lo ? B : -B;
-                    z1l = hi ? -B : B; z1h = hi ? B : -B;
-                    zsl = in ? -B : B; zsh = in ? B : -B;
-                }
-                const float* row = sino + ((size_t)v * g.R + rr) * g.B;
-                const float* dl = g.dlen + (size_t)rr * g.B;
-                for (int bb = blo; bb <= bhi; ++bb) {
-                    const float ub = ((float)bb - g.ucen) * g.pitch;
-                    const float dw = ub * kappa - wc;
-                    const float4 T = __ldg(drow + bb);
-                    const float a = dw * T.x, b = dw * T.y;
-                    const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
-                    const float q = __ldg(row + bb) * __ldg(dl + bb) * scale;
-                    if (mode == 0) {
-                        const float ch = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh) -
-                                               fmaxf(fmaxf(a - Ax, b - Ay), zsl), 0.0f);
-                        acc[0] += q * ch;
-                        if (work) evals += ch > 0.0f;
-                    } else if (mode == 2) {
-                        // quadrants of the block within the slice's z slab
-                        const float zl = zsl, zh = zsh;
-                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
-                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
-                        float w[4];   // index i + 2 j: i x half, j y half (0 first)
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-#pragma unroll
-                            for (int i = 0; i < 2; ++i)
-                                w[i + 2 * j] = fmaxf(fminf(fminf(xh[i], yh[j]), zh) - fmaxf(fmaxf(xl[i], yl[j]), zl),
-                                                     0.0f);
-                        if (work) evals += (w[0] > 0.0f) + (w[1] > 0.0f) + (w[2] > 0.0f) + (w[3] > 0.0f);
-                        // Walsh-Hadamard over (x, y): t = 1 x, 2 y, 3 xy; + on the lower halves
-                        const float s1 = w[0] + w[1], s2 = w[2] + w[3], d1 = w[0] - w[1], d2 = w[2] - w[3];
-                        acc[0] += q * (s1 + s2);
-                        const float W[3] = {flipf(d1 + d2, T.z), flipf(s1 - s2, T.w),
-                                            flipf(flipf(d1 - d2, T.z), T.w)};
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) {
-                            const float ph = q * W[t];
-                            if (ph > 0.0f) acc[1 + 2 * t] += ph; else acc[2 + 2 * t] += ph;
-                        }
-                    } else if (oct) {
-                        // voxel basis: chords of the 8 voxels in physical order (index
-                        // x + 2 y + 4 z, 0 = lower half); a half crossed first is the
-                        // lower one when the direction along that axis is positive
-                        const bool px = T.z > 0.0f, py = T.w > 0.0f, pz = ri > 0.0f;
-                        const float xl[2] = {px ? a - Ax : a, px ? a : a - Ax};
-                        const float xh[2] = {px ? a : a + Ax, px ? a + Ax : a};
-                        const float yl[2] = {py ? b - Ay : b, py ? b : b - Ay};
-                        const float yh[2] = {py ? b : b + Ay, py ? b + Ay : b};
-                        const float zl[2] = {pz ? z0l : z1l, pz ? z1l : z0l};
-                        const float zh[2] = {pz ? z0h : z1h, pz ? z1h : z0h};
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-#pragma unroll
-                            for (int i = 0; i < 2; ++i) {
-                                const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
-#pragma unroll
-                                for (int k = 0; k < 2; ++k) {
-                                    const float ch = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
-                                    acc[i + 2 * j + 4 * k] += q * ch;
-                                    if (work) evals += ch > 0.0f;
-                                }
-                            }
-                    } else {
-                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
-                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
-                        const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
-                        float w[8];   // index i + 2 j + 4 k
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-#pragma unroll
-                            for (int i = 0; i < 2; ++i) {
-                                const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
-#pragma unroll
-                                for (int k = 0; k < 2; ++k)
-                                    w[i + 2 * j + 4 * k] = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
-                            }
-                        if (work) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) evals += w[i] > 0.0f;
-                        }
-                        // in-place Walsh-Hadamard transform over (x, y, z)
-#pragma unroll
-                        for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                if (!(i & h)) {
-                                    const float u0 = w[i], u1 = w[i + h];
-                                    w[i] = u0 + u1;
-                                    w[i + h] = u0 - u1;
-                                }
-                        acc[0] += q * w[0];
-#pragma unroll
-                        for (int t = 1; t < 8; ++t) {
-                            float wt = w[t];
-                            if (t & 1) wt = flipf(wt, T.z);
-                            if (t & 2) wt = flipf(wt, T.w);
-                            if (t & 4) wt = flipf(wt, ri);
-                            const float ph = q * wt;
-                            if (ph > 0.0f) acc[2 * t - 1] += ph; else acc[2 * t] += ph;
-                        }
-                    }
-                }
-            }
-        }
+        if (work) bp3_dispatch<true>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
+        else bp3_dispatch<false>(g, S, z3, bx, by, bz, chunk, wv, sino, acc, evals);
     }
     add_work3(work, evals);
 #pragma unroll
