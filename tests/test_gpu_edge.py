@@ -1,0 +1,125 @@
+"""Edge cases of the GPU path against the FP64 oracle (FP32 bounds of the
+parity tests: RMS <= 1e-5, max <= 1e-4 of max |ref| for operators, 1e-4
+relative for iterates, costs 1e-4 + 2e-5 of the initial cost; FP64: 1e-10):
+
+* odd image sides, where the back-projector works on single pixels instead
+  of 2x2 quads and the strip walk meets ragged edges;
+* a single view, and a detector much wider than the image (most rays miss);
+* I0 given per ray instead of one scalar;
+* counts that are all zero (every ray behind metal): every update is the
+  clamped step |Z0 Delta| = 30 of the degenerate root, on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import am
+from oracle import system_matrix as smx
+from paper_1508_04458_gb300 import inputs as I
+
+from gpu_helpers import cuda
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1508_04458_gb300 import wam  # noqa: E402
+
+FP32_MAX, FP32_RMS = 1e-4, 1e-5
+
+
+def _close(got, want, what, rel=None):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    scale = max(np.max(np.abs(want)), 1e-300)
+    e = np.abs(got - want)
+    bound = FP32_MAX if rel is None else rel
+    assert e.max() <= bound * scale, "%s: max %.3e" % (what, e.max() / scale)
+    if rel is None:
+        assert np.sqrt(np.mean(e * e)) <= FP32_RMS * scale, "%s: rms" % what
+
+
+def _operators(g):
+    H = smx.system_matrix(g)
+    ctx = wam.Context(g)
+    rng = np.random.default_rng(3)
+    mu = rng.random(g.nx * g.ny)
+    s = rng.random(g.n_views * g.n_bins)
+    for dt, rel, proj, back in ((torch.float32, None, wam.wam_project, wam.wam_backproject),
+                                (torch.float64, 1e-10, wam.wam_project_f64, wam.wam_backproject_f64)):
+        mu_d, s_d = cuda(mu, dt), cuda(s, dt)
+        p_d = torch.empty(g.n_views * g.n_bins, dtype=dt, device="cuda")
+        g_d = torch.empty(g.nx * g.ny, dtype=dt, device="cuda")
+        ctx.check(proj(ctx.h, wam.ptr(mu_d), wam.ptr(p_d), wam.current_stream()))
+        ctx.check(back(ctx.h, wam.ptr(s_d), wam.ptr(g_d), wam.current_stream()))
+        torch.cuda.synchronize()
+        _close(p_d.cpu().numpy(), H @ mu, "H mu %s" % dt, rel)
+        _close(g_d.cpu().numpy(), H.T @ s, "H^T s %s" % dt, rel)
+    return H
+
+
+@pytest.mark.parametrize("nx,ny,kind", [(63, 47, I.FAN2D_FLAT), (65, 33, I.PARALLEL2D), (31, 64, I.FAN2D_FLAT)])
+def test_odd_sides_operators_and_plain_am(nx, ny, kind):
+    p = I.small_problem(nx, ny, 29, 91, kind=kind, seed=nx + ny)
+    H = _operators(p.geom)
+    ref = am.plain_am(H, p.d, p.I0, 10)
+    for precision, bound in ((32, 1e-4), (64, 1e-10)):
+        ctx = wam.Context(p.geom)
+        ctx.set_data(p.d.astype(np.float32), p.I0)
+        mu, hist, _, _ = ctx.reconstruct(0, 10, full_am=True, precision=precision)
+        rel = np.linalg.norm(mu.astype(np.float64) - ref.mu) / np.linalg.norm(ref.mu)
+        assert rel <= bound, (precision, rel)
+        atol = (2e-5 if precision == 32 else 1e-12) * ref.cost[0]
+        np.testing.assert_allclose(hist, ref.cost, rtol=bound, atol=atol)
+
+
+def test_single_view_and_wide_detector():
+    p = I.small_problem(40, 24, 1, 57, seed=71)
+    _operators(p.geom)
+    # a detector five times wider than the image's shadow: most rays miss
+    g = I.small_problem(32, 32, 9, 61, seed=72).geom
+    import dataclasses
+    _operators(dataclasses.replace(g, bin_pitch=5.0 * g.bin_pitch))
+
+
+def test_per_ray_I0():
+    p = I.small_problem(48, 48, 24, 77, seed=73)
+    rng = np.random.default_rng(4)
+    I0 = (p.I0 * rng.uniform(0.5, 1.5, p.d.size)).astype(np.float32)
+    d = rng.poisson(I0.astype(np.float64) * np.exp(-(smx.system_matrix(p.geom) @ np.full(48 * 48, 0.01)))).astype(
+        np.float32)
+    H = smx.system_matrix(p.geom)
+    L, J, ea, tau = 2, 10, (3, 6), (0.1, -1.0)
+    ref = am.wavelet_am(H, d, I0.astype(np.float64), 48, 48, L, J, expand_at=ea, taus=tau)
+    ctx = wam.Context(p.geom)
+    ctx.set_data(d, I0)
+    mu, hist, _, _ = ctx.reconstruct(L, J, ea, tau)
+    rel = np.linalg.norm(mu.astype(np.float64) - ref.mu.ravel()) / np.linalg.norm(ref.mu)
+    assert rel <= 1e-4, rel
+    np.testing.assert_allclose(hist, ref.cost, rtol=1e-4, atol=2e-5 * ref.cost[0])
+
+
+@pytest.mark.parametrize("full", [True, False])
+def test_all_counts_zero(full):
+    p = I.small_problem(32, 32, 20, 61, seed=74)
+    d = np.zeros(p.d.size, np.float32)
+    H = smx.system_matrix(p.geom)
+    J = 4
+    if full:
+        ref = am.plain_am(H, d, p.I0, J)
+    else:
+        ref = am.wavelet_am(H, d, p.I0, 32, 32, 2, J, expand_at=(2,), taus=(-1.0,))
+    ctx = wam.Context(p.geom)
+    ctx.set_data(d, p.I0)
+    if full:
+        mu, hist, _, _ = ctx.reconstruct(0, J, full_am=True)
+    else:
+        mu, hist, _, _ = ctx.reconstruct(2, J, (2,), (-1.0,))
+    assert np.all(np.isfinite(mu)) and np.all(np.isfinite(hist))
+    rel = np.linalg.norm(mu.astype(np.float64) - ref.mu.ravel()) / np.linalg.norm(ref.mu)
+    assert rel <= 1e-4, rel
+    np.testing.assert_allclose(hist, ref.cost, rtol=1e-4, atol=2e-5 * ref.cost[0])
+    assert math.isfinite(float(ref.cost[-1]))
