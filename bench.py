@@ -37,6 +37,12 @@ N_ITERS = 100
 EXPAND_AT = (8, 16, 32, 64)
 TAU = (0.1, 0.03, 0.01, -1.0)       # adaptive threshold: last expansion takes every leaf
 TTT_MAX_ITERS = 300                 # multires iterations allowed to reach the target
+
+
+def workload_config():
+    """The benchmark workload, the same for the GPU arm and the reference arm."""
+    return {"workload": WORKLOAD, "levels": L_LEVELS, "iterations": N_ITERS, "expand_after": list(EXPAND_AT),
+            "tau": list(TAU), "seed": 1509}
 K_MIN = 10                          # FP32 instructions per ray-rectangle intersection (floor)
 
 
@@ -155,7 +161,7 @@ def run_reference(args, problem, world):
     line = {"metric": METRIC, "value": value, "unit": "AM iters/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": "AM iters/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "AM iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -289,6 +295,25 @@ def run_wam(args, problem, world, rank, local_rank):
                 "iters_to_target": int(jh[0]) if jh.size else None, "time_to_target_ms": t_hit}
     ordered = {"multires": os_run(False, 16, TTT_MAX_ITERS), "full_am": os_run(True, 8, N_ITERS)}
 
+    # ---- the projector pair at full resolution (plain AM's kernels): per-launch
+    # time (events), exact nonzero intersections (counters, a separate run),
+    # and the bandwidth a stored sparse H (8 B per nonzero) would need to match
+    ctx.profile(mode=wam.WAM_PROFILE_TIME)
+    step(full=True, levels=0)
+    t_st = ctx.stats()
+    ctx.profile(mode=wam.WAM_PROFILE_WORK)
+    step(full=True, levels=0)
+    w_st = ctx.stats()
+    ctx.profile(False)
+    projector = {}
+    for k in ("forward", "backproject"):
+        nl = max(1, t_st[k]["launches"])
+        ms_l = t_st[k]["ms"] / nl
+        nnz = w_st[k]["work"] / nl
+        projector[k] = {"ms_per_launch": ms_l, "intersections_per_launch": nnz,
+                        "G_intersections_per_s": nnz / (ms_l * 1e6) if ms_l > 0 else None,
+                        "stored_matrix_equiv_GBps": 8.0 * nnz / (ms_l * 1e6) if ms_l > 0 else None}
+
     # ---- e2e through the C-ABI from host buffers
     d_host = np.ascontiguousarray(problem.d.astype(np.float32).ravel())
     torch.cuda.synchronize()
@@ -346,10 +371,7 @@ def run_wam(args, problem, world, rank, local_rank):
             "metric": METRIC, "value": value, "unit": "AM iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": L_LEVELS, "iterations": N_ITERS,
-                       "expand_after": list(EXPAND_AT), "tau": list(TAU),
-                       "l2": "flushed between steps (256 MiB write)",
-                       "cost_precision": "f64", "seed": 1509},
+            "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64"),
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
             "roofline": roofline, "cpu_baseline": cpu,
             "multires": {"final_idiv": float(hist_mr[-1]), "ms_per_iter": dev_ms_max / args.steps / N_ITERS,
@@ -361,6 +383,8 @@ def run_wam(args, problem, world, rank, local_rank):
             "target_idiv": target,
             "time_to_equal_objective": curve,
             "ordered_subsets": ordered,
+            "projector": projector,
+            "clamp_hits_per_reconstruction": int(work1["update"]["work"]),
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "work": v["work"]}
                         for k, v in stats.items()},
             "wall_s_timed": wall,

@@ -379,10 +379,11 @@ enum {
 typedef struct {
     double ms[WAM_NKERNEL];                /* summed device time (CUDA events), ms */
     unsigned long long launches[WAM_NKERNEL];
-    /* algorithmic work: FORWARD = leaf blocks visited by rays (ray-rectangle
-     * intersections), BACKPROJECT = ray-rectangle chords evaluated (4 per
-     * (block, ray) pair for a block with active details, 1 otherwise), Z0 =
-     * leaf blocks visited; other classes 0 */
+    /* counted work: FORWARD = ray-cell intersections with a nonzero chord
+     * (cells of the walked grid, or leaf blocks for the leaf walk),
+     * BACKPROJECT = ray-child (or ray-block) chords with nonzero length,
+     * UPDATE = coefficient steps that sit at the clamp |Z0 Delta| = dmax_clamp
+     * (the degenerate roots of Eq. 1.9); other classes 0 */
     unsigned long long work[WAM_NKERNEL];
 } wam_stats;
 

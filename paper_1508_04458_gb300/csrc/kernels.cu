@@ -539,8 +539,9 @@ __device__ __forceinline__ long long detail_index(const Layout& lay, int level, 
 // Eq. 1.9 = 0 solved for Delta = beta~ - betahat.  With u = exp(-Z0 Delta):
 // bp u^2 - b u + bm = 0, bp >= 0 >= bm, whose positive root is taken in the
 // form free of cancellation for the sign of b.  No ray weight (bp = bm = 0):
-// Delta = 0.  A minimiser at +-infinity is clamped to |Z0 Delta| = clamp.
-__device__ __forceinline__ double am_delta(double b, double bp, double bm, double z0, double clamp)
+// Delta = 0.  A minimiser at +-infinity is clamped to |Z0 Delta| = clamp
+// (hit reports that the step sits at the clamp).
+__device__ __forceinline__ double am_delta(double b, double bp, double bm, double z0, double clamp, bool& hit)
 {
     double t;   // = Z0 * Delta = -ln u
     if (bp > 0.0) {
@@ -553,16 +554,18 @@ __device__ __forceinline__ double am_delta(double b, double bp, double bm, doubl
         t = 0.0;
     }
     t = fmin(fmax(t, -clamp), clamp);
+    hit = fabs(t) >= clamp;
     return t / z0;
 }
 
 // The same root in FP32 (iz0 = 1 / Z0 in FP32).  Where the counts are near
 // zero (the data weight b is below 1e-3 of the model weight bp - bm, e.g.
 // rays behind metal) the log ratio is taken in FP64 instead.
-__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp)
+__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp,
+                                               bool& hit)
 {
     const float bf = (float)b;
-    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta(b, (double)bp, (double)bm, z0, clamp);
+    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta(b, (double)bp, (double)bm, z0, clamp, hit);
     float t;
     if (bp > 0.0f) {
         const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
@@ -574,17 +577,18 @@ __device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, dou
         t = 0.0f;
     }
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
+    hit = fabsf(t) >= (float)clamp;
     return (double)(t * iz0);
 }
 
-__device__ __forceinline__ double am_step(double b, float bp, float bm, double z0, float iz0, double clamp)
+__device__ __forceinline__ double am_step(double b, float bp, float bm, double z0, float iz0, double clamp, bool& hit)
 {
-    return am_delta_f32(b, bp, bm, z0, iz0, clamp);
+    return am_delta_f32(b, bp, bm, z0, iz0, clamp, hit);
 }
 
-__device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, float, double clamp)
+__device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, float, double clamp, bool& hit)
 {
-    return am_delta(b, bp, bm, z0, clamp);
+    return am_delta(b, bp, bm, z0, clamp, hit);
 }
 
 // Sum of one slot of an item over the view chunks c = lane, lane + 8, ... of
@@ -617,7 +621,8 @@ __device__ __forceinline__ T group_sum(T x)
 // (coarse trees, whose items carry many view chunks), else 1.
 template <typename T, int G>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
-                         const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
+                         const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
+                         unsigned long long* __restrict__ hits)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cf = gid / G;
@@ -650,7 +655,9 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     if (z < 0 || lane8 != 0) return;
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
-    beta[z] += am_step(bvec[z], bp, bm, z0, iz0, clamp);
+    bool hit = false;
+    beta[z] += am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    add_work(hits, hit ? 1u : 0u);     // steps at the clamp |Z0 Delta| = clamp
 }
 
 // Scatter the reduced bhat+ / bhat- of each item into coefficient layout.
@@ -1086,14 +1093,16 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
 
 template <typename T>
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b,
-                          const double* z0, double clamp, double* beta, cudaStream_t st)
+                          const double* z0, double clamp, double* beta, unsigned long long* hits, cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
     COUNT_LAUNCH();
     if (tab.total_items < 16384)
-        k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+        k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
+                                                                          hits);
     else
-        k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+        k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
+                                                                         hits);
     return cudaGetLastError();
 }
 
@@ -1224,7 +1233,8 @@ __global__ void k_update_dense(Layout lay, const uint8_t* __restrict__ mask, con
         const int bx = (int)(r % lay.gw[l]), by = (int)(r / lay.gw[l]);
         if (!mask[lay.moff[l] + (long long)by * lay.gw[l] + bx]) return;
     }
-    beta[z] += am_delta(bvec[z], bp[z], bm ? bm[z] : 0.0, *z0p, clamp);
+    bool hit = false;
+    beta[z] += am_delta(bvec[z], bp[z], bm ? bm[z] : 0.0, *z0p, clamp, hit);
 }
 
 cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const double* b, const double* bp,
@@ -1247,7 +1257,7 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \
     template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
-                                          double, double*, cudaStream_t);                                        \
+                                          double, double*, unsigned long long*, cudaStream_t);                   \
     template cudaError_t launch_split_out<T>(const SegTable&, const Layout&, const T*, double*, double*,         \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_synth<T>(const Layout&, const uint8_t*, const double*, T*, cudaStream_t);        \

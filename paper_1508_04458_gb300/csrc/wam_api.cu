@@ -824,7 +824,8 @@ struct Run {
                                           work_ptr(c, WAM_K_BACKPROJECT), st));
             }
             PROF(WAM_K_UPDATE);
-            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, st));
+            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta,
+                                 work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
     }
@@ -874,7 +875,7 @@ struct Run {
         }
         {
             PROF(WAM_K_UPDATE);                                                             // a6
-            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, st));
+            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
     }
