@@ -267,7 +267,7 @@ __global__ void k_pad3(const float* __restrict__ mu, int nxf, int nyf, int lam, 
 // ---------------------------------------------------------------------------
 // a2 + a3: projection (leaf or voxel walk), Beer's law, FP64 cost terms
 // ---------------------------------------------------------------------------
-template <bool STRIP>
+template <bool STRIP, bool WORK>
 __global__ void __launch_bounds__(kFwdTPB)
 k_forward3(Geom3 g, const float* __restrict__ mu, const float* __restrict__ pad, const uint8_t* __restrict__ leaf,
            int z3, const float* __restrict__ d, const double* __restrict__ dterm, const float* __restrict__ I0,
@@ -296,7 +296,7 @@ k_forward3(Geom3 g, const float* __restrict__ mu, const float* __restrict__ pad,
                     pa = ca; va = wa;
                     pb = cb; vb = wb;
                     pc = cc; vc = wc;
-                    steps += (ca > 0.0f) + (cb > 0.0f) + (cc > 0.0f);
+                    if (WORK) steps += (ca > 0.0f) + (cb > 0.0f) + (cc > 0.0f);
                 });
                 acc += pa * va;
                 acc += pb * vb;
@@ -306,12 +306,12 @@ k_forward3(Geom3 g, const float* __restrict__ mu, const float* __restrict__ pad,
                 // the same (possibly coarse) grid, reading the padded row-major copy
                 walk3(g, nullptr, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
                     acc += c * __ldg(pad + (((size_t)iz + 1) * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1);
-                    ++steps;
+                    if (WORK) ++steps;
                 });
             } else {
                 walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int, int, int, int, float c) {
                     acc += c * __ldg(mu + ((size_t)iz * g.ny + iy) * g.nx + ix);
-                    ++steps;
+                    if (WORK) ++steps;
                 });
             }
         }
@@ -323,7 +323,7 @@ k_forward3(Geom3 g, const float* __restrict__ mu, const float* __restrict__ pad,
             term = dterm[y] + (double)d[y] * (double)acc + (double)q;
         }
     }
-    add_work3(work, steps);
+    if (WORK) add_work3(work, steps);
     if (cost_part) {
         term = wsum(term);
         if ((threadIdx.x & 31) == 0)
@@ -359,12 +359,20 @@ cudaError_t launch_forward3(const Geom3& g, const float* mu, float* pad, const u
         k_pad3<<<dim3(nb(gc.nx + 2, 32), nb(gc.ny + 2, 32), gc.nz + 2), dim3(32, 8), 0, st>>>(
             mu, g.nx, g.ny, lam, lamz, gc.nx, gc.ny, gc.nz, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2) * (gc.nz + 2));
         count_launch();
-        k_forward3<true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, z3, d, dterm, I0, qhat, p_out, cost_part,
-                                                    work);
+        if (work)
+            k_forward3<true, true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, z3, d, dterm, I0, qhat, p_out,
+                                                              cost_part, work);
+        else
+            k_forward3<true, false><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, z3, d, dterm, I0, qhat, p_out,
+                                                               cost_part, work);
     } else {
         count_launch();
-        k_forward3<false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, z3, d, dterm, I0, qhat, p_out,
-                                                     cost_part, work);
+        if (work)
+            k_forward3<false, true><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, z3, d, dterm, I0, qhat, p_out,
+                                                               cost_part, work);
+        else
+            k_forward3<false, false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, z3, d, dterm, I0, qhat, p_out,
+                                                                cost_part, work);
     }
     return cudaGetLastError();
 }

@@ -89,7 +89,7 @@ __global__ void k_pad2(const T* __restrict__ mu, int nxf, int lam, int nx, int n
     }
 }
 
-template <typename T, bool PIX>
+template <typename T, bool PIX, bool WORK>
 __global__ void __launch_bounds__(kFwdTPB)
 k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
           const float* __restrict__ d, const double* __restrict__ dterm,
@@ -117,14 +117,14 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
                     acc += pcb * pvb;
                     pca = ca; pva = va;
                     pcb = cb; pvb = vb;
-                    steps += (ca > T(0)) + (cb > T(0));
+                    if (WORK) steps += (ca > T(0)) + (cb > T(0));
                 });
                 acc += pca * pva;
                 acc += pcb * pvb;
             } else {
                 traverse(g, leaf, r, [&](int ix, int iy, int, int, int, T c) {
                     acc += c * __ldg(mu + iy * g.nx + ix);
-                    ++steps;
+                    if (WORK) ++steps;
                 });
             }
         }
@@ -138,7 +138,7 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
             term = dterm[y] + (double)d[y] * (double)acc + (double)q;
         }
     }
-    add_work(work, steps);
+    if (WORK) add_work(work, steps);
     if (cost_part) {
         // one partial per CTA: warp sums, then the warps in a fixed order (a
         // CTA's slot frees only when its last warp ends, so the barrier costs
@@ -990,8 +990,12 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
     if (leaf) {
         COUNT_LAUNCH();
-        k_forward<T, false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, d, dterm, I0, qhat, p_out, resid,
-                                                      cost_part, work);
+        if (work)
+            k_forward<T, false, true><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, d, dterm, I0, qhat, p_out,
+                                                                resid, cost_part, work);
+        else
+            k_forward<T, false, false><<<grid, kFwdTPB, 0, st>>>(g, mu, nullptr, leaf, d, dterm, I0, qhat, p_out,
+                                                                 resid, cost_part, work);
     } else {
         if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
             return cudaErrorInvalidValue;
@@ -1007,8 +1011,12 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
         k_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
             mu, g.nx, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
         COUNT_LAUNCH();
-        k_forward<T, true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
-                                                     cost_part, work);
+        if (work)
+            k_forward<T, true, true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
+                                                               cost_part, work);
+        else
+            k_forward<T, true, false><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out,
+                                                                resid, cost_part, work);
     }
     return cudaGetLastError();
 }
@@ -1031,8 +1039,13 @@ cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8
     k_synth_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
         lay, leaf, beta, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
     COUNT_LAUNCH();
-    k_forward<T, true><<<dim3(nblk(g.B, kFwdTPB), g.V), kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0,
-                                                                          qhat, p_out, resid, cost_part, work);
+    const dim3 grid(nblk(g.B, kFwdTPB), g.V);
+    if (work)
+        k_forward<T, true, true><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out,
+                                                           resid, cost_part, work);
+    else
+        k_forward<T, true, false><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out,
+                                                            resid, cost_part, work);
     return cudaGetLastError();
 }
 
