@@ -196,9 +196,9 @@ def run_wam(args, problem, world, rank, local_rank):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K complete reconstructions, L2 flushed between them;
-    # CUDA events bracket every kernel (no work counters in the kernels)
-    ctx.profile(mode=wam.WAM_PROFILE_TIME)
+    # ---- timed region: K complete reconstructions, L2 flushed between them,
+    # no instrumentation inside the library (events only around each step)
+    ctx.profile(False)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
@@ -217,6 +217,14 @@ def run_wam(args, problem, world, rank, local_rank):
     if world > 1:
         dist.barrier()
     launches = wam.kernel_launches() - launches0
+    # the kernel-timing pass: K more steps of the same workload (L2 flushed
+    # between them) with CUDA events on the library's stream around every
+    # kernel class, for the per-kernel times and the roofline
+    ctx.profile(mode=wam.WAM_PROFILE_TIME)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
     stats = ctx.stats()
     # the same step once more with the kernels' work counters (outside the
     # timed region: counting adds instructions); the work is deterministic

@@ -692,36 +692,25 @@ __device__ __forceinline__ float sum_slot3(const Segment3& S, const float* __res
     return s;
 }
 
-// the AM root in FP32 with the FP64 fallback near zero counts (as in 2-D)
-__device__ __forceinline__ double am_delta64(double b, double bp, double bm, double z0, double clamp)
-{
-    double t;
-    if (bp > 0.0) {
-        const double disc = sqrt(b * b - 4.0 * bp * bm);
-        const double u = (b >= 0.0) ? (b + disc) / (2.0 * bp) : 2.0 * bm / (b - disc);
-        t = (u > 0.0) ? -log(u) : clamp;
-    } else if (bm < 0.0) {
-        t = (b < 0.0) ? -log(bm / b) : -clamp;
-    } else {
-        t = 0.0;
-    }
-    t = fmin(fmax(t, -clamp), clamp);
-    return t / z0;
-}
-
+// the AM root of Eq. 1.9 in FP32 on b, bp, bm divided by the largest of
+// |b|, bp, -bm (the root is a ratio; nothing overflows, no FP64 arithmetic)
 __device__ __forceinline__ double am_delta32(double b, float bp, float bm, double z0, float iz0, double clamp)
 {
-    const float bf = (float)b;
-    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta64(b, bp, bm, z0, clamp);
-    float t;
-    if (bp > 0.0f) {
-        const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
-        const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
-        t = (u > 0.0f) ? -logf(u) : (float)clamp;
-    } else if (bm < 0.0f) {
-        t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
-    } else {
-        t = 0.0f;
+    float bf = (float)b;
+    const float sc = fmaxf(fmaxf(bp, -bm), fabsf(bf));
+    float t = 0.0f;
+    if (sc > 0.0f) {
+        const float r = 1.0f / fmaxf(sc, 1e-30f);
+        bf *= r;
+        bp *= r;
+        bm *= r;
+        if (bp > 0.0f) {
+            const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
+            const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
+            t = (u > 0.0f) ? -logf(u) : (float)clamp;
+        } else if (bm < 0.0f) {
+            t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
+        }
     }
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
     return (double)(t * iz0);

@@ -89,16 +89,48 @@ __global__ void k_pad2(const T* __restrict__ mu, int nxf, int lam, int nx, int n
     }
 }
 
+// Per-ray I-divergence term dterm + d p + q of the cost.  FP64: as written.
+// FP32: the three addends are of order d |log(d/I0)| while their sum is of
+// order one, so they are added in float-float (the exact product d p by an
+// FMA, exact sums by Knuth's two-sum) and only the sum is rounded to float;
+// the warp sums of these terms are then FP32 and the CTA's in FP64.
+template <typename T> struct CostAccT { using type = double; };
+template <> struct CostAccT<float> { using type = float; };
+template <typename T> using CostAcc = typename CostAccT<T>::type;
+
+__device__ __forceinline__ double cost_term(double dt, float d, double p, double q)
+{
+    return dt + (double)d * p + q;
+}
+
+// s + e = a + b exactly (round-to-nearest, no contraction)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float cost_term(float2 dt, float d, float p, float q)
+{
+    const float ph = __fmul_rn(d, p);
+    const float pl = __fmaf_rn(d, p, -ph);      // d p = ph + pl exactly
+    float s1, e1, s2, e2;
+    two_sum(dt.x, ph, s1, e1);
+    two_sum(s1, q, s2, e2);
+    return __fadd_rn(s2, __fadd_rn(__fadd_rn(dt.y, pl), __fadd_rn(e1, e2)));
+}
+
 template <typename T, bool PIX, bool WORK>
 __global__ void __launch_bounds__(kFwdTPB)
 k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
-          const float* __restrict__ d, const double* __restrict__ dterm,
+          const float* __restrict__ d, const typename CostTerm<T>::type* __restrict__ dterm,
           const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
           T* __restrict__ resid, double* __restrict__ cost_part, unsigned long long* __restrict__ work)
 {
     const int v = blockIdx.y;
     const int b = blockIdx.x * kFwdTPB + threadIdx.x;
-    double term = 0.0;
+    CostAcc<T> term = 0;
     unsigned steps = 0;
     if (b < g.B) {
         Ray<T> r;
@@ -135,7 +167,7 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
             if (qhat) qhat[y] = q;
             if (resid) resid[y] = T(d[y]) - q;   // dI/dp = d - q
             // d log(d/q) - d + q = [d (log d - log I0) - d] + d p + q
-            term = dterm[y] + (double)d[y] * (double)acc + (double)q;
+            term = cost_term(dterm[y], d[y], acc, q);
         }
     }
     if (WORK) add_work(work, steps);
@@ -143,7 +175,7 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
         // one partial per CTA: warp sums, then the warps in a fixed order (a
         // CTA's slot frees only when its last warp ends, so the barrier costs
         // no occupancy)
-        __shared__ double wsum[kFwdTPB / 32];
+        __shared__ CostAcc<T> wsum[kFwdTPB / 32];
         term = warp_reduce(term, OpSum());
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = term;
         __syncthreads();
@@ -379,22 +411,25 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 acc[3] += q * chh;
                 if (WORK) evals += (cll > T(0)) + (chl > T(0)) + (clh > T(0)) + (chh > T(0));
             } else if (MODE == kBpSplit) {
-                // Haar split from the crossing-ordered child chords (first / second
-                // half along the travel direction), the halves' order fixed by signs
-                T cFF, cFS, cSF, cSS;
-                child_chords_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w), cFF, cFS, cSF, cSS);
+                // Haar split: the block chord and the three first-minus-second
+                // half differences along the travel direction (haar_split), the
+                // halves' physical order fixed by the direction's signs
+                T A, dx, dy, dg;
+                haar_split(a, b, hx * fabs(dd.z), hy * fabs(dd.w), A, dx, dy, dg);
                 const T qs = q * scale;
-                const T xF = cFF + cFS, xS = cSF + cSS;      // first / second x half
-                const T yF = cFF + cSF, yS = cFS + cSS;
-                acc[0] += qs * (xF + xS);
+                acc[0] += qs * A;
                 // lower half minus upper half, by the travel direction's signs
-                const T ph = qs * flip(yF - yS, dd.w);
-                const T pv = qs * flip(xF - xS, dd.z);
-                const T pd = qs * flip2((cFF + cSS) - (cFS + cSF), dd.z, dd.w);
+                const T ph = qs * flip(dy, dd.w);
+                const T pv = qs * flip(dx, dd.z);
+                const T pd = qs * flip2(dg, dd.z, dd.w);
                 if (ph > T(0)) acc[1] += ph; else acc[2] += ph;
                 if (pv > T(0)) acc[3] += pv; else acc[4] += pv;
                 if (pd > T(0)) acc[5] += pd; else acc[6] += pd;
-                if (WORK) evals += (cFF > T(0)) + (cFS > T(0)) + (cSF > T(0)) + (cSS > T(0));
+                if (WORK) {
+                    T cFF, cFS, cSF, cSS;
+                    child_chords_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w), cFF, cFS, cSF, cSS);
+                    evals += (cFF > T(0)) + (cFS > T(0)) + (cSF > T(0)) + (cSS > T(0));
+                }
             } else {
                 const T ch = block_chord_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w));
                 acc[0] += q * scale * ch;
@@ -558,23 +593,30 @@ __device__ __forceinline__ double am_delta(double b, double bp, double bm, doubl
     return t / z0;
 }
 
-// The same root in FP32 (iz0 = 1 / Z0 in FP32).  Where the counts are near
-// zero (the data weight b is below 1e-3 of the model weight bp - bm, e.g.
-// rays behind metal) the log ratio is taken in FP64 instead.
+// The same root in FP32 (iz0 = 1 / Z0 in FP32).  The root u is a ratio, so
+// b, bp and bm are first divided by the largest of |b|, bp, -bm (at least
+// 1e-30, for q-hat underflowing behind metal): no square or product can
+// overflow, and no case needs FP64 arithmetic (GB300's FP64 rate is a small
+// fraction of its FP32 rate).  A square that underflows leaves u at most a
+// factor 2 off where -ln u > 43, i.e. beyond any clamp.
 __device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp,
                                                bool& hit)
 {
-    const float bf = (float)b;
-    if (!(fabsf(bf) >= 1e-3f * (bp - bm))) return am_delta(b, (double)bp, (double)bm, z0, clamp, hit);
-    float t;
-    if (bp > 0.0f) {
-        const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
-        const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
-        t = (u > 0.0f) ? -logf(u) : (float)clamp;
-    } else if (bm < 0.0f) {
-        t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
-    } else {
-        t = 0.0f;
+    float bf = (float)b;
+    const float sc = fmaxf(fmaxf(bp, -bm), fabsf(bf));
+    float t = 0.0f;
+    if (sc > 0.0f) {
+        const float r = 1.0f / fmaxf(sc, 1e-30f);
+        bf *= r;
+        bp *= r;
+        bm *= r;
+        if (bp > 0.0f) {
+            const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
+            const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
+            t = (u > 0.0f) ? -logf(u) : (float)clamp;
+        } else if (bm < 0.0f) {
+            t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
+        }
     }
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
     hit = fabsf(t) >= (float)clamp;
@@ -599,6 +641,7 @@ __device__ __forceinline__ T sum_slot_lane(const Segment& S, const T* __restrict
     T s = T(0);
     const T* p = part + S.part_off + (size_t)slot * S.n_items + item;
     const size_t stride = (size_t)S.n_slots * S.n_items;
+#pragma unroll 4
     for (int c = lane; c < S.n_chunks; c += G) s += p[c * stride];
     return s;
 }
@@ -622,7 +665,7 @@ __device__ __forceinline__ T group_sum(T x)
 template <typename T, int G>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
-                         unsigned long long* __restrict__ hits)
+                         float* __restrict__ beta32, unsigned long long* __restrict__ hits)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cf = gid / G;
@@ -656,7 +699,9 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
     bool hit = false;
-    beta[z] += am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    const double nb = beta[z] + am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    beta[z] = nb;
+    if (beta32) beta32[z] = (float)nb;
     add_work(hits, hit ? 1u : 0u);     // steps at the clamp |Z0 Delta| = clamp
 }
 
@@ -735,6 +780,25 @@ __device__ __forceinline__ double synth_at(const Layout& lay, const double* __re
     return v;
 }
 
+// The same sum in FP32 from the float copy of the coefficients (the FP32
+// forward's input; 2^-l applied exactly).
+__device__ __forceinline__ float pow2mf(int l) { return __int_as_float((127 - l) << 23); }
+
+__device__ __forceinline__ float synth_at(const Layout& lay, const float* __restrict__ beta, int ix, int iy, int lam)
+{
+    const int L = lay.L;
+    float v = beta[(long long)(iy >> L) * lay.gw[L] + (ix >> L)] * pow2mf(L);
+    for (int l = L; l > lam; --l) {
+        const int bx = ix >> l, by = iy >> l;
+        const float sh = ((iy >> (l - 1)) & 1) ? -1.0f : 1.0f;
+        const float sv = ((ix >> (l - 1)) & 1) ? -1.0f : 1.0f;
+        const long long n = (long long)lay.gw[l] * lay.gh[l];
+        const long long z = lay.coff[l] + (long long)by * lay.gw[l] + bx;
+        v += (sh * beta[z] + sv * beta[z + n] + sh * sv * beta[z + 2 * n]) * pow2mf(l);
+    }
+    return v;
+}
+
 template <typename T>
 __global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
                         T* __restrict__ mu)
@@ -753,8 +817,9 @@ __global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const doub
 // (cells of 2^lam pixels, row-major and transposed) filled straight from the
 // coefficients; a cell's value is mu at its first pixel.
 template <typename T>
-__global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf, const double* __restrict__ beta,
-                             int lam, int nx, int ny, T* __restrict__ py, T* __restrict__ px)
+__global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf,
+                             const typename SynthCoef<T>::type* __restrict__ beta, int lam, int nx, int ny,
+                             T* __restrict__ py, T* __restrict__ px)
 {
     __shared__ T tile[32][33];
     const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1;
@@ -928,12 +993,15 @@ __global__ void k_haar_synthesis(Layout lay, int l, const double* __restrict__ a
 
 // per-ray constant of the cost: d (log d - log I0) - d, 0 log 0 = 0
 __global__ void k_dterm(const float* __restrict__ d, const float* __restrict__ I0, long long n,
-                        double* __restrict__ out)
+                        double* __restrict__ out, float2* __restrict__ out2)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dd = d[i];
-    out[i] = dd > 0.0 ? dd * (log(dd) - log((double)I0[i])) - dd : 0.0;
+    const double t = dd > 0.0 ? dd * (log(dd) - log((double)I0[i])) - dd : 0.0;
+    out[i] = t;
+    const float hi = (float)t;
+    out2[i] = make_float2(hi, (float)(t - (double)hi));
 }
 
 __global__ void k_fill_f32(float* __restrict__ x, long long n, float v)
@@ -981,11 +1049,12 @@ cudaError_t launch_permute_rows(const E* src, E* dst, const int* perm, int V, in
 }
 template cudaError_t launch_permute_rows<float>(const float*, float*, const int*, int, int, cudaStream_t);
 template cudaError_t launch_permute_rows<double>(const double*, double*, const int*, int, int, cudaStream_t);
+template cudaError_t launch_permute_rows<float2>(const float2*, float2*, const int*, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d,
-                           const double* dterm, const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
-                           unsigned long long* work, cudaStream_t st)
+                           const typename CostTerm<T>::type* dterm, const float* I0, T* qhat, T* p_out, T* resid,
+                           double* cost_part, unsigned long long* work, cudaStream_t st)
 {
     dim3 grid(nblk(g.B, kFwdTPB), g.V);
     if (leaf) {
@@ -1022,9 +1091,10 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
 }
 
 template <typename T>
-cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, const double* beta,
-                                int lam, T* pad, const float* d, const double* dterm, const float* I0, T* qhat,
-                                T* p_out, T* resid, double* cost_part, unsigned long long* work, cudaStream_t st)
+cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf,
+                                const typename SynthCoef<T>::type* beta, int lam, T* pad, const float* d, const typename CostTerm<T>::type* dterm,
+                                const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
+                                unsigned long long* work, cudaStream_t st)
 {
     if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
         return cudaErrorInvalidValue;
@@ -1106,16 +1176,17 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
 
 template <typename T>
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b,
-                          const double* z0, double clamp, double* beta, unsigned long long* hits, cudaStream_t st)
+                          const double* z0, double clamp, double* beta, float* beta32, unsigned long long* hits,
+                          cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
     COUNT_LAUNCH();
     if (tab.total_items < 16384)
         k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                          hits);
+                                                                          beta32, hits);
     else
         k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                         hits);
+                                                                         beta32, hits);
     return cudaGetLastError();
 }
 
@@ -1205,10 +1276,10 @@ cudaError_t launch_haar(const Layout& lay, const double* in, double* out, int in
     return cudaGetLastError();
 }
 
-cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, cudaStream_t st)
+cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, float2* out2, cudaStream_t st)
 {
     COUNT_LAUNCH();
-    k_dterm<<<nblk(n, 256), 256, 0, st>>>(d, I0, n, out);
+    k_dterm<<<nblk(n, 256), 256, 0, st>>>(d, I0, n, out, out2);
     return cudaGetLastError();
 }
 
@@ -1261,16 +1332,18 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
 
 // explicit instantiations
 #define WAM_INST(T)                                                                                              \
-    template cudaError_t launch_forward_tree<T>(const Geom<T>&, const Layout&, const uint8_t*, const double*, int, T*, \
-                                                const float*, const double*, const float*, T*, T*, T*, double*,       \
-                                                unsigned long long*, cudaStream_t);                                   \
-    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, T*, const uint8_t*, int, const float*, const double*, \
-                                           const float*, T*, T*, T*, double*, unsigned long long*, cudaStream_t); \
+    template cudaError_t launch_forward_tree<T>(const Geom<T>&, const Layout&, const uint8_t*,                      \
+                                                const typename SynthCoef<T>::type*, int, T*,                          \
+                                                const float*, const typename CostTerm<T>::type*, const float*, T*,    \
+                                                T*, T*, double*, unsigned long long*, cudaStream_t);                  \
+    template cudaError_t launch_forward<T>(const Geom<T>&, const T*, T*, const uint8_t*, int, const float*,          \
+                                           const typename CostTerm<T>::type*, const float*, T*, T*, T*, double*,      \
+                                           unsigned long long*, cudaStream_t);                                        \
     template cudaError_t launch_z0<T>(const Geom<T>&, const Layout&, const uint8_t*, double*, cudaStream_t);     \
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \
     template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
-                                          double, double*, unsigned long long*, cudaStream_t);                   \
+                                          double, double*, float*, unsigned long long*, cudaStream_t);           \
     template cudaError_t launch_split_out<T>(const SegTable&, const Layout&, const T*, double*, double*,         \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_synth<T>(const Layout&, const uint8_t*, const double*, T*, cudaStream_t);        \

@@ -28,6 +28,7 @@ enum BufId {
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
     B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER, B_MUT,
     B_PERM, B_CSP32, B_CSP64, B_DIRP32, B_DIRP64, B_DP, B_I0P, B_DTP, B_BSUB, B_Z0SUB, B_SINOP,
+    B_DTERM2, B_BETA32,
     B_NBUF
 };
 
@@ -126,6 +127,13 @@ wam_status ensure_t(wam_ctx* c, BufId id, size_t count, P** out)
     WST(ensure(c, id, count * sizeof(P), &p));
     *out = static_cast<P*>(p);
     return WAM_OK;
+}
+
+// the per-ray cost constant in the form the forward of type T reads
+template <typename T>
+const typename CostTerm<T>::type* dterm_buf(const wam_ctx* c)
+{
+    return static_cast<const typename CostTerm<T>::type*>(c->buf[sizeof(T) == 4 ? B_DTERM2 : B_DTERM].p);
 }
 
 // Elements of the strip walk's two apron-padded image (2-D) or volume
@@ -560,10 +568,11 @@ struct Run {
     T *q = nullptr, *mu = nullptr, *mut = nullptr, *sino = nullptr, *part = nullptr;
     double *beta = nullptr, *bvec = nullptr, *costs = nullptr, *z0 = nullptr, *scratch = nullptr;
     double *tmpa = nullptr, *tmpb = nullptr, *gimg = nullptr, *cpart = nullptr;
+    float* beta32 = nullptr;    // FP32 runs: the float copy of beta the forward synthesises from
     uint8_t *mask = nullptr, *mask2 = nullptr, *leaf = nullptr;
     int* counter = nullptr;
     const float *dsino = nullptr, *I0 = nullptr;
-    const double* dterm = nullptr;
+    const typename CostTerm<T>::type* dterm = nullptr;
     const void* dirt = nullptr;
     SegTable tab{};
     const uint8_t* fwd_leaf = nullptr;
@@ -578,7 +587,7 @@ struct Run {
     std::vector<Geom<T>> gsub;  // each subset as a scan of its own
     Geom<T> gperm{};            // the whole scan in subset-major order
     const float *dP = nullptr, *I0P = nullptr;
-    const double* dtP = nullptr;
+    const typename CostTerm<T>::type* dtP = nullptr;
     const void* dirP = nullptr;
     double *bsub = nullptr, *z0sub = nullptr;   // per subset: b (Eq. 1.6 on its rays), Z0
 
@@ -614,6 +623,7 @@ struct Run {
         WST(ensure_t(c, B_MU, (size_t)N, &mu));
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
         WST(ensure_t(c, B_BETA, (size_t)N, &beta));
+        if (sizeof(T) == 4) WST(ensure_t(c, B_BETA32, (size_t)N, &beta32));
         WST(ensure_t(c, B_BVEC, (size_t)N, &bvec));
         WST(ensure_t(c, B_COSTS, (size_t)J + 1, &costs));
         WST(ensure_t(c, B_Z0, 1, &z0));
@@ -632,7 +642,7 @@ struct Run {
         }
         dsino = static_cast<const float*>(c->buf[B_D].p);
         I0 = static_cast<const float*>(c->buf[B_I0].p);
-        dterm = static_cast<const double*>(c->buf[B_DTERM].p);
+        dterm = dterm_buf<T>(c);
         WST(dir_table<T>(c, &dirt));
 
         // a0, Eq. 1.6: b = Phi^T d = Omega^T (H^T d) for every coefficient
@@ -657,6 +667,7 @@ struct Run {
         }
         // beta^(0) = 0; the tree holds the approximations only
         WCK(c, cudaMemsetAsync(beta, 0, N * sizeof(double), st));
+        if (beta32) WCK(c, cudaMemsetAsync(beta32, 0, N * sizeof(float), st));
         WCK(c, cudaMemsetAsync(counter, 0, sizeof(int), st));
         if (L > 0) {
             WCK(c, cudaMemsetAsync(mask, 0, lay.mask_bytes, st));
@@ -708,13 +719,13 @@ struct Run {
         WST(ensure_t(c, sizeof(T) == 4 ? B_CSP32 : B_CSP64, csh.size(), &csp));
         WCK(c, cudaMemcpyAsync(csp, csh.data(), csh.size() * sizeof(T), cudaMemcpyHostToDevice, st));
         float *dp = nullptr, *ip = nullptr;
-        double* dtp = nullptr;
+        typename CostTerm<T>::type* dtp = nullptr;
         WST(ensure_t(c, B_DP, (size_t)M, &dp));
         WST(ensure_t(c, B_I0P, (size_t)M, &ip));
         WST(ensure_t(c, B_DTP, (size_t)M, &dtp));
         WCK(c, launch_permute_rows<float>(dsino, dp, dperm, V, B, st));
         WCK(c, launch_permute_rows<float>(I0, ip, dperm, V, B, st));
-        WCK(c, launch_permute_rows<double>(dterm, dtp, dperm, V, B, st));
+        WCK(c, launch_permute_rows<typename CostTerm<T>::type>(dterm, dtp, dperm, V, B, st));
         dP = dp;
         I0P = ip;
         dtP = dtp;
@@ -783,9 +794,17 @@ struct Run {
         return WAM_OK;
     }
 
+    // the coefficients the strip-walk forward synthesises its cells from
+    const typename SynthCoef<T>::type* synth_src() const
+    {
+        return reinterpret_cast<const typename SynthCoef<T>::type*>(sizeof(T) == 4 ? (const void*)beta32
+                                                                                   : (const void*)beta);
+    }
+
     // a1 + a2 + a3 on a scan (the whole one or a subset): qhat into qq and,
     // with cp, the cost partials
-    wam_status fwd(const Geom<T>& gg, const float* dd, const double* dt, const float* ii, T* qq, double* cp,
+    wam_status fwd(const Geom<T>& gg, const float* dd, const typename CostTerm<T>::type* dt, const float* ii, T* qq,
+                   double* cp,
                    cudaStream_t st)
     {
         if (fwd_leaf) {
@@ -798,7 +817,7 @@ struct Run {
                                   work_ptr(c, WAM_K_FORWARD), st));
         } else {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_forward_tree(gg, lay, L > 0 ? leaf : nullptr, beta, fwd_lam, mut, dd, dt, ii, qq,
+            WCK(c, launch_forward_tree(gg, lay, L > 0 ? leaf : nullptr, synth_src(), fwd_lam, mut, dd, dt, ii, qq,
                                        (T*)nullptr, (T*)nullptr, cp, work_ptr(c, WAM_K_FORWARD), st));
         }
         return WAM_OK;
@@ -824,7 +843,7 @@ struct Run {
                                           work_ptr(c, WAM_K_BACKPROJECT), st));
             }
             PROF(WAM_K_UPDATE);
-            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta,
+            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, beta32,
                                  work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
@@ -839,6 +858,7 @@ struct Run {
             r.mask.size() != (L > 0 ? (size_t)lay.mask_bytes : 0))
             return fail(c, WAM_ERR_STATE, "resume: the checkpoint's sizes do not fit this schedule");
         WCK(c, cudaMemcpyAsync(beta, r.beta.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (beta32) WCK(c, (launch_convert<double, float>(beta, beta32, N, st)));
         WCK(c, cudaMemcpyAsync(costs, r.hist.data(), r.hist.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         if (L > 0) {
             WCK(c, cudaMemcpyAsync(mask, r.mask.data(), lay.mask_bytes, cudaMemcpyHostToDevice, st));
@@ -864,7 +884,7 @@ struct Run {
                 WCK(c, launch_forward(g, mu, mut, fwd_leaf, 0, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
                                       work_ptr(c, WAM_K_FORWARD), st));
             else
-                WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, beta, fwd_lam, mut, dsino, dterm, I0, q,
+                WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, synth_src(), fwd_lam, mut, dsino, dterm, I0, q,
                                            (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, npc, costs + j, st));
@@ -875,7 +895,7 @@ struct Run {
         }
         {
             PROF(WAM_K_UPDATE);                                                             // a6
-            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, work_ptr(c, WAM_K_UPDATE), st));
+            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, beta32, work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
     }
@@ -901,6 +921,8 @@ struct Run {
         return replan(st);
     }
 
+    // the image out (FP64 synthesis) and the last cost, on the forward path
+    // of the iterations (so that the history is that of one run, cut or not)
     wam_status final_cost(cudaStream_t st, bool use_counter)
     {
         {
@@ -909,8 +931,12 @@ struct Run {
         }
         {
             PROF(WAM_K_FORWARD);
-            WCK(c, launch_forward(g, mu, mut, fwd_leaf, fwd_lam, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
-                                  work_ptr(c, WAM_K_FORWARD), st));
+            if (fwd_leaf)
+                WCK(c, launch_forward(g, mu, mut, fwd_leaf, 0, dsino, dterm, I0, q, (T*)nullptr, (T*)nullptr, cpart,
+                                      work_ptr(c, WAM_K_FORWARD), st));
+            else
+                WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, synth_src(), fwd_lam, mut, dsino, dterm,
+                                           I0, q, (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
             if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
             else WCK(c, launch_sum_final(cpart, npc, costs + J, st));
         }
@@ -1029,8 +1055,8 @@ wam_status forward_impl(wam_ctx* c, int levels, const unsigned char* masks, cons
     T* mut = nullptr;
     WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
     WCK(c, launch_forward<T>(g, mu, mut, leaf, 0, static_cast<const float*>(c->buf[B_D].p),
-                             static_cast<const double*>(c->buf[B_DTERM].p),
-                             static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr, cpart, nullptr,
+                             dterm_buf<T>(c), static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, nullptr,
+                             cpart, nullptr,
                              st));
     WCK(c, launch_sum_final(cpart, forward_cost_parts(g.V, g.B), cost, st));
     return WAM_OK;
@@ -1540,6 +1566,8 @@ wam_status wam_set_data(wam_ctx* c, const float* d, const float* I0, int I0_is_s
         WST(ensure_t(c, B_D, (size_t)M, &dd));
         WST(ensure_t(c, B_I0, (size_t)M, &ii));
         WST(ensure_t(c, B_DTERM, (size_t)M, &dt));
+        float2* dt2 = nullptr;
+        WST(ensure_t(c, B_DTERM2, (size_t)M, &dt2));
         // validate on the host (device data are copied back once)
         std::vector<float> hd((size_t)M), hi(I0_is_scalar ? 1 : (size_t)M);
         const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
@@ -1556,7 +1584,7 @@ wam_status wam_set_data(wam_ctx* c, const float* d, const float* I0, int I0_is_s
         } else {
             WCK(c, cudaMemcpyAsync(ii, hi.data(), M * sizeof(float), cudaMemcpyHostToDevice, st));
         }
-        WCK(c, launch_dterm(dd, ii, M, dt, st));
+        WCK(c, launch_dterm(dd, ii, M, dt, dt2, st));
         WCK(c, cudaStreamSynchronize(st));
         c->has_data = true;
         c->last = RunRecord{};
@@ -2209,8 +2237,8 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
         float* mut = nullptr;
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
         WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, static_cast<const float*>(c->buf[B_D].p),
-                                     static_cast<const double*>(c->buf[B_DTERM].p),
-                                     static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr, res, cpart, nullptr,
+                                     dterm_buf<float>(c), static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr,
+                                     res, cpart, nullptr,
                                      st));
         double* coef = nullptr;
         WST(sino_to_coef(c, lay, res, &coef, st));

@@ -357,6 +357,26 @@ __device__ __forceinline__ void child_chords_phys(T a, T b, T Hx, T Hy, T ix, T 
     chh = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
 }
 
+// The Haar split of a ray through a block without its four child chords:
+// with [lo, hi] the ray's parameter interval inside the block (a, b, Ax, Ay
+// as in child_chords_ab) and ca, cb the centre-line crossings clamped to it,
+// the chord is A = hi - lo, the first x half minus the second is
+// 2 ca - (lo + hi), likewise in y with cb, and the diagonal difference
+// (FF + SS) - (FS + SF) is A - 2 |ca - cb| (the part between the two
+// crossings lies in the mixed children).  A miss gives hi = lo: all zero.
+template <typename T>
+__device__ __forceinline__ void haar_split(T a, T b, T Ax, T Ay, T& A, T& dx, T& dy, T& dg)
+{
+    const T lo = fmax(a - Ax, b - Ay);
+    const T hi = fmax(fmin(a + Ax, b + Ay), lo);
+    const T ca = fmin(fmax(a, lo), hi), cb = fmin(fmax(b, lo), hi);
+    const T s = lo + hi;
+    A = hi - lo;
+    dx = fma(T(2), ca, -s);
+    dy = fma(T(2), cb, -s);
+    dg = fma(T(-2), fabs(ca - cb), A);
+}
+
 template <typename T>
 __device__ __forceinline__ void child_chords_ab(T a, T b, T Ax, T Ay, T& cFF, T& cFS, T& cSF, T& cSS)
 {

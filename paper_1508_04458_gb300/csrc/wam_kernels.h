@@ -5,21 +5,36 @@
 
 namespace wam {
 
+// The per-ray cost constant d (log d - log I0) - d as the forward of type T
+// reads it: FP64 for T = double; for T = float a pair (hi, lo) of floats
+// with hi + lo equal to the FP64 value to about 2^-48 relative (the FP32
+// forward then forms the cancelling sum dterm + d p + q in float-float and
+// needs no FP64 arithmetic per ray).
+template <typename T> struct CostTerm { using type = double; };
+template <> struct CostTerm<float> { using type = float2; };
+
+// The coefficients the strip-walk forward of type T synthesises its cells
+// from: FP64 for T = double; for T = float the float copy of beta that the
+// FP32 update keeps beside it (no FP64 arithmetic per cell).
+template <typename T> struct SynthCoef { using type = double; };
+template <> struct SynthCoef<float> { using type = float; };
+
 template <typename T>
 // leaf: the leaf walk over the tree's leaf map; null: the strip walk over the
 // grid of 2^lam-pixel cells (mu must be constant on them; lam = 0: pixels).
 // pad: scratch of 2 (nx + 2)(ny + 2) elements, required when leaf is null
 // (the strip walk reads apron-padded copies of the cell values written there).
-cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d, const double* dterm,
-                           const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
+cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d,
+                           const typename CostTerm<T>::type* dterm, const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
                            unsigned long long* work, cudaStream_t st);
 // a1 + a2 + a3 for the strip walk: the padded cell images of 2^lam pixels
 // synthesised from the coefficients beta over the tree (leaf map; null when
 // L = 0) straight into pad, then the forward pass.
 template <typename T>
-cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf, const double* beta,
-                                int lam, T* pad, const float* d, const double* dterm, const float* I0, T* qhat,
-                                T* p_out, T* resid, double* cost_part, unsigned long long* work, cudaStream_t st);
+cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8_t* leaf,
+                                const typename SynthCoef<T>::type* beta, int lam, T* pad, const float* d, const typename CostTerm<T>::type* dterm,
+                                const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
+                                unsigned long long* work, cudaStream_t st);
 int forward_parts(int V, int B);
 int forward_cost_parts(int V, int B);   // cost partials a forward launch writes (one per CTA)
 // dst row k = src row perm[k], rows of B elements (views of a scan reordered)
@@ -34,8 +49,10 @@ template <typename T>
 cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* sino, const void* dirtab, T* part,
                                unsigned long long* work, cudaStream_t st);
 template <typename T>
+// beta32 (optional): the float copy of beta, rewritten for every updated
+// coefficient
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b, const double* z0,
-                          double clamp, double* beta, unsigned long long* hits, cudaStream_t st);
+                          double clamp, double* beta, float* beta32, unsigned long long* hits, cudaStream_t st);
 template <typename T>
 cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
                              cudaStream_t st);
@@ -52,7 +69,8 @@ cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lis
                            int* counts, cudaStream_t st);
 cudaError_t launch_haar(const Layout& lay, const double* in, double* out, int inverse, double* tmp_a,
                         double* tmp_b, cudaStream_t st);
-cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, cudaStream_t st);
+// dterm of every ray in FP64 (out) and as float pairs (out2)
+cudaError_t launch_dterm(const float* d, const float* I0, long long n, double* out, float2* out2, cudaStream_t st);
 cudaError_t launch_fill_f32(float* x, long long n, float v, cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_convert(const A* x, B* y, long long n, cudaStream_t st);
