@@ -226,8 +226,13 @@ wam_status wam_resume(wam_ctx* ctx, const char* path);
 
 /* Tuning knobs (set by the caller or by an autotuner that times them). */
 enum {
-    WAM_TUNE_BACK_CTAS_PER_SM = 1   /* back-projector launches aim at this many 256-thread CTAs
+    WAM_TUNE_BACK_CTAS_PER_SM = 1,  /* back-projector launches aim at this many 256-thread CTAs
                                        per SM (default 32, range 0.25 .. 256) by splitting views */
+    WAM_TUNE_GRAPHS = 2             /* 1 (default): wam_reconstruct captures one iteration per tree
+                                       epoch (the iterations between two expansions repeat the same
+                                       launches) in a CUDA graph and replays it, when no profiling is
+                                       on and the run has no ordered subsets; 0: every kernel is
+                                       launched directly.  Results are identical either way. */
 };
 wam_status wam_set_tuning(wam_ctx* ctx, int key, double value);
 

@@ -1038,6 +1038,7 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 template <typename E>

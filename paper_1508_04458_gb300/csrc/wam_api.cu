@@ -68,6 +68,7 @@ struct wam_ctx {
     int last_lmin = 0;                     // ... and its finest leaf level
     // tuning
     double back_ctas_per_sm = 32.0;        // back-projector work split: CTAs per SM per launch
+    bool graphs = true;                    // replay each tree epoch's iteration as a CUDA graph
     cudaStream_t prof_stream = nullptr;
     int device = 0;
     int num_sms = 148;
@@ -965,6 +966,66 @@ struct Run {
     }
 };
 
+// Iterations j0 .. J-1 of a run by tree epochs: the iterations between two
+// expansions launch the same kernels (the cost slot comes from the device
+// counter), so one of them is captured in a CUDA graph and the graph is
+// replayed for the rest of the epoch.  Capture needs a stream other than the
+// legacy default one: the work runs on a private stream ordered after st, and
+// st waits for it at the end.
+template <typename T>
+wam_status iterate_graphs(wam_ctx* c, Run<T>& run, cudaStream_t st)
+{
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev = nullptr;
+    auto done = [&](wam_status s) {
+        if (gs && ev && cudaEventRecord(ev, gs) == cudaSuccess) cudaStreamWaitEvent(st, ev, 0);
+        if (gs) cudaStreamDestroy(gs);
+        if (ev) cudaEventDestroy(ev);
+        if (s != WAM_OK) cudaGetLastError();
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess ||
+        cudaStreamWaitEvent(gs, ev, 0) != cudaSuccess)
+        return done(fail(c, WAM_ERR_CUDA, "stream or event creation failed"));
+    const int j0 = run.j0;
+    if (cudaMemcpyAsync(run.counter, &j0, sizeof(int), cudaMemcpyHostToDevice, gs) != cudaSuccess)
+        return done(fail(c, WAM_ERR_CUDA, "counter copy failed"));
+    int j = j0;
+    while (j < run.J) {
+        int e = run.J;
+        if (run.L > 0 && run.next_exp < run.exp_at.size()) e = std::min(run.J, run.exp_at[run.next_exp]);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long n0 = kernel_launches();
+        if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return done(fail(c, WAM_ERR_CUDA, "stream capture could not start"));
+        wam_status s = run.iteration(j, gs, true);
+        const cudaError_t ec = cudaStreamEndCapture(gs, &graph);
+        if (s != WAM_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return done(s != WAM_OK ? s : fail(c, WAM_ERR_CUDA, "stream capture failed"));
+        }
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return done(fail(c, WAM_ERR_CUDA, "graph instantiation failed"));
+        }
+        const unsigned long long per_iter = kernel_launches() - n0;
+        for (int k = j; k < e && s == WAM_OK; ++k)
+            if (cudaGraphLaunch(exec, gs) != cudaSuccess) s = fail(c, WAM_ERR_CUDA, "graph launch failed");
+        add_launches(per_iter * (unsigned long long)(e - j - 1));
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (s != WAM_OK) return done(s);
+        j = e;
+        if (run.expands_after(j - 1)) {
+            s = run.expand(gs);
+            if (s != WAM_OK) return done(s);
+        }
+    }
+    return done(WAM_OK);
+}
+
 template <typename T>
 wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, double* hist, unsigned char* mask_out,
                             int on_device, cudaStream_t st)
@@ -973,9 +1034,13 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     c->last.valid = false;
     Run<T> run;
     WST(run.setup(c, sc, st));
-    for (int j = run.j0; j < run.J; ++j) {
-        WST(run.iteration(j, st, false));
-        if (run.expands_after(j)) WST(run.expand(st));
+    if (c->graphs && !c->prof && !c->prof_work && run.S == 1 && run.j0 < run.J) {
+        WST(iterate_graphs(c, run, st));
+    } else {
+        for (int j = run.j0; j < run.J; ++j) {
+            WST(run.iteration(j, st, false));
+            if (run.expands_after(j)) WST(run.expand(st));
+        }
     }
     WST(run.final_cost(st, false));
     std::vector<double> h;
@@ -1972,6 +2037,11 @@ wam_status wam_set_tuning(wam_ctx* c, int key, double value)
     if (key == WAM_TUNE_BACK_CTAS_PER_SM) {
         if (!(value >= 0.25 && value <= 256.0)) return fail(c, WAM_ERR_ARG, "CTAs per SM must be in [0.25, 256]");
         c->back_ctas_per_sm = value;
+        return WAM_OK;
+    }
+    if (key == WAM_TUNE_GRAPHS) {
+        if (value != 0.0 && value != 1.0) return fail(c, WAM_ERR_ARG, "graphs: 0 or 1");
+        c->graphs = value != 0.0;
         return WAM_OK;
     }
     return fail(c, WAM_ERR_ARG, "unknown tuning key");

@@ -78,6 +78,8 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
                                 const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st);
 
 unsigned long long kernel_launches();
+// kernels run by graph replays (counted once when captured)
+void add_launches(unsigned long long n);
 void count_launch();
 
 // grad.cu: operators for the gradient and the unrolled-AM patterns

@@ -35,6 +35,7 @@ WAM_ERR_IO = -6
 WAM_WARN_NONMONOTONE = 1
 WAM_MAX_LEVELS = 8
 WAM_TUNE_BACK_CTAS_PER_SM = 1
+WAM_TUNE_GRAPHS = 2
 WAM_PROFILE_OFF, WAM_PROFILE_ALL, WAM_PROFILE_TIME, WAM_PROFILE_WORK = 0, 1, 2, 3
 
 
