@@ -211,8 +211,15 @@ def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
     return AMResult(beta, mu, np.array(costs), np.array(z0s), tree, trees, np.array(nact))
 
 
-def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None) -> AMResult:
-    """O'Sullivan-Benac AM: Algorithm 1 with Omega = I and every pixel active."""
+def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None, nonneg: bool = False) -> AMResult:
+    """O'Sullivan-Benac AM: Algorithm 1 with Omega = I and every pixel active.
+
+    nonneg: keep mu >= 0 by ending each pixel's step at mu = 0 where the
+    unconstrained step would cross it.  With Omega = I the surrogate of
+    Eq. 1.8 is a sum of one-dimensional convex functions, one per pixel, so
+    this clamp is its exact minimiser over mu >= 0 and the decrease guarantee
+    holds.  Algorithm 1 itself is unconstrained (the default); the paper's
+    problem statement (Eq. 1.3) asks for a nonnegative image."""
     d = np.asarray(d, dtype=np.float64).ravel()
     Hc = H.tocsc()
     b = Hc.T @ d
@@ -223,6 +230,8 @@ def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None) -> AMResult:
         costs.append(cost)
         z0s.append(Z0)
         mu += delta
+        if nonneg:
+            mu = np.maximum(mu, 0.0)
     costs.append(idiv(d, I0, Hc @ mu))
     out = mu.reshape(shape) if shape is not None else mu
     return AMResult(mu, out, np.array(costs), np.array(z0s), None, [], np.array([H.shape[1]] * n_iter))

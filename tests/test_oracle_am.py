@@ -314,3 +314,39 @@ def test_os_single_pixel_reaches_the_fixed_point_in_one_sub_step():
     H = sp.csr_matrix(np.full((n, 1), h))
     r = am.os_wavelet_am(H, np.full(n, dv), I0, 1, 1, 0, 3, 3, 1)
     assert abs(r.beta[0] - np.log(I0 / dv) / h) <= 1e-14
+
+
+def test_nonneg_plain_am_minimises_the_surrogate_over_nonnegative_images():
+    # low counts, so that unconstrained AM drives background pixels negative
+    p, H = _small(nx=16, ny=16, V=20, B=29, seed=11)
+    rng = np.random.default_rng(12)
+    I0 = 30.0
+    d = rng.poisson(I0 * np.exp(-p.line_integrals.ravel())).astype(np.float64)
+    free = am.plain_am(H, d, I0, 30)
+    assert free.mu.min() < -1e-4
+    nn = am.plain_am(H, d, I0, 30, nonneg=True)
+    assert nn.mu.min() >= 0.0
+    assert np.all(np.diff(nn.cost) <= 1e-12 * nn.cost[:-1])
+    # the oracle's clamped step from an iterate with pixels at the bound equals
+    # the minimiser over mu >= 0 of the surrogate of Eq. 1.8 (Omega = I), found
+    # by a generic bounded quasi-Newton search on the surrogate's own formula
+    Hc = H.tocsc()
+    b = Hc.T @ d
+    mu_hat = am.plain_am(H, d, I0, 12, nonneg=True).mu
+    assert np.sum(mu_hat == 0.0) > 0
+    delta, _, Z0 = am.am_step(Hc, b, mu_hat, d, I0)
+    step = np.maximum(mu_hat + delta, 0.0)
+    qhat = I0 * np.exp(-(Hc @ mu_hat))
+    Hd = H.toarray()
+    r = Hd / Z0
+
+    def F(mu):
+        ex = r * np.exp(-Z0 * (mu - mu_hat)[None, :])
+        val = b @ mu + qhat @ (ex.sum(axis=1) + 1.0 - r.sum(axis=1))
+        grad = b - Z0 * (qhat @ ex)
+        return val, grad
+
+    res = so.minimize(F, mu_hat, jac=True, method="L-BFGS-B", bounds=[(0.0, None)] * mu_hat.size,
+                      options=dict(ftol=1e-15, gtol=1e-12, maxiter=5000))
+    np.testing.assert_allclose(res.x, step, atol=2e-6 * max(1.0, np.abs(step).max()))
+    assert np.any((step == 0.0) & (mu_hat + delta < 0.0))   # the bound is active somewhere
