@@ -111,6 +111,12 @@ typedef struct {
                                  that subset's b = Phi_s^T d_s, bhat+- and Z0 (max over its rays).
                                  2-D contexts, wam_reconstruct only; idiv_hist still holds the
                                  full I-divergence at the start of every iteration. */
+    int nonneg;               /* plain AM only (full_am, or levels = 0): 1 = keep mu >= 0 by ending
+                                 each pixel's (voxel's) step at 0.  With Omega = I the surrogate of
+                                 Eq. 1.8 is a sum of one-dimensional convex functions, so this is its
+                                 exact minimiser over mu >= 0 and the cost still decreases at every
+                                 iteration.  0 (default) = Algorithm 1 as stated, unconstrained.
+                                 WAM_ERR_ARG with a Haar tree (levels > 0 and not full_am). */
 } wam_schedule;
 
 typedef struct wam_ctx wam_ctx;
@@ -197,10 +203,10 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
  * history I(d || qhat^(0..j)), the schedule it ran, the geometry, CRC-32
  * fingerprints of d and I0, and the back-projector tuning value; the file ends
  * with a CRC-32 of its contents and is written to "<path>.tmp" and renamed.
- * Format (little endian): "WAMCKPT1", u32 version 1, u32 0; 21 int64 (kind,
+ * Format (little endian): "WAMCKPT1", u32 version 2, u32 0; 22 int64 (kind,
  * nx, ny, nz, n_views, n_bins, n_rows, levels, dims, zsum_criterion,
  * precision, full_am, n_expand, iterations done, expansions done, N,
- * mask bytes, history length, crc(d), crc(I0), n_subsets); 11 double (vx, vy, vz,
+ * mask bytes, history length, crc(d), crc(I0), n_subsets, nonneg); 11 double (vx, vy, vz,
  * angle0, angle_span, bin_pitch, row_pitch, sod, sdd, dmax_clamp, tuning);
  * int64 expand_at[n_expand]; double tau[n_expand]; double beta[N];
  * u8 masks[mask bytes]; double history[iterations done + 1]; u32 crc.
@@ -215,7 +221,7 @@ wam_status wam_checkpoint(wam_ctx* ctx, const char* path);
  * The context's back-projector tuning is set to the checkpoint's.  Requires
  * data set (wam_set_data) equal to the checkpoint's (CRC-32 of d and I0) and
  * an equal geometry; the continuing schedule must have the same levels, dims,
- * zsum_criterion, precision, full_am, dmax_clamp and n_subsets, n_iters >= j, and the
+ * zsum_criterion, precision, full_am, dmax_clamp, n_subsets and nonneg, n_iters >= j, and the
  * same first expansions (those applied so far) with no other expansion at or
  * before j, else that wam_reconstruct returns WAM_ERR_STATE and the loaded
  * state stays pending.  wam_set_data discards a pending state.

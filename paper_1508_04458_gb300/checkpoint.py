@@ -13,7 +13,7 @@ import numpy as np
 MAGIC = b"WAMCKPT1"
 INT_FIELDS = ("kind", "nx", "ny", "nz", "n_views", "n_bins", "n_rows", "levels", "dims", "zsum_criterion",
               "precision", "full_am", "n_expand", "iters_done", "expansions_done", "n_coef", "mask_bytes",
-              "n_hist", "crc_d", "crc_I0", "n_subsets")
+              "n_hist", "crc_d", "crc_I0", "n_subsets", "nonneg")
 DBL_FIELDS = ("vx", "vy", "vz", "angle0", "angle_span", "bin_pitch", "row_pitch", "sod", "sdd", "dmax_clamp",
               "tuning")
 
@@ -31,7 +31,7 @@ def parse(buf: bytes) -> dict:
     if zlib.crc32(buf[:-4]) & 0xFFFFFFFF != crc:
         raise CheckpointError("CRC mismatch")
     version, _ = struct.unpack_from("<II", buf, 8)
-    if version != 1:
+    if version != 2:
         raise CheckpointError("unsupported version %d" % version)
     at = 16
     head = 8 * (len(INT_FIELDS) + len(DBL_FIELDS))

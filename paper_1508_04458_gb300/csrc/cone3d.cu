@@ -720,7 +720,7 @@ __device__ __forceinline__ double am_delta32(double b, float bp, float bm, doubl
 // octet, or (k = 0) the approximation and (k = 1..7) detail type k of a block
 // (types 1..3 only for the per-slice 2-D tree).
 __global__ void k_update3(SegTable3 tab, Layout3 lay, const float* __restrict__ part, const double* __restrict__ bvec,
-                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta)
+                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta, int nonneg)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= 8LL * tab.total_items) return;
@@ -736,13 +736,15 @@ __global__ void k_update3(SegTable3 tab, Layout3 lay, const float* __restrict__ 
     if (S.octet) {
         const long long z = ((long long)(2 * bz + (k >> 2)) * lay.ny + 2 * by + ((k >> 1) & 1)) * lay.nx +
                             2 * bx + (k & 1);
-        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, k), 0.0f, z0, iz0, clamp);
+        const double nb = beta[z] + am_delta32(bvec[z], sum_slot3(S, part, item, k), 0.0f, z0, iz0, clamp);
+        beta[z] = nonneg ? fmax(nb, 0.0) : nb;       // plain AM kept nonnegative: the step ends at 0
         return;
     }
     if (k == 0) {
         if (!S.has_approx) return;
         const long long z = approx3(lay, bx, by, bz);
-        beta[z] += am_delta32(bvec[z], sum_slot3(S, part, item, 0), 0.0f, z0, iz0, clamp);
+        const double nb = beta[z] + am_delta32(bvec[z], sum_slot3(S, part, item, 0), 0.0f, z0, iz0, clamp);
+        beta[z] = (nonneg && S.level == 0) ? fmax(nb, 0.0) : nb;
         return;
     }
     if (!S.has_details || k > (lay.z3 ? 7 : 3)) return;
@@ -753,11 +755,11 @@ __global__ void k_update3(SegTable3 tab, Layout3 lay, const float* __restrict__ 
 }
 
 cudaError_t launch_update3(const SegTable3& tab, const Layout3& lay, const float* part, const double* b,
-                           const double* z0, double clamp, double* beta, cudaStream_t st)
+                           const double* z0, double clamp, double* beta, int nonneg, cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
     count_launch();
-    k_update3<<<nb(8LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta);
+    k_update3<<<nb(8LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta, nonneg);
     return cudaGetLastError();
 }
 

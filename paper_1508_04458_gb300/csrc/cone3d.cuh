@@ -58,8 +58,9 @@ cudaError_t launch_forward3(const Geom3& g, const float* mu, float* pad, const u
 int forward3_parts(const Geom3& g);
 cudaError_t launch_backproject3(const Geom3& g, const SegTable3& tab, int z3, const float* sino, float* part,
                                 unsigned long long* work, cudaStream_t st);
+// nonneg: voxel coefficients (plain AM) end their step at 0
 cudaError_t launch_update3(const SegTable3& tab, const Layout3& lay, const float* part, const double* b,
-                           const double* z0, double clamp, double* beta, cudaStream_t st);
+                           const double* z0, double clamp, double* beta, int nonneg, cudaStream_t st);
 cudaError_t launch_reduce_voxels3(const SegTable3& tab, const Layout3& lay, const float* part, double* out,
                                   float* outf, cudaStream_t st);
 cudaError_t launch_z03(const Geom3& g, const Layout3& lay, const uint8_t* leaf, double* part, cudaStream_t st);

@@ -665,19 +665,21 @@ __device__ __forceinline__ T group_sum(T x)
 template <typename T, int G>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
-                         float* __restrict__ beta32, unsigned long long* __restrict__ hits)
+                         float* __restrict__ beta32, int nonneg, unsigned long long* __restrict__ hits)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cf = gid / G;
     const int lane8 = (int)(gid % G);
     long long z = -1;
     T bp = T(0), bm = T(0);
+    bool pix = false;                      // a pixel coefficient (pixel basis)
     if (cf < 4LL * tab.total_items) {      // every lane reaches the shuffles below
         const int it = (int)(cf >> 2), k = (int)(cf & 3);
         const Segment& S = tab.s[find_item_segment(tab, it)];
         const int item = it - S.item_begin;
         int bx, by;
         item_block(S, item, bx, by);
+        pix = S.quad || S.level == 0;
         if (S.quad) {
             z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
             bp = sum_slot_lane<G>(S, part, item, k, lane8);
@@ -699,7 +701,10 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
     bool hit = false;
-    const double nb = beta[z] + am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    double nb = beta[z] + am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    // plain AM kept nonnegative: the pixel's step ends at mu = 0 (the
+    // separable surrogate's minimiser over mu >= 0)
+    if (nonneg && pix) nb = fmax(nb, 0.0);
     beta[z] = nb;
     if (beta32) beta32[z] = (float)nb;
     add_work(hits, hit ? 1u : 0u);     // steps at the clamp |Z0 Delta| = clamp
@@ -1177,17 +1182,17 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
 
 template <typename T>
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b,
-                          const double* z0, double clamp, double* beta, float* beta32, unsigned long long* hits,
-                          cudaStream_t st)
+                          const double* z0, double clamp, double* beta, float* beta32, int nonneg,
+                          unsigned long long* hits, cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
     COUNT_LAUNCH();
     if (tab.total_items < 16384)
         k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                          beta32, hits);
+                                                                          beta32, nonneg, hits);
     else
         k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                         beta32, hits);
+                                                                         beta32, nonneg, hits);
     return cudaGetLastError();
 }
 
@@ -1344,7 +1349,7 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \
     template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
-                                          double, double*, float*, unsigned long long*, cudaStream_t);           \
+                                          double, double*, float*, int, unsigned long long*, cudaStream_t);      \
     template cudaError_t launch_split_out<T>(const SegTable&, const Layout&, const T*, double*, double*,         \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_synth<T>(const Layout&, const uint8_t*, const double*, T*, cudaStream_t);        \

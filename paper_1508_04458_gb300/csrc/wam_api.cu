@@ -47,7 +47,7 @@ struct RunRecord {
     double clamp = 30.0;
     std::vector<int> expand_at;
     std::vector<double> tau;
-    int iters_done = 0, expansions_done = 0, n_subsets = 1;
+    int iters_done = 0, expansions_done = 0, n_subsets = 1, nonneg = 0;
     double tuning = 32.0;
     std::vector<double> beta, hist;     // host copies (loaded state only)
     std::vector<uint8_t> mask;
@@ -169,6 +169,7 @@ void record_run(wam_ctx* c, const wam_schedule* sc, int iters, int expansions)
     r.iters_done = iters;
     r.expansions_done = expansions;
     r.n_subsets = std::max(1, sc->n_subsets);
+    r.nonneg = sc->nonneg != 0;
     r.tuning = c->back_ctas_per_sm;
     c->pending = RunRecord{};
 }
@@ -181,7 +182,8 @@ wam_status check_resume(wam_ctx* c, const wam_schedule* sc)
     if (!r.valid) return WAM_OK;
     const int L = sc->full_am ? 0 : sc->levels;
     if (L != r.levels || sc->full_am != r.full_am || sc->precision != r.precision || eff_dims(c, sc) != r.dims ||
-        sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp || std::max(1, sc->n_subsets) != r.n_subsets)
+        sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp || std::max(1, sc->n_subsets) != r.n_subsets ||
+        (sc->nonneg != 0) != (r.nonneg != 0))
         return fail(c, WAM_ERR_STATE, "resume: the schedule's method differs from the checkpoint's");
     if (sc->n_iters < r.iters_done) return fail(c, WAM_ERR_STATE, "resume: n_iters is below the iterations done");
     if (L > 0) {
@@ -844,7 +846,7 @@ struct Run {
                                           work_ptr(c, WAM_K_BACKPROJECT), st));
             }
             PROF(WAM_K_UPDATE);
-            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, beta32,
+            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, beta32, sc->nonneg,
                                  work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
@@ -896,7 +898,8 @@ struct Run {
         }
         {
             PROF(WAM_K_UPDATE);                                                             // a6
-            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, beta32, work_ptr(c, WAM_K_UPDATE), st));
+            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, beta32, sc->nonneg, work_ptr(c, WAM_K_UPDATE),
+                                 st));
         }
         return WAM_OK;
     }
@@ -1442,7 +1445,7 @@ wam_status reconstruct3_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, d
         }
         {
             PROF(WAM_K_UPDATE);
-            WCK(c, launch_update3(tab, lay, part, bvec, z0, clamp, beta, st));
+            WCK(c, launch_update3(tab, lay, part, bvec, z0, clamp, beta, sc->nonneg, st));
         }
         if (L > 0 && next_exp < exp_at.size() && exp_at[next_exp] == j + 1) {
             const double tau = sc->tau[next_exp];
@@ -1672,6 +1675,9 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
         return fail(c, WAM_ERR_ARG, "n_subsets must be in 0..n_views");
     if (sc->n_subsets > 1 && c->g.kind == WAM_CONE3D_FLAT_CIRCULAR)
         return fail(c, WAM_ERR_ARG, "ordered subsets: 2-D contexts only");
+    if (sc->nonneg != 0 && sc->nonneg != 1) return fail(c, WAM_ERR_ARG, "nonneg must be 0 or 1");
+    if (sc->nonneg && !sc->full_am && sc->levels != 0)
+        return fail(c, WAM_ERR_ARG, "nonneg applies to plain AM (full_am or levels = 0) only");
     if (sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c, WAM_ERR_ARG, "expand_at/tau missing");
     for (int k = 0; k < sc->n_expand; ++k) {
@@ -1710,13 +1716,13 @@ wam_status wam_checkpoint(wam_ctx* c, const char* path)
         const wam_geometry& g = c->g;
         CkptWriter w;
         w.raw(kCkptMagic, 8);
-        const uint32_t version = 1, zero = 0;
+        const uint32_t version = 2, zero = 0;
         w.raw(&version, 4);
         w.raw(&zero, 4);
-        const long long ints[21] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
+        const long long ints[22] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
                                     r.zsum, r.precision, r.full_am, (long long)r.expand_at.size(), r.iters_done,
                                     r.expansions_done, c->N, (long long)mb, (long long)hist.size(), cd, ci,
-                                    r.n_subsets};
+                                    r.n_subsets, r.nonneg};
         for (long long v : ints) w.i64(v);
         const double dbl[11] = {g.vx, g.vy, g.vz, g.angle0, g.angle_span, g.bin_pitch, g.row_pitch, g.sod, g.sdd,
                                 r.clamp, r.tuning};
@@ -1770,9 +1776,9 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         CkptReader rd{buf.data(), buf.size() - 4};
         rd.at = 8;
         uint32_t version = 0, zero = 0;
-        if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || version != 1)
+        if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || version != 2)
             return fail(c, WAM_ERR_IO, "unsupported checkpoint version");
-        long long v[21];
+        long long v[22];
         double d[11];
         for (long long& x : v)
             if (!rd.i64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
@@ -1798,13 +1804,14 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         r.iters_done = (int)v[13];
         r.expansions_done = (int)v[14];
         r.n_subsets = (int)v[20];
+        r.nonneg = (int)v[21];
         r.clamp = d[9];
         r.tuning = d[10];
         const size_t mb = r.levels > 0 ? wam_mask_bytes_dims(c, r.levels, r.dims) : 0;
         if (r.levels < 0 || r.levels > WAM_MAX_LEVELS || n_expand < 0 || n_expand > 4096 || r.iters_done < 0 ||
             r.expansions_done < 0 || r.expansions_done > n_expand || v[15] != c->N || v[16] != (long long)mb ||
             v[17] != (long long)r.iters_done + 1 || !(r.tuning >= 0.25 && r.tuning <= 256.0) || r.n_subsets < 1 ||
-            r.n_subsets > c->g.n_views)
+            r.n_subsets > c->g.n_views || (r.nonneg != 0 && r.nonneg != 1))
             return fail(c, WAM_ERR_IO, "checkpoint header is inconsistent with this context");
         r.expand_at.resize((size_t)n_expand);
         r.tau.resize((size_t)n_expand);

@@ -50,9 +50,10 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
                                unsigned long long* work, cudaStream_t st);
 template <typename T>
 // beta32 (optional): the float copy of beta, rewritten for every updated
-// coefficient
+// coefficient; nonneg: pixel coefficients end their step at 0 (plain AM)
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b, const double* z0,
-                          double clamp, double* beta, float* beta32, unsigned long long* hits, cudaStream_t st);
+                          double clamp, double* beta, float* beta32, int nonneg, unsigned long long* hits,
+                          cudaStream_t st);
 template <typename T>
 cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
                              cudaStream_t st);

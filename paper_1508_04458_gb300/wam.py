@@ -53,7 +53,7 @@ class wam_schedule(ctypes.Structure):
                 ("n_expand", ctypes.c_int), ("expand_at", ctypes.POINTER(ctypes.c_int)),
                 ("tau", ctypes.POINTER(ctypes.c_double)), ("zsum_criterion", ctypes.c_int),
                 ("precision", ctypes.c_int), ("full_am", ctypes.c_int), ("dmax_clamp", ctypes.c_double),
-                ("n_subsets", ctypes.c_int)]
+                ("n_subsets", ctypes.c_int), ("nonneg", ctypes.c_int)]
 
 
 WAM_K_FORWARD, WAM_K_BACKPROJECT, WAM_K_UPDATE, WAM_K_Z0, WAM_K_SYNTH, WAM_K_TREE = range(6)
@@ -150,14 +150,15 @@ def geometry(g) -> wam_geometry:
 
 def schedule(levels: int, n_iters: int, expand_at: Sequence[int] = (), tau: Sequence[float] = (),
              precision: int = 32, full_am: bool = False, clamp: float = 30.0, dims: int = 2,
-             zsum: bool = False, n_subsets: int = 1):
+             zsum: bool = False, n_subsets: int = 1, nonneg: bool = False):
     """wam_schedule plus the arrays it points to (keep the tuple alive)."""
     ea = (ctypes.c_int * max(1, len(expand_at)))(*expand_at)
     ta = (ctypes.c_double * max(1, len(tau)))(*tau)
     s = wam_schedule(levels=levels, dims=dims, n_iters=n_iters, n_expand=len(expand_at),
                      expand_at=ctypes.cast(ea, ctypes.POINTER(ctypes.c_int)),
                      tau=ctypes.cast(ta, ctypes.POINTER(ctypes.c_double)), zsum_criterion=1 if zsum else 0,
-                     precision=precision, full_am=1 if full_am else 0, dmax_clamp=clamp, n_subsets=n_subsets)
+                     precision=precision, full_am=1 if full_am else 0, dmax_clamp=clamp, n_subsets=n_subsets,
+                     nonneg=1 if nonneg else 0)
     return s, (ea, ta)
 
 
@@ -210,13 +211,14 @@ class Context:
 
     def reconstruct(self, levels: int, n_iters: int, expand_at=(), tau=(), precision: int = 32,
                     full_am: bool = False, device_out: bool = False, stream: Optional[int] = None,
-                    dims: int = 2, zsum: bool = False, n_subsets: int = 1):
+                    dims: int = 2, zsum: bool = False, n_subsets: int = 1, nonneg: bool = False):
         """Run the method; returns (mu, idiv history, masks, status).  Cone-beam
         contexts: dims = 3 (3-D Haar) or dims = 2 with zsum (per-slice Haar).
-        n_subsets > 1: ordered subsets of views (2-D)."""
+        n_subsets > 1: ordered subsets of views (2-D).  nonneg: plain AM with
+        mu >= 0 (each pixel's step ends at 0)."""
         import torch
         sc, keep = schedule(levels, n_iters, expand_at, tau, precision, full_am, dims=dims, zsum=zsum,
-                            n_subsets=n_subsets)
+                            n_subsets=n_subsets, nonneg=nonneg)
         L = 0 if full_am else levels
         N = self.geom.nx * self.geom.ny * max(1, getattr(self.geom, "nz", 1))
         s = current_stream() if stream is None else stream

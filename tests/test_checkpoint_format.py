@@ -11,8 +11,8 @@ from paper_1508_04458_gb300 import checkpoint as ck
 
 
 def _assemble(ints, dbls, expand_at, tau, beta, masks, hist):
-    b = bytearray(b"WAMCKPT1") + struct.pack("<II", 1, 0)
-    b += struct.pack("<21q", *ints) + struct.pack("<11d", *dbls)
+    b = bytearray(b"WAMCKPT1") + struct.pack("<II", 2, 0)
+    b += struct.pack("<22q", *ints) + struct.pack("<11d", *dbls)
     b += struct.pack("<%dq" % len(expand_at), *expand_at) + struct.pack("<%dd" % len(tau), *tau)
     b += np.asarray(beta, "<f8").tobytes() + np.asarray(masks, np.uint8).tobytes()
     b += np.asarray(hist, "<f8").tobytes()
@@ -28,7 +28,7 @@ def _example():
     beta = rng.normal(size=N)
     masks = (rng.random(mb) < 0.5).astype(np.uint8)
     hist = np.sort(rng.random(7))[::-1] * 1e5
-    ints = [1, nx, ny, 1, 30, 41, 1, L, 2, 0, 32, 0, 2, 6, 1, N, mb, 7, 123456789, 987654321, 4]
+    ints = [1, nx, ny, 1, 30, 41, 1, L, 2, 0, 32, 0, 2, 6, 1, N, mb, 7, 123456789, 987654321, 4, 0]
     dbls = [1.0, 1.0, 1.0, 0.0, 6.283185307179586, 1.2, 1.0, 500.0, 800.0, 30.0, 32.0]
     return _assemble(ints, dbls, [3, 9], [0.1, -1.0], beta, masks, hist), beta, masks, hist
 
@@ -39,6 +39,7 @@ def test_round_trip():
     assert (c["nx"], c["ny"], c["levels"], c["iters_done"], c["expansions_done"]) == (16, 8, 2, 6, 1)
     assert c["expand_at"] == [3, 9] and c["tau"] == [0.1, -1.0]
     assert c["crc_d"] == 123456789 and c["sdd"] == 800.0 and c["tuning"] == 32.0 and c["n_subsets"] == 4
+    assert c["nonneg"] == 0
     np.testing.assert_array_equal(c["beta"], beta)
     np.testing.assert_array_equal(c["masks"], masks)
     np.testing.assert_array_equal(c["hist"], hist)
