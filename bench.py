@@ -363,6 +363,13 @@ def run_wam(args, problem, world, rank, local_rank):
                 "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS sm_max_mhz) / %d "
                               "instructions per intersection" % (sms, clk_mhz, K_MIN),
                 "work_per_launch": per_launch_work, "ms_per_launch": per_launch_ms}
+    if traffic and per_launch_ms > 0:
+        # the HBM side of the same kernel: its DRAM bytes per launch (ncu, cold replay) over its live
+        # launch time, against the measured copy rate -- small, since the working set lives in L2
+        gbps = traffic / (per_launch_ms / 1e3) / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6746.0))
+        roofline["dram"] = {"GBps": gbps, "peak_GBps": hbm, "frac": gbps / hbm,
+                            "basis": "dram__bytes per launch (ncu) / live launch time; peak = MEASURED_PEAKS hbm_gbs"}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
