@@ -384,7 +384,10 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
         const double full = (double)kItemsPerCta * V * cost[i];
         int chunks = (int)std::ceil(full / per_cta);
         chunks = std::max(1, std::min(chunks, max_chunks));
+        // views per chunk a multiple of the CTA's view lanes, so that its warps
+        // get equal view counts and meet at the final barrier together
         s.vpc = (V + chunks - 1) / chunks;
+        s.vpc = std::min(V, (s.vpc + kViewLanes - 1) / kViewLanes * kViewLanes);
         s.n_chunks = (V + s.vpc - 1) / s.vpc;
         s.tiles = (li.n + kItemsPerCta - 1) / kItemsPerCta;
         s.cta_begin = cta;
