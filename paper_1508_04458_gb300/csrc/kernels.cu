@@ -633,10 +633,11 @@ __device__ __forceinline__ double am_step(double b, double bp, double bm, double
     return am_delta(b, bp, bm, z0, clamp, hit);
 }
 
-// Sum of one slot of an item over the view chunks c = lane, lane + 8, ... of
-// one lane of a group of 8 (fixed order within the lane).
-template <int G, typename T>
-__device__ __forceinline__ T sum_slot_lane(const Segment& S, const T* __restrict__ part, int item, int slot, int lane)
+// Sum of one slot of an item over the view chunks c = lane, lane + G, ... of
+// one lane of a group of G (fixed order within the lane).
+template <typename T>
+__device__ __forceinline__ T sum_slot_lane(const Segment& S, const T* __restrict__ part, int item, int slot, int lane,
+                                           int G)
 {
     T s = T(0);
     const T* p = part + S.part_off + (size_t)slot * S.n_items + item;
@@ -662,41 +663,57 @@ __device__ __forceinline__ T group_sum(T x)
 // block; the lanes split the item's view-chunk partials, a fixed butterfly
 // adds them, and lane 0 applies the update.  G = 8 when the items are few
 // (coarse trees, whose items carry many view chunks), else 1.
-template <typename T, int G>
+// Lanes per coefficient of a segment: 8 when its items carry many view
+// chunks (the chunk sums split over the lanes, then a fixed butterfly), else 1.
+__host__ __device__ __forceinline__ int upd_lanes(const Segment& S) { return S.n_chunks >= 8 ? 8 : 1; }
+// Threads of a segment in the update grid: 4 coefficients per item, its lanes
+// each, padded to whole warps (a warp never spans two segments).
+__host__ __device__ __forceinline__ long long upd_threads(const Segment& S)
+{
+    return (4LL * S.n_items * upd_lanes(S) + 31) / 32 * 32;
+}
+
+template <typename T>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
                          float* __restrict__ beta32, int nonneg, unsigned long long* __restrict__ hits)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long cf = gid / G;
-    const int lane8 = (int)(gid % G);
+    int si = 0;
+    long long first = 0;
+    while (si < tab.n && gid >= first + upd_threads(tab.s[si])) first += upd_threads(tab.s[si++]);
+    if (si >= tab.n) return;                 // whole warps past the last segment
+    const Segment& S = tab.s[si];
+    const int G = upd_lanes(S);              // uniform over the warp
+    const long long local = gid - first;
+    const long long cf = local / G;
+    const int lane8 = (int)(local % G);
     long long z = -1;
     T bp = T(0), bm = T(0);
-    bool pix = false;                      // a pixel coefficient (pixel basis)
-    if (cf < 4LL * tab.total_items) {      // every lane reaches the shuffles below
-        const int it = (int)(cf >> 2), k = (int)(cf & 3);
-        const Segment& S = tab.s[find_item_segment(tab, it)];
-        const int item = it - S.item_begin;
+    const bool pix = S.quad || S.level == 0;   // a pixel coefficient (pixel basis)
+    if (cf < 4LL * S.n_items) {              // every lane reaches the shuffles below
+        const int item = (int)(cf >> 2), k = (int)(cf & 3);
         int bx, by;
         item_block(S, item, bx, by);
-        pix = S.quad || S.level == 0;
         if (S.quad) {
             z = (long long)(2 * by + (k >> 1)) * lay.nx + 2 * bx + (k & 1);
-            bp = sum_slot_lane<G>(S, part, item, k, lane8);
+            bp = sum_slot_lane(S, part, item, k, lane8, G);
         } else if (k == 0) {
             if (S.has_approx) {
                 z = approx_index(lay, S.level, bx, by);
-                bp = sum_slot_lane<G>(S, part, item, 0, lane8);
+                bp = sum_slot_lane(S, part, item, 0, lane8, G);
             }
         } else if (S.has_details) {
             const int t = k - 1, slot = (S.has_approx ? 1 : 0) + 2 * t;
             z = detail_index(lay, S.level, t, bx, by);
-            bp = sum_slot_lane<G>(S, part, item, slot, lane8);
-            bm = sum_slot_lane<G>(S, part, item, slot + 1, lane8);
+            bp = sum_slot_lane(S, part, item, slot, lane8, G);
+            bm = sum_slot_lane(S, part, item, slot + 1, lane8, G);
         }
     }
-    bp = group_sum<G>(bp);
-    bm = group_sum<G>(bm);
+    if (G == 8) {
+        bp = group_sum<8>(bp);
+        bm = group_sum<8>(bm);
+    }
     if (z < 0 || lane8 != 0) return;
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
@@ -1186,13 +1203,10 @@ cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part,
                           unsigned long long* hits, cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
+    long long threads = 0;
+    for (int i = 0; i < tab.n; ++i) threads += upd_threads(tab.s[i]);
     COUNT_LAUNCH();
-    if (tab.total_items < 16384)
-        k_update<T, 8><<<nblk(32LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                          beta32, nonneg, hits);
-    else
-        k_update<T, 1><<<nblk(4LL * tab.total_items, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta,
-                                                                         beta32, nonneg, hits);
+    k_update<T><<<nblk(threads, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta, beta32, nonneg, hits);
     return cudaGetLastError();
 }
 
