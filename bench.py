@@ -384,7 +384,8 @@ def run_wam(args, problem, world, rank, local_rank):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "AM iters/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+            "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps,
+            "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64"),
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
