@@ -928,48 +928,94 @@ __device__ __forceinline__ uint32_t compact_bits(uint32_t x)
     return x;
 }
 
+// A list's Morton codes go by chunks of 1024, one CTA each: a first launch
+// counts each chunk's kept blocks, a second one writes them at the offset the
+// chunks before it sum to (the same order as one sequential pass).
+struct CompactList {
+    int level, want, gw, gh;
+    long long ncode;
+};
+
+__device__ __forceinline__ CompactList compact_list(const Layout& lay, int list)
+{
+    CompactList c;
+    c.level = list <= 1 ? lay.L : lay.L - (list - 1);
+    c.want = list == 0 ? 0 : 1;
+    c.gw = lay.gw[c.level];
+    c.gh = lay.gh[c.level];
+    int side = 1;
+    while (side < c.gw || side < c.gh) side <<= 1;
+    c.ncode = (long long)side * side;
+    return c;
+}
+
+// kept blocks of chunk `chunk` of list `list`: this thread's flag and code,
+// the CTA's total and this thread's rank among the kept (in code order)
+__device__ __forceinline__ void compact_chunk(const Layout& lay, const uint8_t* __restrict__ mask,
+                                              const CompactList& cl, int chunk, bool& keep, uint32_t& code,
+                                              int& rank, int& total)
+{
+    __shared__ int warp_cnt[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long m = (long long)chunk * 1024 + threadIdx.x;
+    keep = false;
+    code = 0;
+    if (m < cl.ncode) {
+        const int bx = (int)compact_bits((uint32_t)m), by = (int)compact_bits((uint32_t)(m >> 1));
+        if (bx < cl.gw && by < cl.gh) {
+            const int e = mask[lay.moff[cl.level] + (long long)by * cl.gw + bx] ? 1 : 0;
+            keep = (e == cl.want);
+            code = ((uint32_t)by << 16) | (uint32_t)bx;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) warp_cnt[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+        const int n = warp_cnt[w];
+        off += w < wid ? n : 0;
+        tot += n;
+    }
+    rank = off + __popc(bal & ((1u << lane) - 1u));
+    total = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_compact_count(Layout lay, const uint8_t* __restrict__ mask,
+                                                        int* __restrict__ chunk_cnt, int max_chunks)
+{
+    const int list = blockIdx.y, chunk = blockIdx.x;
+    const CompactList cl = compact_list(lay, list);
+    if ((long long)chunk * 1024 >= cl.ncode) return;
+    bool keep;
+    uint32_t code;
+    int rank, total;
+    compact_chunk(lay, mask, cl, chunk, keep, code, rank, total);
+    if (threadIdx.x == 0) chunk_cnt[list * max_chunks + chunk] = total;
+}
+
 __global__ void __launch_bounds__(1024) k_compact(Layout lay, const uint8_t* __restrict__ mask,
                                                   uint32_t* __restrict__ lists, long long list_stride,
+                                                  const int* __restrict__ chunk_cnt, int max_chunks,
                                                   int* __restrict__ counts)
 {
-    const int list = blockIdx.x;
-    const int level = list <= 1 ? lay.L : lay.L - (list - 1);
-    const int want = list == 0 ? 0 : 1;
-    const int gw = lay.gw[level], gh = lay.gh[level];
-    int side = 1;
-    while (side < gw || side < gh) side <<= 1;
-    const long long ncode = (long long)side * side;
-    uint32_t* out = lists + list_stride * list;
-    __shared__ int warp_cnt[32];
+    const int list = blockIdx.y, chunk = blockIdx.x;
+    const CompactList cl = compact_list(lay, list);
+    const int nchunk = (int)((cl.ncode + 1023) / 1024);
+    if (chunk >= nchunk) return;
     __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long m0 = 0; m0 < ncode; m0 += blockDim.x) {
-        const long long m = m0 + threadIdx.x;
-        bool keep = false;
-        int bx = 0, by = 0;
-        if (m < ncode) {
-            bx = (int)compact_bits((uint32_t)m);
-            by = (int)compact_bits((uint32_t)(m >> 1));
-            if (bx < gw && by < gh) {
-                const int e = mask[lay.moff[level] + (long long)by * gw + bx] ? 1 : 0;
-                keep = (e == want);
-            }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) warp_cnt[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < wid; ++w) off += warp_cnt[w];
-        int tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_cnt[w];
-        if (keep) out[base + off + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)by << 16) | (uint32_t)bx;
-        __syncthreads();
-        if (threadIdx.x == 0) base += tot;
-        __syncthreads();
+    if (threadIdx.x < 32) {                  // the earlier chunks' counts, summed by one warp
+        int b = 0;
+        for (int c = threadIdx.x; c < chunk; c += 32) b += chunk_cnt[list * max_chunks + c];
+        b = warp_reduce(b, OpSum());
+        if (threadIdx.x == 0) base = b;
     }
-    if (threadIdx.x == 0) counts[list] = base;
+    bool keep;
+    uint32_t code;
+    int rank, total;
+    compact_chunk(lay, mask, cl, chunk, keep, code, rank, total);   // its barrier publishes base
+    if (keep) lists[list_stride * list + base + rank] = code;
+    if (chunk == nchunk - 1 && threadIdx.x == 0) counts[list] = base + total;
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,12 +1305,26 @@ cudaError_t launch_expand(const Layout& lay, const T* S, double tau, const uint8
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lists, long long list_stride,
-                           int* counts, cudaStream_t st)
+int compact_chunks(const Layout& lay)
 {
-    const int nlists = lay.L + 1;
+    int gw = 1, gh = 1;
+    for (int l = 1; l <= lay.L; ++l) {
+        gw = std::max(gw, lay.gw[l]);
+        gh = std::max(gh, lay.gh[l]);
+    }
+    long long side = 1;
+    while (side < gw || side < gh) side <<= 1;
+    return (int)((side * side + 1023) / 1024);
+}
+
+cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lists, long long list_stride,
+                           int* counts, int* chunk_cnt, cudaStream_t st)
+{
+    const int nlists = lay.L + 1, maxc = compact_chunks(lay);
     COUNT_LAUNCH();
-    k_compact<<<nlists, 1024, 0, st>>>(lay, mask, lists, list_stride, counts);
+    k_compact_count<<<dim3(maxc, nlists), 1024, 0, st>>>(lay, mask, chunk_cnt, maxc);
+    COUNT_LAUNCH();
+    k_compact<<<dim3(maxc, nlists), 1024, 0, st>>>(lay, mask, lists, list_stride, chunk_cnt, maxc, counts);
     return cudaGetLastError();
 }
 

@@ -480,8 +480,9 @@ wam_status plan_tree(wam_ctx* c, const Layout& lay, const uint8_t* mask, uint8_t
     uint32_t* lists = nullptr;
     int* counts = nullptr;
     WST(ensure_t(c, B_LISTS, (size_t)stride * (L + 1), &lists));
-    WST(ensure_t(c, B_COUNTS, (size_t)(L + 1), &counts));
-    WCK(c, launch_compact(lay, mask, lists, stride, counts, st));
+    const int maxc = compact_chunks(lay);
+    WST(ensure_t(c, B_COUNTS, (size_t)(L + 1) * (1 + maxc), &counts));
+    WCK(c, launch_compact(lay, mask, lists, stride, counts, counts + (L + 1), st));
     std::vector<int> h(L + 1);
     WCK(c, cudaMemcpyAsync(h.data(), counts, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
     WCK(c, cudaStreamSynchronize(st));

@@ -66,8 +66,10 @@ cudaError_t launch_leafmap(const Layout& lay, const uint8_t* mask, uint8_t* leaf
 template <typename T>
 cudaError_t launch_expand(const Layout& lay, const T* S, double tau, const uint8_t* leaf_old, uint8_t* mask_new,
                           double* scratch, cudaStream_t st);
+// chunk_cnt: scratch of (L + 1) * compact_chunks(lay) ints
+int compact_chunks(const Layout& lay);
 cudaError_t launch_compact(const Layout& lay, const uint8_t* mask, uint32_t* lists, long long list_stride,
-                           int* counts, cudaStream_t st);
+                           int* counts, int* chunk_cnt, cudaStream_t st);
 cudaError_t launch_haar(const Layout& lay, const double* in, double* out, int inverse, double* tmp_a,
                         double* tmp_b, cudaStream_t st);
 // dterm of every ray in FP64 (out) and as float pairs (out2)
