@@ -236,23 +236,23 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
     if (b < g.B) {
         Ray<T> r;
         if (make_ray(g, v, b, r)) {
-            T acc[LM > 0 ? LM : 1][4];
+            // per expanded ancestor level, the ray's three Haar detail sums of the
+            // current block (lower minus upper half, left minus right, diagonal)
+            T hs[LM > 0 ? LM : 1], vs[LM > 0 ? LM : 1], ds[LM > 0 ? LM : 1];
             int cur[LM > 0 ? LM : 1];
 #pragma unroll
             for (int l = 0; l < LM; ++l) {
                 cur[l] = -1;
-                acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = T(0);
+                hs[l] = vs[l] = ds[l] = T(0);
             }
             T total = T(0), rs = T(0);
             const int L = LM;
             auto flush = [&](int li) {
                 if (cur[li] >= 0) {
-                    const T* a = acc[li];
                     const T s = T(1) / T(1 << (li + 1));
-                    rs += s * (fabs(a[0] + a[1] - a[2] - a[3]) + fabs(a[0] - a[1] + a[2] - a[3]) +
-                               fabs(a[0] - a[1] - a[2] + a[3]));
+                    rs += s * (fabs(hs[li]) + fabs(vs[li]) + fabs(ds[li]));
                 }
-                acc[li][0] = acc[li][1] = acc[li][2] = acc[li][3] = T(0);
+                hs[li] = vs[li] = ds[li] = T(0);
             };
             traverse(g, leaf, r, [&](int ix, int iy, int lam, int bx0, int by0, T c) {
                 total += c;
@@ -262,11 +262,10 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
                     if (l > lam) {
                         const int id = ((iy >> l) << 16) | (ix >> l);
                         if (id != cur[li]) { flush(li); cur[li] = id; }
-                        const int q = (((by0 >> li) & 1) << 1) | ((bx0 >> li) & 1);
-                        acc[li][0] += q == 0 ? c : T(0);
-                        acc[li][1] += q == 1 ? c : T(0);
-                        acc[li][2] += q == 2 ? c : T(0);
-                        acc[li][3] += q == 3 ? c : T(0);
+                        const bool yb = (by0 >> li) & 1, xb = (bx0 >> li) & 1;
+                        hs[li] += yb ? -c : c;
+                        vs[li] += xb ? -c : c;
+                        ds[li] += (yb != xb) ? -c : c;
                     }
                 }
             });
