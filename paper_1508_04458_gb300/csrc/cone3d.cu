@@ -795,6 +795,10 @@ cudaError_t launch_reduce_voxels3(const SegTable3& tab, const Layout3& lay, cons
 // ---------------------------------------------------------------------------
 constexpr int kMaxL3 = 5;
 
+// Z3: the 3-D tree (octant sums, a Walsh-Hadamard transform at each
+// block's end); else the per-slice 2-D tree (three signed detail sums per
+// level, as in 2-D)
+template <bool Z3>
 __global__ void __launch_bounds__(kFwdTPB)
 k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict__ part)
 {
@@ -804,37 +808,42 @@ k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict
     if (b < g.B) {
         Ray3 ray;
         if (make_ray3(g, v, r, b, ray)) {
-            const int L = lay.L, z3 = lay.z3;
-            float acc[kMaxL3][8];
+            const int L = lay.L, z3 = Z3 ? 1 : 0;
+            float acc[kMaxL3][Z3 ? 8 : 3];
             long long cur[kMaxL3];
 #pragma unroll
             for (int l = 0; l < kMaxL3; ++l) {
                 cur[l] = -1;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[l][k] = 0.0f;
+                for (int k = 0; k < (Z3 ? 8 : 3); ++k) acc[l][k] = 0.0f;
             }
             float total = 0.0f, rs = 0.0f;
             auto flush = [&](int li) {
                 if (cur[li] >= 0) {
-                    float w[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) w[k] = acc[li][k];
-#pragma unroll
-                    for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (!(i & h)) {
-                                const float u0 = w[i], u1 = w[i + h];
-                                w[i] = u0 + u1;
-                                w[i + h] = u0 - u1;
-                            }
                     float sa = 0.0f;
-                    const int nt = z3 ? 8 : 4;
-                    for (int t = 1; t < nt; ++t) sa += fabsf(w[t]);
+                    if (Z3) {
+                        float w[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) w[k] = acc[li][k];
+#pragma unroll
+                        for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                if (!(i & h)) {
+                                    const float u0 = w[i], u1 = w[i + h];
+                                    w[i] = u0 + u1;
+                                    w[i + h] = u0 - u1;
+                                }
+#pragma unroll
+                        for (int t = 1; t < 8; ++t) sa += fabsf(w[t]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) sa += fabsf(acc[li][t]);
+                    }
                     rs += (float)basis_scale(z3, li + 1) * sa;
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[li][k] = 0.0f;
+                for (int k = 0; k < (Z3 ? 8 : 3); ++k) acc[li][k] = 0.0f;
             };
             walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int lam, int bx0, int by0, int bz0, float c) {
                 total += c;
@@ -848,9 +857,17 @@ k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict
                             flush(li);
                             cur[li] = id;
                         }
-                        const int q = ((bx0 >> li) & 1) + 2 * ((by0 >> li) & 1) + (z3 ? 4 * ((bz0 >> li) & 1) : 0);
+                        if (Z3) {
+                            const int q = ((bx0 >> li) & 1) + 2 * ((by0 >> li) & 1) + 4 * ((bz0 >> li) & 1);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[li][k] += (q == k) ? c : 0.0f;
+                            for (int k = 0; k < 8; ++k) acc[li][k] += (q == k) ? c : 0.0f;
+                        } else {
+                            // Walsh-Hadamard rows 1..3 of the quadrant: x, y, x^y signs
+                            const bool xb = (bx0 >> li) & 1, yb = (by0 >> li) & 1;
+                            acc[li][0] += xb ? -c : c;
+                            acc[li][1] += yb ? -c : c;
+                            acc[li][2] += (xb != yb) ? -c : c;
+                        }
                     }
                 }
             });
@@ -869,7 +886,8 @@ cudaError_t launch_z03(const Geom3& g, const Layout3& lay, const uint8_t* leaf, 
     if (lay.L > kMaxL3) return cudaErrorInvalidValue;
     count_launch();
     dim3 grid(nb(g.B, kFwdTPB), g.R, g.V);
-    k_z03<<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
+    if (lay.z3) k_z03<true><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
+    else k_z03<false><<<grid, kFwdTPB, 0, st>>>(g, lay, leaf, part);
     return cudaGetLastError();
 }
 
