@@ -123,3 +123,22 @@ def test_all_counts_zero(full):
     assert rel <= 1e-4, rel
     np.testing.assert_allclose(hist, ref.cost, rtol=1e-4, atol=2e-5 * ref.cost[0])
     assert math.isfinite(float(ref.cost[-1]))
+
+
+@pytest.mark.parametrize("I0", [1e5, 1e7])
+def test_cost_cancellation_at_mu_zero(I0):
+    # at beta = 0 the projection is exactly 0 and q = I0, so the first cost
+    # entry isolates the per-ray cost terms d (log d - log I0) - d + I0: with
+    # d ~ Poisson(I0) their addends (~I0 |log|) cancel to order one per ray.
+    # The FP32 path must keep them to FP32 precision of the small result
+    # (float-float terms), i.e. far below the 1e-4 parity bound.
+    p = I.small_problem(48, 40, 36, 83, seed=75)
+    rng = np.random.default_rng(9)
+    d = rng.poisson(I0, p.d.size).astype(np.float32)
+    ref = am.idiv(d.astype(np.float64), I0, np.zeros(d.size))
+    assert ref < 2.0 * d.size                 # order one per ray: the cancellation is real
+    ctx = wam.Context(p.geom)
+    ctx.set_data(d, I0)
+    for kw in (dict(levels=0, n_iters=1, full_am=True), dict(levels=2, n_iters=1)):
+        _, hist, _, _ = ctx.reconstruct(**kw)
+        assert abs(hist[0] - ref) <= 1e-6 * ref, (kw, hist[0], ref)
