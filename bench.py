@@ -455,6 +455,47 @@ def run_batch32(args):
     print(json.dumps(line), flush=True)
 
 
+def run_autograd(args):
+    """The differentiation workload: a batch of 8 coefficient vectors on a
+    256x256 fan-beam bag (360 views x 512 bins, L = 4 Haar levels): the
+    I-divergence + l1 loss with its gradient for the whole batch, and 10
+    unrolled AM steps (full tree) differentiated with respect to beta^(0)."""
+    import torch
+    from paper_1508_04458_gb300 import inputs as I, wam
+    from paper_1508_04458_gb300.autograd import AMUnroll, IDivLoss, Operators
+    prob = I.problem_fan(256, 360, 512, 1e5, seed=I.SEED_BASE + 3)
+    L, B, steps = 4, 8, 10
+    ctx = wam.Context(prob.geom)
+    ctx.set_data(prob.d.astype(np.float32), prob.I0)
+    ops = Operators(ctx, L)
+    ops.setup(torch.from_numpy(prob.d.astype(np.float32).ravel()).cuda())
+    rng = np.random.default_rng(4)
+    N = prob.geom.nx * prob.geom.ny
+    nA = (prob.geom.nx >> L) * (prob.geom.ny >> L)
+    betas = np.zeros((B, N), np.float32)
+    betas[:, :nA] = 0.02 * (1 << L)
+    betas[:, nA:] = rng.normal(0.0, 1e-3, (B, N - nA))
+    bt = torch.tensor(betas, device="cuda", requires_grad=True)
+
+    def loss_grad():
+        bt.grad = None
+        IDivLoss.apply(bt, ops, 1.0).sum().backward()
+
+    def unrolled():
+        b0 = torch.tensor(betas[0], device="cuda", requires_grad=True)
+        IDivLoss.apply(AMUnroll.apply(b0, ops, steps), ops, 1.0).backward()
+
+    out = {}
+    for name, fn, items in (("loss_grad_batch8", loss_grad, B), ("unroll10_grad", unrolled, 1)):
+        for _ in range(max(2, args.warmup)):
+            fn()
+        (_, ms) = _timed(lambda: [fn() for _ in range(args.steps)])
+        out[name] = {"ms_per_call": ms / args.steps, "items_per_s": items * args.steps / (ms / 1e3)}
+    line = {"workload": "autograd: batch 8 x 256x256 fan beam (360 views x 512 bins), L=4 Haar, "
+                        "loss + l1 gradient; 10 unrolled AM steps with their gradient", **out}
+    print(json.dumps(line), flush=True)
+
+
 def run_cone256(args):
     """3-D circular cone beam 256x256x128 @1.5 mm, 900 views, 64 x 768,
     I0 5e4: plain AM and multiresolution AM (3-D Haar, L=3, expansions
@@ -516,9 +557,10 @@ def main():
     ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="batch32: skip the autotuner")
-    ap.add_argument("--workload", choices=("fan512", "batch32", "cone256"), default="fan512",
-                    help="fan512 (default): the benchmark line; batch32 / cone256: secondary "
-                         "measurements of the batched and 3-D cone-beam paths (one JSON line each)")
+    ap.add_argument("--workload", choices=("fan512", "batch32", "cone256", "autograd"), default="fan512",
+                    help="fan512 (default): the benchmark line; batch32 / cone256 / autograd: secondary "
+                         "measurements of the batched, 3-D cone-beam and differentiation paths "
+                         "(one JSON line each)")
     ap.add_argument("--profile-case", choices=("multires", "full"), default=None,
                     help="run two reconstructions (multires or plain AM) of a 256x256 fan-beam bag "
                          "(360 views x 512 bins) for kernel profiling, print nothing")
@@ -531,6 +573,9 @@ def main():
         return
     if args.workload == "cone256":
         run_cone256(args)
+        return
+    if args.workload == "autograd":
+        run_autograd(args)
         return
 
     world = _env_int("WORLD_SIZE", 1)
