@@ -287,39 +287,9 @@ __device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& 
 }
 
 // ---------------------------------------------------------------------------
-// closed-form chords through an axis-aligned block, in block-local
-// coordinates: (qx, qy) a point of the ray relative to the block centre,
-// (idx, idy) the reciprocal unit direction, (hx, hy) the half sizes.
+// closed-form chords through an axis-aligned block
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T block_chord(T qx, T qy, T idx, T idy, T hx, T hy)
-{
-    const T x0 = (-hx - qx) * idx, x1 = (hx - qx) * idx;
-    const T y0 = (-hy - qy) * idy, y1 = (hy - qy) * idy;
-    const T lo = fmax(fmin(x0, x1), fmin(y0, y1));
-    const T hi = fmin(fmax(x0, x1), fmax(y0, y1));
-    return fmax(hi - lo, T(0));
-}
-
-// Chords through the four children: c00 (y lo, x lo), c01 (y lo, x hi),
-// c10 (y hi, x lo), c11 (y hi, x hi).
-template <typename T>
-__device__ __forceinline__ void child_chords(T qx, T qy, T idx, T idy, T hx, T hy,
-                                             T& c00, T& c01, T& c10, T& c11)
-{
-    const T tx0 = (-hx - qx) * idx, tx1 = -qx * idx, tx2 = (hx - qx) * idx;
-    const T ty0 = (-hy - qy) * idy, ty1 = -qy * idy, ty2 = (hy - qy) * idy;
-    const T xl0 = fmin(tx0, tx1), xl1 = fmax(tx0, tx1);   // x-lo slab
-    const T xh0 = fmin(tx1, tx2), xh1 = fmax(tx1, tx2);   // x-hi slab
-    const T yl0 = fmin(ty0, ty1), yl1 = fmax(ty0, ty1);
-    const T yh0 = fmin(ty1, ty2), yh1 = fmax(ty1, ty2);
-    c00 = fmax(fmin(xl1, yl1) - fmax(xl0, yl0), T(0));
-    c01 = fmax(fmin(xh1, yl1) - fmax(xh0, yl0), T(0));
-    c10 = fmax(fmin(xl1, yh1) - fmax(xl0, yh0), T(0));
-    c11 = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
-}
-
-// Crossing-ordered form of the same chords.  Measured along the unit
+// Chords in crossing order.  Measured along the unit
 // direction from a point of the ray, the ray crosses the block's centre lines
 // x = cx at t = a and y = cy at t = b, and its faces at a -+ Ax (x) and
 // b -+ Ay (y), Ax = hx |1/dx|, Ay = hy |1/dy|, always in this order.  The
