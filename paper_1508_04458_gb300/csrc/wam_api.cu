@@ -2074,6 +2074,9 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
     wam_ctx* c0 = ctxs[0];
     if (sc->precision != 32) return fail(c0, WAM_ERR_ARG, "batched reconstruction runs in precision 32");
     if (sc->n_subsets > 1) return fail(c0, WAM_ERR_ARG, "batched reconstruction has no ordered subsets");
+    if (sc->nonneg != 0 && sc->nonneg != 1) return fail(c0, WAM_ERR_ARG, "nonneg must be 0 or 1");
+    if (sc->nonneg && !sc->full_am && sc->levels != 0)
+        return fail(c0, WAM_ERR_ARG, "nonneg applies to plain AM (full_am or levels = 0) only");
     if (sc->n_iters < 0 || sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c0, WAM_ERR_ARG, "bad schedule");
     for (int k = 0; k < sc->n_expand; ++k)
