@@ -491,23 +491,29 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                     acc[0] += q * ch;
                     if (WORK) evals += ch > 0.0f;
                 } else if (MODE == kBp3Quad) {
-                    // quadrants of the block within the slice's z slab
+                    // the split of the block within the slice's z slab from the
+                    // clamped centre-line crossings, as in 2-D: [lo, hi] the ray's
+                    // interval in block and slab, ca, cb its x and y centre-plane
+                    // crossings clamped to it; first-minus-second half differences
+                    // 2 ca - (lo + hi), 2 cb - (lo + hi), diagonal (hi - lo) - 2|ca - cb|
                     const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
-                    const float zl = zsl, zh = zsh;
-                    const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
-                    const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
-                    float w[4];   // index i + 2 j: i x half, j y half (0 first)
+                    const float lo = fmaxf(fmaxf(a - Ax, b - Ay), zsl);
+                    const float hi = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh), lo);
+                    const float ca = fminf(fmaxf(a, lo), hi), cb = fminf(fmaxf(b, lo), hi);
+                    const float sm = lo + hi;
+                    if (WORK) {
+                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
 #pragma unroll
-                    for (int j = 0; j < 2; ++j)
+                        for (int j = 0; j < 2; ++j)
 #pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            w[i + 2 * j] = fmaxf(fminf(fminf(xh[i], yh[j]), zh) - fmaxf(fmaxf(xl[i], yl[j]), zl),
-                                                 0.0f);
-                    if (WORK) evals += (w[0] > 0.0f) + (w[1] > 0.0f) + (w[2] > 0.0f) + (w[3] > 0.0f);
-                    // Walsh-Hadamard over (x, y): t = 1 x, 2 y, 3 xy; + on the lower halves
-                    const float s1 = w[0] + w[1], s2 = w[2] + w[3], d1 = w[0] - w[1], d2 = w[2] - w[3];
-                    acc[0] += q * (s1 + s2);
-                    const float W[3] = {flipf(d1 + d2, T.z), flipf(s1 - s2, T.w), flipf(flipf(d1 - d2, T.z), T.w)};
+                            for (int i = 0; i < 2; ++i)
+                                evals += fminf(fminf(xh[i], yh[j]), zsh) - fmaxf(fmaxf(xl[i], yl[j]), zsl) > 0.0f;
+                    }
+                    acc[0] += q * (hi - lo);
+                    // + on the lower halves: t = 1 x, 2 y, 3 xy
+                    const float W[3] = {flipf(fmaf(2.0f, ca, -sm), T.z), flipf(fmaf(2.0f, cb, -sm), T.w),
+                                        flipf(flipf(fmaf(-2.0f, fabsf(ca - cb), hi - lo), T.z), T.w)};
 #pragma unroll
                     for (int t = 0; t < 3; ++t) {
                         const float ph = q * W[t];
