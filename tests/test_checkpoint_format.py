@@ -58,3 +58,18 @@ def test_truncation_is_rejected():
     for n in (10, 100, len(buf) - 1):
         with pytest.raises(ck.CheckpointError):
             ck.parse(buf[:n])
+
+
+def test_version_and_nonneg_field():
+    buf, beta, masks, hist = _example()
+    # the nonnegativity flag is the 22nd integer field
+    b = bytearray(buf[:-4])
+    struct.pack_into("<q", b, 16 + 8 * 21, 1)
+    b += struct.pack("<I", zlib.crc32(bytes(b)) & 0xFFFFFFFF)
+    assert ck.parse(bytes(b))["nonneg"] == 1
+    # an older layout (version 1) is refused, CRC intact
+    old = bytearray(buf[:-4])
+    struct.pack_into("<I", old, 8, 1)
+    old += struct.pack("<I", zlib.crc32(bytes(old)) & 0xFFFFFFFF)
+    with pytest.raises(ck.CheckpointError):
+        ck.parse(bytes(old))
