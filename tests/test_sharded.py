@@ -131,3 +131,53 @@ def test_view_blocks():
     s = sharded.shard_geometry(g, 180, 90)
     assert s.n_views == 90 and math.isclose(s.angle0, 180 * 2 * math.pi / 720)
     assert math.isclose(s.angle_span / s.n_views, g.angle_span / g.n_views)
+
+
+class FailingSteps(OracleSteps):
+    """A rank whose forward step fails at its third call (a host-side fault)."""
+
+    calls = 0
+
+    def forward(self, masks, mu):
+        FailingSteps.calls += 1
+        if FailingSteps.calls == 3:
+            raise RuntimeError("injected step failure")
+        return super().forward(masks, mu)
+
+
+def _worker_fail(rank, world, port, out):
+    import datetime
+    import time
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    p = _problem()
+    v0, n = sharded.view_block(p.geom.n_views, world, rank)
+    cls = FailingSteps if rank == 1 else OracleSteps
+    steps = cls(sharded.shard_geometry(p.geom, v0, n), sharded.shard_rows(p.d, p.geom, v0, n), p.I0, L)
+    t0 = time.monotonic()
+    try:
+        sharded.reconstruct_sharded(steps, J, EXPAND_AT, TAUS)
+        outcome = "finished"
+    except Exception as e:   # the failure as each rank sees it
+        outcome = type(e).__name__ + ": " + str(e)[:200]
+    with open(out % rank, "w") as f:
+        f.write("%s\n%.1f\n" % (outcome, time.monotonic() - t0))
+    if rank == 1:
+        os._exit(0)          # the failed rank leaves without its remaining collectives
+    dist.destroy_process_group()
+
+
+def test_a_failing_rank_ends_the_others_collective_with_an_error(tmp_path):
+    # rank 1's third forward raises and the rank leaves; rank 0 learns of it
+    # from its next all-reduce, which fails (peer gone, or the 10 s process-
+    # group timeout) instead of waiting forever
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "rank%d.txt")
+    mp.spawn(_worker_fail, args=(2, _free_port(), out), nprocs=2, join=True)
+    r0 = open(out % 0).read().split("\n")
+    r1 = open(out % 1).read().split("\n")
+    assert r1[0].startswith("RuntimeError: injected step failure")
+    assert r0[0] != "finished", r0
+    assert float(r0[1]) < 60.0
