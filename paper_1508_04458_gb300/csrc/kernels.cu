@@ -660,10 +660,8 @@ __device__ __forceinline__ T group_sum(T x)
 // group of G lanes per coefficient: coefficient 4 i + k of item i is pixel k
 // of a quad, or (k = 0) the approximation and (k = 1..3) detail type k of a
 // block; the lanes split the item's view-chunk partials, a fixed butterfly
-// adds them, and lane 0 applies the update.  G = 8 when the items are few
-// (coarse trees, whose items carry many view chunks), else 1.
-// Lanes per coefficient of a segment: 8 when its items carry many view
-// chunks (the chunk sums split over the lanes, then a fixed butterfly), else 1.
+// adds them, and lane 0 applies the update.  G is chosen per segment: 8 when
+// its items carry 8 or more view chunks (coarse levels), else 1.
 __host__ __device__ __forceinline__ int upd_lanes(const Segment& S) { return S.n_chunks >= 8 ? 8 : 1; }
 // Threads of a segment in the update grid: 4 coefficients per item, its lanes
 // each, padded to whole warps (a warp never spans two segments).
