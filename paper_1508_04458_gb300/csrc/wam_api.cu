@@ -347,8 +347,9 @@ struct ListInfo {
     int quad = 0;
 };
 
-// Split every list into view ranges so that the grid is about one full wave
-// of 256-thread CTAs (8 per SM) with similar work (chord evaluations) each.
+// Split every list into view ranges so that the grid holds about
+// back_ctas_per_sm 256-thread CTAs per SM (a tuning value, default 32) with
+// similar work (chord evaluations) each.
 template <typename T>
 wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTable* tab, T** part_out, int nv = 0)
 {
