@@ -116,3 +116,38 @@ def test_monotone_decrease_3d_modes(mode):
     a = am.wavelet_am3d(H, p.d, p.I0, 16, 16, 8, 0, 4)
     b = am.plain_am(H, p.d, p.I0, 4)
     np.testing.assert_allclose(a.beta, b.beta, rtol=1e-12, atol=1e-15)
+
+
+def test_analytic_3d_bag_integrals_against_point_sampling():
+    # the cone-beam data's closed-form integrals (ray/ellipsoid, ray/box,
+    # ray/cylinder-rod intervals, painter order on the ray) against midpoint
+    # sampling of the painter-ordered 3-D phantom along random segments
+    rng = np.random.default_rng(22)
+    shapes = I.phantom_bag3d(8, 60.0, 40.0, n_min=8, n_max=12)
+    n_rays, h, length = 40, 0.004, 200.0
+    P = rng.uniform(-30, 30, (n_rays, 3))
+    D = rng.normal(size=(n_rays, 3))
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    seg = np.concatenate([P - 0.5 * length * D, P + 0.5 * length * D], axis=1)
+    got = I.painter_line_integrals_3d(shapes, seg)
+    t = (np.arange(int(length / h)) + 0.5) * h
+    bound = 2 * len(shapes) * h * 1.0 + 1e-9
+    for k in range(n_rays):
+        X, Y, Z = (seg[k, i] + t * D[k, i] for i in range(3))
+        val = np.zeros_like(t)
+        for sh in shapes:
+            px, py, pz = X - sh.cx, Y - sh.cy, Z - sh.cz
+            if sh.kind == "rod":
+                w = sh.axis
+                pa = px * w[0] + py * w[1] + pz * w[2]
+                inside = (px * px + py * py + pz * pz - pa * pa < sh.a * sh.a) & (np.abs(pa) < sh.c)
+            else:
+                c, s = math.cos(sh.psi), math.sin(sh.psi)
+                rx, ry = c * px + s * py, -s * px + c * py
+                if sh.kind == "ellipsoid":
+                    inside = (rx / sh.a) ** 2 + (ry / sh.b) ** 2 + (pz / sh.c) ** 2 < 1.0
+                else:
+                    inside = (np.abs(rx) < sh.a) & (np.abs(ry) < sh.b) & (np.abs(pz) < sh.c)
+            val[inside] = sh.mu
+        assert abs(got[k] - val.sum() * h) <= bound, (k, got[k], val.sum() * h)
+    assert np.count_nonzero(got) > n_rays // 2
