@@ -151,3 +151,48 @@ def test_analytic_3d_bag_integrals_against_point_sampling():
             val[inside] = sh.mu
         assert abs(got[k] - val.sum() * h) <= bound, (k, got[k], val.sum() * h)
     assert np.count_nonzero(got) > n_rays // 2
+
+
+@pytest.mark.parametrize("vox", [(15, 4, 9), (3, 16, 2)])
+def test_cone_hot_voxel_shadow_placement(vox):
+    # The cone-beam scan convention, pinned without the oracle's own ray code:
+    # the source at SOD e in the plane z = 0, the flat detector through
+    # -(SDD - SOD) e spanned by u = (-sin, cos, 0) and z.  By similar triangles
+    # a point with a = <P, e>, w = <P, u> and height z meets the detector at
+    # (u, v) = SDD (w, z) / (SOD - a).  One hot voxel off centre in x, y and z:
+    # at view 0 and a quarter turn later, the rays (row, bin) that cross it are
+    # exactly those whose detector point lies inside the convex hull of its
+    # eight projected corners.  A detector at -SDD, a flipped row or bin axis,
+    # or a half-pitch shift of the row or bin centres moves this set.
+    from scipy.spatial import Delaunay
+    ix, iy, iz = vox
+    nx, ny, nz, sod, sdd = 20, 20, 12, 50.0, 120.0
+    g = I.Geometry(kind=I.CONE3D_FLAT_CIRCULAR, nx=nx, ny=ny, nz=nz, n_views=4, angle0=0.0,
+                   angle_span=2 * math.pi, n_bins=401, n_rows=201, bin_pitch=0.5, row_pitch=0.5,
+                   sod=sod, sdd=sdd)
+    vol = np.zeros((nz, ny, nx))
+    vol[iz, iy, ix] = 1.0
+    proj = (smx.system_matrix(g) @ vol.ravel()).reshape(4, g.n_rows, g.n_bins)
+    x0, y0, z0 = -0.5 * nx + ix, -0.5 * ny + iy, -0.5 * nz + iz
+    corners = [(x0 + i, y0 + j, z0 + k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    ub = (np.arange(g.n_bins) - 0.5 * (g.n_bins - 1)) * g.bin_pitch
+    vr = (np.arange(g.n_rows) - 0.5 * (g.n_rows - 1)) * g.row_pitch
+    V, U = np.meshgrid(vr, ub, indexing="ij")
+    pts = np.stack([U.ravel(), V.ravel()], 1)
+    for k in (0, 1):                                   # theta = 0 and pi/2
+        th = k * math.pi / 2
+        c, s = math.cos(th), math.sin(th)
+        shadow = []
+        for x, y, z in corners:
+            a, w = x * c + y * s, -x * s + y * c
+            shadow.append((sdd * w / (sod - a), sdd * z / (sod - a)))
+        shadow = np.array(shadow)
+        hull = Delaunay(shadow)
+        cen = shadow.mean(axis=0)
+        # shrink / grow the hull about its centre to keep rays on its edge out
+        inside = hull.find_simplex(cen + (pts - cen) / (1 - 1e-6)) >= 0
+        near = hull.find_simplex(cen + (pts - cen) / (1 + 1e-6)) >= 0
+        got = proj[k].ravel() > 0
+        assert inside.sum() >= 9
+        assert np.all(got[inside]), k
+        assert not np.any(got & ~near), k
