@@ -351,11 +351,11 @@ wam_status wam_phi_split_project(wam_ctx* ctx, int levels, const float* gbar, co
 #define WAM_STATIC_SCRATCH_BYTES (8u << 20)
 
 /* H^T s like wam_backproject, for callers that cannot allocate device memory:
- * code that runs inside a CUDA stream capture (where cudaMalloc is not
- * allowed), or a host application that hands out all device memory from its
- * own fixed pool at start-up and forbids later allocations.  The paper has no
- * counterpart to this call; it is a deployment convenience.
- *   g    scan geometry (as for wam_create); no context is needed
+ * a host application that reserves all of its device memory in a fixed pool
+ * at start-up and forbids any later cudaMalloc (a serving process with a hard
+ * memory budget, or a plug-in whose host owns the device allocator).  The
+ * paper has no counterpart to this call; it is a deployment convenience.
+ *   g    scan geometry (as for wam_create; 2-D kinds only); no context is needed
  *   s    device [n_views * n_bins] float sinogram, caller-owned
  *   out  device [nx * ny] float image, caller-owned
  * The per-view table and the partial sums live in one static device array of
@@ -364,14 +364,15 @@ wam_status wam_phi_split_project(wam_ctx* ctx, int levels, const float* gbar, co
  * 256) plus 4 * nx * ny * (number of view ranges) bytes of it; a geometry that
  * needs more is rejected with WAM_ERR_ARG (at most about 1.9 Mpixel images).
  * Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating
- * library routine is called.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device
- * share the array and it keeps the last call's contents (every entry a call
- * reads is written by that call first): calls that overlap on the GPU, on
- * different streams or threads, race and must be serialised by the caller.
- * Errors: WAM_ERR_ARG (bad geometry or null pointer, scratch too small),
- * WAM_ERR_CUDA. */
+ * library routine is called, and no host memory is copied to the device (the
+ * view table is computed by a kernel).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents (every entry a
+ * call reads is written by that call first): calls that overlap on the GPU,
+ * on different streams or threads, race and must be serialised by the
+ * caller.  Errors: WAM_ERR_ARG (a geometry wam_create would reject, a
+ * cone-beam geometry, a null pointer, scratch too small), WAM_ERR_CUDA. */
 wam_status wam_backproject_static(const wam_geometry* g, const float* s, float* out, void* stream);
 
 /* ---- measurement ---------------------------------------------------------- */

@@ -515,7 +515,11 @@ wam_status compute_z0(wam_ctx* c, const Geom<T>& g, const Layout& lay, const uin
     return WAM_OK;
 }
 
-wam_status check_geometry(const wam_geometry* g, std::string* why)
+}  // namespace
+
+// Shared with the non-allocating back-projector (wam_static.cu), so both entry
+// points accept the same 2-D geometries.
+wam_status wam::check_geometry(const wam_geometry* g, std::string* why)
 {
     if (!g) { *why = "geometry is NULL"; return WAM_ERR_ARG; }
     if (g->kind == WAM_CONE3D_FLAT_CIRCULAR) {
@@ -552,6 +556,8 @@ wam_status check_geometry(const wam_geometry* g, std::string* why)
     }
     return WAM_OK;
 }
+
+namespace {
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 

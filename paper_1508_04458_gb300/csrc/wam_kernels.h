@@ -1,9 +1,16 @@
 // Host-side launchers of the libwam kernels (internal).
 #pragma once
 
+#include "../../include/wam.h"
 #include "wam_internal.cuh"
 
+#include <string>
+
 namespace wam {
+
+// WAM_OK for a geometry wam_create accepts, else WAM_ERR_ARG with the reason
+// in *why (wam_api.cu).
+wam_status check_geometry(const wam_geometry* g, std::string* why);
 
 // The per-ray cost constant d (log d - log I0) - d as the forward of type T
 // reads it: FP64 for T = double; for T = float a pair (hi, lo) of floats

@@ -9,7 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
-#include <vector>
+#include <string>
 
 namespace {
 
@@ -38,20 +38,28 @@ wam_status scratch_address(int dev, float** out)
     return WAM_OK;
 }
 
+// The per-view cos/sin table, written on the device into the scratch: the
+// angle in FP64 exactly as the context path forms it (angle0 + k * span / V),
+// its cosine and sine in FP64, each rounded once to float.
+__global__ void k_static_views(float* __restrict__ cs, int V, double angle0, double step)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= V) return;
+    const double th = angle0 + k * step;
+    double sn, c;
+    sincos(th, &sn, &c);
+    cs[2 * k] = (float)c;
+    cs[2 * k + 1] = (float)sn;
+}
+
 }  // namespace
 
 extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float* s, float* out, void* stream)
 {
     using namespace wam;
     if (!w || !s || !out) return WAM_ERR_ARG;
-    if ((w->kind != WAM_PARALLEL2D && w->kind != WAM_FAN2D_FLAT) || w->nx <= 0 || w->ny <= 0 ||
-        w->n_views <= 0 || w->n_bins <= 0 || w->nz > 1 || w->n_rows > 1 || !(w->vx > 0) || !(w->vy > 0) ||
-        !(w->bin_pitch > 0) || w->nx > 65536 || w->ny > 65536)
-        return WAM_ERR_ARG;
-    if (w->kind == WAM_FAN2D_FLAT) {
-        const double r = 0.5 * std::hypot(w->nx * w->vx, w->ny * w->vy);
-        if (!(w->sod > r) || !(w->sdd - w->sod > r)) return WAM_ERR_ARG;
-    }
+    std::string why;
+    if (check_geometry(w, &why) != WAM_OK || w->kind == WAM_CONE3D_FLAT_CIRCULAR) return WAM_ERR_ARG;
     const long long N = (long long)w->nx * w->ny;
     const int V = w->n_views;
 
@@ -79,8 +87,12 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
     sg.n_items = (int)N;
     sg.items = nullptr;
     sg.gw = w->nx;
-    sg.n_chunks = (V + vpc - 1) / vpc;
-    sg.vpc = (V + sg.n_chunks - 1) / sg.n_chunks;
+    // at most V / (view lanes) ranges, each a whole number of view lanes long
+    // (capped at V), so that the CTA's warps get equal view counts
+    const int chunks = std::max(1, std::min((V + vpc - 1) / vpc, std::max(1, V / kViewLanes)));
+    sg.vpc = (V + chunks - 1) / chunks;
+    sg.vpc = std::min(V, (sg.vpc + kViewLanes - 1) / kViewLanes * kViewLanes);
+    sg.n_chunks = (V + sg.vpc - 1) / sg.vpc;
     sg.tiles = (int)((N + kItemsPerCta - 1) / kItemsPerCta);
     sg.cta_begin = 0;
     sg.item_begin = 0;
@@ -100,18 +112,11 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
     float* cs = base;
     float* part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(base) + cs_bytes);
 
-    std::vector<float> hcs(2 * (size_t)V);
-    for (int k = 0; k < V; ++k) {
-        const double th = w->angle0 + k * (w->angle_span / V);
-        hcs[2 * k] = (float)std::cos(th);
-        hcs[2 * k + 1] = (float)std::sin(th);
-    }
     cudaStream_t cst = static_cast<cudaStream_t>(stream);
-    // pageable source: the copy is staged before this call returns
-    if (cudaMemcpyAsync(cs, hcs.data(), hcs.size() * sizeof(float), cudaMemcpyHostToDevice, cst) != cudaSuccess) {
-        cudaGetLastError();
-        return WAM_ERR_CUDA;
-    }
+    // the view table is written on the device: no host-to-device copy
+    count_launch();
+    k_static_views<<<(V + 127) / 128, 128, 0, cst>>>(cs, V, w->angle0, w->angle_span / V);
+    if (cudaGetLastError() != cudaSuccess) return WAM_ERR_CUDA;
 
     Geom<float> g;
     g.kind = w->kind;

@@ -1,7 +1,9 @@
 """wam_backproject_static: the back-projection for callers that cannot allocate
-device memory (inside a stream capture, or under a fixed start-up memory
-pool).  It must give the same H^T s as wam_backproject, on consecutive calls
-that reuse its fixed scratch.  This file is collected last on purpose."""
+device memory (an application that reserves all of its device memory in a
+fixed pool at start-up and forbids later cudaMalloc calls).  It must give the
+same H^T s as wam_backproject, on consecutive calls that reuse its fixed
+scratch, and a call must leave the device's free memory unchanged.  This file
+is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -40,9 +42,17 @@ def test_static_backprojection_matches_allocating_one(kind, nx, ny, V, B):
         ref = torch.empty(nx * ny, dtype=torch.float32, device="cuda")
         out = torch.full((nx * ny,), float("nan"), dtype=torch.float32, device="cuda")
         ctx.check(wam.wam_backproject(ctx.h, wam.ptr(s), wam.ptr(ref), st))
+        torch.cuda.synchronize()
+        # the first call on a device may load the library's module, which
+        # places the static array; from the second call on nothing may change
+        free0 = torch.cuda.mem_get_info()[0]
+        torch_bytes0 = torch.cuda.memory_allocated()
         rc = wam.wam_backproject_static(ctypes.byref(gs), wam.ptr(s), wam.ptr(out), st)
         assert rc == wam.WAM_OK
         torch.cuda.synchronize()
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0, "device memory changed"
+            assert torch.cuda.memory_allocated() == torch_bytes0
         assert torch.isfinite(out).all()
         _check(out, ref, "call %d" % call)
     ctx.close()
@@ -58,3 +68,18 @@ def test_static_backprojection_rejects_oversize():
     out = torch.zeros(2048 * 2048, dtype=torch.float32, device="cuda")
     rc = wam.wam_backproject_static(ctypes.byref(gs), wam.ptr(s), wam.ptr(out), wam.current_stream())
     assert rc == wam.WAM_ERR_ARG
+
+
+def test_static_backprojection_rejects_what_wam_create_rejects():
+    # the same geometry check as wam_create: a non-finite angle, a cone-beam
+    # geometry, a fan source inside the image
+    s = torch.zeros(16 * 32, dtype=torch.float32, device="cuda")
+    out = torch.zeros(32 * 32, dtype=torch.float32, device="cuda")
+    base = I.small_problem(32, 32, 16, 32, kind=I.FAN2D_FLAT, seed=3).geom
+    bad = [dict(angle0=float("nan")), dict(angle_span=float("inf")), dict(sod=5.0),
+           dict(kind=I.CONE3D_FLAT_CIRCULAR, nz=4, n_rows=2, vz=1.0, row_pitch=1.0)]
+    import dataclasses
+    for kw in bad:
+        gs = wam.geometry(dataclasses.replace(base, **kw))
+        rc = wam.wam_backproject_static(ctypes.byref(gs), wam.ptr(s), wam.ptr(out), wam.current_stream())
+        assert rc == wam.WAM_ERR_ARG, kw
