@@ -168,15 +168,36 @@ def _row_abs_max(Ps: sp.spmatrix) -> float:
     return float(np.max(np.asarray(abs(Ps).sum(axis=1)).ravel()))
 
 
-def am_step(Ps: sp.csc_matrix, b_s, beta_s, d, I0):
-    """One AM iteration on the active columns Ps of Phi; returns (Delta, cost, Z0)."""
-    p = Ps @ beta_s
+@dataclasses.dataclass
+class ActiveColumns:
+    """The columns of Phi active in one tree epoch, with the quantities of
+    Algorithm 1 that depend on them alone: Z0 (Eq. 1.61, a max over rays of
+    the row sums of |phi|) and the positive and negative parts of phi whose
+    products with qhat give bhat+ and bhat- (Eq. 1.10).  Built once per
+    epoch; every iteration of the epoch reuses them (the same numbers an
+    iteration would form from scratch)."""
+    P: sp.csc_matrix
+    Pplus: sp.csc_matrix
+    Pminus: sp.csc_matrix
+    Z0: float
+
+
+def active_columns(Ps: sp.spmatrix) -> ActiveColumns:
+    Ps = sp.csc_matrix(Ps)
+    return ActiveColumns(Ps, Ps.maximum(0).tocsc(), Ps.minimum(0).tocsc(), _row_abs_max(Ps))
+
+
+def am_step(A, b_s, beta_s, d, I0):
+    """One AM iteration on the active columns A (an ActiveColumns, or a
+    matrix of Phi's active columns); returns (Delta, cost, Z0)."""
+    if not isinstance(A, ActiveColumns):
+        A = active_columns(A)
+    p = A.P @ beta_s
     q = np.broadcast_to(np.asarray(I0, dtype=np.float64), p.shape) * np.exp(-p)
     cost = idiv(d, I0, p)
-    Z0 = _row_abs_max(Ps)
-    bp = Ps.maximum(0).T @ q
-    bm = Ps.minimum(0).T @ q
-    return am_root(b_s, bp, bm, Z0), cost, Z0
+    bp = A.Pplus.T @ q
+    bm = A.Pminus.T @ q
+    return am_root(b_s, bp, bm, A.Z0), cost, A.Z0
 
 
 def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
@@ -194,10 +215,12 @@ def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
     tree = [t.copy() for t in tree0] if tree0 is not None else empty_tree(nx, ny, L)
     costs, z0s, trees, nact = [], [], [], []
     sched = dict(zip(expand_at, taus))
+    A = None
     for j in range(n_iter):
         act = np.tile(active_mask(tree, nx, ny, L), nz)
-        Ps = Phi[:, act]
-        delta, cost, Z0 = am_step(Ps, b[act], beta[act], d, I0)
+        if A is None:                                    # a new tree epoch
+            A = active_columns(Phi[:, act])
+        delta, cost, Z0 = am_step(A, b[act], beta[act], d, I0)
         costs.append(cost)
         z0s.append(Z0)
         nact.append(int(act.sum()))
@@ -206,6 +229,7 @@ def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
             mu = (Omega @ beta).reshape(nz, ny, nx)
             tree = expand(tree, mu.sum(axis=0), sched[j + 1])
             trees.append([t.copy() for t in tree])
+            A = None
     costs.append(idiv(d, I0, Phi @ beta))
     mu = (Omega @ beta).reshape(nz, ny, nx) if nz > 1 else (Omega @ beta).reshape(ny, nx)
     return AMResult(beta, mu, np.array(costs), np.array(z0s), tree, trees, np.array(nact))
@@ -223,10 +247,11 @@ def plain_am(H: sp.spmatrix, d, I0, n_iter: int, shape=None, nonneg: bool = Fals
     d = np.asarray(d, dtype=np.float64).ravel()
     Hc = H.tocsc()
     b = Hc.T @ d
+    A = active_columns(Hc)
     mu = np.zeros(H.shape[1])
     costs, z0s = [], []
     for _ in range(n_iter):
-        delta, cost, Z0 = am_step(Hc, b, mu, d, I0)
+        delta, cost, Z0 = am_step(A, b, mu, d, I0)
         costs.append(cost)
         z0s.append(Z0)
         mu += delta
@@ -352,9 +377,12 @@ def wavelet_am3d(H: sp.spmatrix, d, I0, nx: int, ny: int, nz: int, L: int, n_ite
     tree = empty_tree3d(nx, ny, nz, L)
     costs, z0s, trees, nact = [], [], [], []
     sched = dict(zip(expand_at, taus))
+    A = None
     for j in range(n_iter):
         act = active_mask3d(tree, nx, ny, nz, L)
-        delta, cost, Z0 = am_step(Phi[:, act], b[act], beta[act], d, I0)
+        if A is None:                                    # a new tree epoch
+            A = active_columns(Phi[:, act])
+        delta, cost, Z0 = am_step(A, b[act], beta[act], d, I0)
         costs.append(cost)
         z0s.append(Z0)
         nact.append(int(act.sum()))
@@ -362,6 +390,7 @@ def wavelet_am3d(H: sp.spmatrix, d, I0, nx: int, ny: int, nz: int, L: int, n_ite
         if (j + 1) in sched:
             tree = expand3d(tree, (Omega @ beta).reshape(nz, ny, nx), sched[j + 1])
             trees.append([t.copy() for t in tree])
+            A = None
     costs.append(idiv(d, I0, Phi @ beta))
     return AMResult(beta, (Omega @ beta).reshape(nz, ny, nx), np.array(costs), np.array(z0s), tree, trees,
                     np.array(nact))
