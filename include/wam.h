@@ -299,6 +299,23 @@ wam_status wam_update(wam_ctx* ctx, int levels, const unsigned char* masks, cons
                       const double* bplus, const double* bminus, const double* z0, double clamp,
                       double* beta, void* stream);
 
+/* a6 per coefficient, exactly as wam_reconstruct computes it: Delta(z) =
+ * beta~(z) - betahat(z), the zero of Eq. 1.9 (the step of Algorithm 1's inner
+ * loop) from b(z), bhat+(z) >= 0 >= bhat-(z), clamped to |Z0 Delta| <= clamp
+ * (<= 0 means 30).  precision 32: the FP32 reconstruction's root, i.e.
+ * bhat+- rounded to float (they are FP32 sums there), the root in FP32 on
+ * inputs divided by max(|b|, bhat+, -bhat-), times an FP32 1/Z0; precision
+ * 64: the FP64 root.  No context is needed.
+ *   n         number of coefficients (0 does nothing)
+ *   b, bplus, bminus   device [n] FP64
+ *   z0        Z0 > 0 (Eq. 1.61)
+ *   delta     device [n] FP64 output
+ *   at_clamp  device [n] int output (1 where the step sits at the clamp), or NULL
+ * Errors: WAM_ERR_ARG (null pointer, precision not 32/64, Z0 not positive
+ * and finite), WAM_ERR_CUDA. */
+wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus, double z0,
+                        double clamp, int precision, double* delta, int* at_clamp, void* stream);
+
 /* a7, Results section: one tree expansion.  Every pixel with S > tau * max S
  * (compared in FP64; tau < 0 selects every pixel) expands its current leaf
  * (read from mask_in) by one level.  S [nx*ny]; mask_in, mask_out distinct
@@ -408,10 +425,11 @@ enum {
 };
 
 /* A mode other than WAM_PROFILE_OFF resets the statistics; from then on every
- * kernel launch of wam_reconstruct is bracketed with CUDA events on its
- * stream (ALL, TIME; two event records per launch) and/or counts its work
- * (ALL, WORK: ray-cell intersections with a nonzero chord); WAM_PROFILE_OFF
- * stops.  Errors: WAM_ERR_ARG for an unknown mode. */
+ * kernel launch of wam_reconstruct (and the projections and back-projections
+ * of wam_project_coef, wam_backproject_coef and wam_idiv_grad) is bracketed
+ * with CUDA events on its stream (ALL, TIME; two event records per launch)
+ * and/or counts its work (ALL, WORK: ray-cell intersections with a nonzero
+ * chord); WAM_PROFILE_OFF stops.  Errors: WAM_ERR_ARG for an unknown mode. */
 wam_status wam_profile(wam_ctx* ctx, int enable);
 
 /* Statistics gathered since wam_profile(ctx, 1); synchronises the stream

@@ -1398,6 +1398,33 @@ __global__ void k_update_dense(Layout lay, const uint8_t* __restrict__ mask, con
     beta[z] += am_delta(bvec[z], bp[z], bm ? bm[z] : 0.0, *z0p, clamp, hit);
 }
 
+// a6 per coefficient on flat arrays, with the same root the reconstruction's
+// k_update<T> applies (am_step: FP32 on normalised inputs for T = float, FP64
+// for T = double): the step-level view of the AM update.
+template <typename T>
+__global__ void k_am_delta(long long n, const double* __restrict__ bvec, const double* __restrict__ bp,
+                           const double* __restrict__ bm, double z0, double clamp, double* __restrict__ delta,
+                           int* __restrict__ at_clamp)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool hit = false;
+    delta[i] = am_step(bvec[i], (T)bp[i], (T)bm[i], z0, 1.0f / (float)z0, clamp, hit);
+    if (at_clamp) at_clamp[i] = hit ? 1 : 0;
+}
+
+cudaError_t launch_am_delta(int precision, long long n, const double* b, const double* bp, const double* bm,
+                            double z0, double clamp, double* delta, int* at_clamp, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    COUNT_LAUNCH();
+    if (precision == 32)
+        k_am_delta<float><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, z0, clamp, delta, at_clamp);
+    else
+        k_am_delta<double><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, z0, clamp, delta, at_clamp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const double* b, const double* bp,
                                 const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st)
 {

@@ -87,6 +87,11 @@ cudaError_t launch_convert(const A* x, B* y, long long n, cudaStream_t st);
 cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const double* b, const double* bp,
                                 const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st);
 
+// Eq. 1.9's step per coefficient on flat arrays with the reconstruction's own
+// root (precision 32: bp, bm rounded to float and the FP32 root; 64: FP64)
+cudaError_t launch_am_delta(int precision, long long n, const double* b, const double* bp, const double* bm,
+                            double z0, double clamp, double* delta, int* at_clamp, cudaStream_t st);
+
 unsigned long long kernel_launches();
 // kernels run by graph replays (counted once when captured)
 void add_launches(unsigned long long n);

@@ -92,6 +92,7 @@ _PROTOS = {
     "wam_z0": (_S, [_P, _I, _P, _P, _P]),
     "wam_update": (_S, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "wam_expand": (_S, [_P, _I, _P, _D, _P, _P, _P]),
+    "wam_am_delta": (_S, [ctypes.c_longlong, _P, _P, _P, _D, _D, _I, _P, _P, _P]),
     "wam_project_coef": (_S, [_P, _I, _P, _P, _P]),
     "wam_backproject_coef": (_S, [_P, _I, _P, _P, _P]),
     "wam_idiv_grad": (_S, [_P, _I, _P, ctypes.c_float, _P, _P, _P, _P]),
