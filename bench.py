@@ -116,6 +116,22 @@ class ClockSampler:
 # the oracle on a bounded sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
+def sample_scan(problem, view_stride: int):
+    """Every view_stride-th view of the workload's scan: its geometry and counts."""
+    from paper_1508_04458_gb300 import inputs as I
+    g = problem.geom
+    nv = g.n_views // view_stride
+    sub = I.Geometry(**{**g.__dict__, "n_views": nv,
+                        "angle_span": g.angle_span * (nv * view_stride) / g.n_views})
+    return sub, np.ascontiguousarray(problem.d[::view_stride][:nv])
+
+
+def sample_schedule(n_iters: int):
+    """The benchmark's expansions at the same fractions of a shorter run."""
+    exp_at = tuple(sorted(set(max(1, round(n_iters * e / N_ITERS)) for e in EXPAND_AT)))
+    return exp_at, TAU[: len(exp_at)]
+
+
 def oracle_sample(problem, view_stride: int, n_iters: int):
     """Time the FP64 oracle's Algorithm 1 on every view_stride-th view of the
     workload (full image; the schedule scaled to n_iters, i.e. expansions
@@ -125,20 +141,39 @@ def oracle_sample(problem, view_stride: int, n_iters: int):
     workload."""
     from oracle import am
     from oracle import system_matrix as smx
-    from paper_1508_04458_gb300 import inputs as I
 
     g = problem.geom
-    sub = I.Geometry(**{**g.__dict__, "n_views": g.n_views // view_stride,
-                        "angle_span": g.angle_span * ((g.n_views // view_stride) * view_stride) / g.n_views})
-    d = problem.d[::view_stride][: sub.n_views]
+    sub, d = sample_scan(problem, view_stride)
     t0 = time.perf_counter()
     H = smx.system_matrix(sub)
-    exp_at = tuple(sorted(set(max(1, round(n_iters * e / N_ITERS)) for e in EXPAND_AT)))
-    r = am.wavelet_am(H, d, problem.I0, g.nx, g.ny, L_LEVELS, n_iters,
-                      expand_at=exp_at, taus=TAU[: len(exp_at)])
+    exp_at, taus = sample_schedule(n_iters)
+    r = am.wavelet_am(H, d, problem.I0, g.nx, g.ny, L_LEVELS, n_iters, expand_at=exp_at, taus=taus)
     dt = time.perf_counter() - t0
     rate = n_iters / dt / view_stride
     return rate, dt, r
+
+
+def gpu_error_vs_oracle(problem, view_stride: int, n_iters: int, ref):
+    """The GPU path (FP32, through the C-ABI) on the oracle's own sample scan
+    and schedule, against the oracle's result: relative L2 error of mu, the
+    largest relative deviation of the I-divergence history, and whether the
+    final trees agree."""
+    from paper_1508_04458_gb300 import wam
+    sub, d = sample_scan(problem, view_stride)
+    g = problem.geom
+    exp_at, taus = sample_schedule(n_iters)
+    ctx = wam.Context(sub)
+    ctx.set_data(d.astype(np.float32), problem.I0)
+    mu, hist, masks, st = ctx.reconstruct(L_LEVELS, n_iters, exp_at, taus, precision=32)
+    ctx.close()
+    ref_masks = np.concatenate([ref.tree[l - 1].astype(np.uint8).ravel() for l in range(L_LEVELS, 0, -1)])
+    mu_rel = float(np.linalg.norm(mu.astype(np.float64) - ref.mu.ravel()) / np.linalg.norm(ref.mu))
+    cost_rel = float(np.max(np.abs(hist - ref.cost) / np.abs(ref.cost)))
+    return {"mu_rel_l2": mu_rel, "idiv_max_rel": cost_rel, "trees_equal": bool(np.array_equal(masks, ref_masks)),
+            "status": int(st), "bound": {"mu_rel_l2": 1e-4, "idiv_max_rel": 1e-4},
+            "sample": "the cpu_baseline sample: every %dth view (%d of %d), full %dx%d image, %d iterations, "
+                      "expansions after %s" % (view_stride, sub.n_views, g.n_views, g.nx, g.ny, n_iters,
+                                               list(exp_at))}
 
 
 def run_reference(args, problem, world):
@@ -171,6 +206,40 @@ def run_reference(args, problem, world):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+
+def roofline_of(stats, sms: int, what: str = "ray-rectangle"):
+    """ALU roofline of the dominant kernel class (forward or back-projector):
+    its counted intersections per launch over its event-timed launch duration,
+    against SMs x 128 FP32 lanes x the maximum SM clock / K_MIN."""
+    dom = max(("forward", "backproject"), key=lambda k: stats[k]["ms"])
+    sd = stats[dom]
+    clk_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    peak = sms * 128 * clk_mhz * 1e6 / K_MIN / 1e9            # G intersections / s
+    per_launch_work = sd["work"] / max(1, sd["launches"])
+    per_launch_ms = sd["ms"] / max(1, sd["launches"])
+    achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+            "unit": "G %s intersections/s" % what, "frac": achieved / peak if peak else None,
+            "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS sm_max_mhz) / %d "
+                          "instructions per intersection" % (sms, clk_mhz, K_MIN),
+            "work_per_launch": per_launch_work, "ms_per_launch": per_launch_ms}
+
+
+def profiled(ctx, fn):
+    """Per-kernel-class times (events only) and work (counters only, a second
+    run) of one call of fn on ctx."""
+    from paper_1508_04458_gb300 import wam
+    ctx.profile(mode=wam.WAM_PROFILE_TIME)
+    fn()
+    st = ctx.stats()
+    ctx.profile(mode=wam.WAM_PROFILE_WORK)
+    fn()
+    w = ctx.stats()
+    ctx.profile(False)
+    for k in st:
+        st[k]["work"] = w[k]["work"]
+    return st
+
 
 def run_wam(args, problem, world, rank, local_rank):
     import torch
@@ -340,15 +409,11 @@ def run_wam(args, problem, world, rank, local_rank):
         e2e["value"] = world * args.steps * N_ITERS / float(t.item())
 
     # ---- roofline of the dominant kernel (ALU bound: ray-rectangle intersections)
-    dom = max(("forward", "backproject"), key=lambda k: stats[k]["ms"])
-    sd = stats[dom]
     peaks = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = sms * 128 * clk_mhz * 1e6 / K_MIN / 1e9            # G intersections / s
-    per_launch_work = sd["work"] / max(1, sd["launches"])
-    per_launch_ms = sd["ms"] / max(1, sd["launches"])
-    achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    roofline = roofline_of(stats, sms)
+    dom = roofline["kernel"][2:]
+    per_launch_ms = roofline["ms_per_launch"]
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -357,12 +422,7 @@ def run_wam(args, problem, world, rank, local_rank):
             traffic = tj.get(dom, {}).get("dram_bytes_per_launch")
         except Exception:
             traffic = None
-    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
-                "unit": "G ray-rectangle intersections/s", "frac": achieved / peak if peak else None,
-                "traffic": traffic,
-                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (MEASURED_PEAKS sm_max_mhz) / %d "
-                              "instructions per intersection" % (sms, clk_mhz, K_MIN),
-                "work_per_launch": per_launch_work, "ms_per_launch": per_launch_ms}
+    roofline["traffic"] = traffic
     if traffic and per_launch_ms > 0:
         # the HBM side of the same kernel: its DRAM bytes per launch (ncu, cold replay) over its live
         # launch time, against the measured copy rate -- small, since the working set lives in L2
@@ -373,13 +433,24 @@ def run_wam(args, problem, world, rank, local_rank):
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
+    err_vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu:
         stride, iters = 15, 25
-        rate, dt, _ = oracle_sample(problem, stride, iters)
+        rate, dt, ref = oracle_sample(problem, stride, iters)
         cpu = {"value": rate, "unit": "AM iters/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "every %dth view (%d of %d), full 512x512 image, %d iterations, expansions at the "
                          "same fractions of the run, %.1f s; rate scaled by %d" % (stride, g.n_views // stride,
                                                                                  g.n_views, iters, dt, stride)}
+        err_vs_oracle = gpu_error_vs_oracle(problem, stride, iters, ref)
+
+    # ---- the other workloads, as compact sub-records (rank 0, one GPU)
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        for name, fn in (("cone256", sub_cone256), ("batch32", sub_batch32), ("autograd", sub_autograd)):
+            with ClockSampler(local_rank) as ck:
+                rec = fn(args, quick=True)
+            rec["clocks"] = ck.summary()
+            extra[name] = rec
 
     if rank == 0:
         line = {
@@ -389,7 +460,7 @@ def run_wam(args, problem, world, rank, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64"),
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "cpu_baseline": cpu, "err_vs_oracle": err_vs_oracle,
             "multires": {"final_idiv": float(hist_mr[-1]), "ms_per_iter": dev_ms_max / args.steps / N_ITERS,
                          "time_to_target_ms": ttt_mr, "iters_to_target": j_hit,
                          "idiv_after_%d" % TTT_MAX_ITERS: float(hist_long[-1]),
@@ -404,6 +475,7 @@ def run_wam(args, problem, world, rank, local_rank):
             "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "work": v["work"]}
                         for k, v in stats.items()},
             "wall_s_timed": wall,
+            **extra,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -420,7 +492,7 @@ def _timed(fn, stream=None):
     return out, a.elapsed_time(b)
 
 
-def run_batch32(args):
+def sub_batch32(args, quick: bool = False):
     """32 seeded bags of uneven size (256^2..768^2, 360..1440 views,
     512..1536 bins, I0 1e4..1e5), 100 multiresolution iterations each:
     batched (one CUDA graph per tree epoch) against the per-bag loop."""
@@ -440,22 +512,38 @@ def run_batch32(args):
             tuned[autotune.geometry_class(c.geom)] = autotune.tune(c, cache=cache)
     loop = lambda: [c.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, device_out=True) for c in ctxs]
     batch = lambda: wam.reconstruct_batch(ctxs, L_LEVELS, N_ITERS, EXPAND_AT, TAU, use_graph=True)
-    for _ in range(max(1, args.warmup)):
+    steps = 2 if quick else args.steps
+    for _ in range(1 if quick else max(1, args.warmup)):
         loop()
         batch()
-    t_loop = min(_timed(loop)[1] for _ in range(args.steps))
-    t_batch = min(_timed(batch)[1] for _ in range(args.steps))
+    t_loop = min(_timed(loop)[1] for _ in range(steps))
+    t_batch = min(_timed(batch)[1] for _ in range(steps))
+    # kernel classes of one pass over the bags (the same kernels the batch runs)
+    agg = None
+    for c in ctxs:
+        st = profiled(c, lambda: c.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, device_out=True))
+        if agg is None:
+            agg = st
+        else:
+            for k in agg:
+                for f in ("ms", "launches", "work"):
+                    agg[k][f] += st[k][f]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     iters = 32 * N_ITERS
-    line = {"workload": "batch32: 32 fan-beam bags 256..768 px, 360..1440 views, 512..1536 bins, "
-                        "L=4, 100 iterations", "unit": "AM iters/s (all bags)",
-            "batched_graph": iters / (t_batch / 1e3), "per_bag_loop": iters / (t_loop / 1e3),
-            "ms_batched": t_batch, "ms_loop": t_loop, "speedup": t_loop / t_batch,
-            "autotuned_back_ctas_per_sm": tuned, "pixels": int(sum(p.geom.nx * p.geom.ny for p in bags)),
-            "rays": int(sum(p.geom.n_views * p.geom.n_bins for p in bags))}
-    print(json.dumps(line), flush=True)
+    out = {"workload": "batch32: 32 fan-beam bags 256..768 px, 360..1440 views, 512..1536 bins, "
+                       "L=4, 100 iterations", "unit": "AM iters/s (all bags)",
+           "iters_per_s": iters / (t_batch / 1e3), "batched_graph": iters / (t_batch / 1e3),
+           "per_bag_loop": iters / (t_loop / 1e3),
+           "ms_batched": t_batch, "ms_loop": t_loop, "speedup": t_loop / t_batch,
+           "roofline": roofline_of(agg, sms),
+           "autotuned_back_ctas_per_sm": tuned, "pixels": int(sum(p.geom.nx * p.geom.ny for p in bags)),
+           "rays": int(sum(p.geom.n_views * p.geom.n_bins for p in bags))}
+    for c in ctxs:
+        c.close()
+    return out
 
 
-def run_autograd(args):
+def sub_autograd(args, quick: bool = False):
     """The differentiation workload: a batch of 8 coefficient vectors on a
     256x256 fan-beam bag (360 views x 512 bins, L = 4 Haar levels): the
     I-divergence + l1 loss with its gradient for the whole batch, and 10
@@ -486,17 +574,23 @@ def run_autograd(args):
         IDivLoss.apply(AMUnroll.apply(b0, ops, steps), ops, 1.0).backward()
 
     out = {}
+    reps = 3 if quick else args.steps
     for name, fn, items in (("loss_grad_batch8", loss_grad, B), ("unroll10_grad", unrolled, 1)):
-        for _ in range(max(2, args.warmup)):
+        for _ in range(2 if quick else max(2, args.warmup)):
             fn()
-        (_, ms) = _timed(lambda: [fn() for _ in range(args.steps)])
-        out[name] = {"ms_per_call": ms / args.steps, "items_per_s": items * args.steps / (ms / 1e3)}
-    line = {"workload": "autograd: batch 8 x 256x256 fan beam (360 views x 512 bins), L=4 Haar, "
-                        "loss + l1 gradient; 10 unrolled AM steps with their gradient", **out}
-    print(json.dumps(line), flush=True)
+        (_, ms) = _timed(lambda: [fn() for _ in range(reps)])
+        out[name] = {"ms_per_call": ms / reps, "items_per_s": items * reps / (ms / 1e3)}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    st = profiled(ctx, loss_grad)
+    rec = {"workload": "autograd: batch 8 x 256x256 fan beam (360 views x 512 bins), L=4 Haar, "
+                       "loss + l1 gradient; 10 unrolled AM steps with their gradient",
+           "unit": "items/s", "iters_per_s": out["loss_grad_batch8"]["items_per_s"], **out,
+           "roofline": roofline_of(st, sms)}
+    ctx.close()
+    return rec
 
 
-def run_cone256(args):
+def sub_cone256(args, quick: bool = False):
     """3-D circular cone beam 256x256x128 @1.5 mm, 900 views, 64 x 768,
     I0 5e4: plain AM and multiresolution AM (3-D Haar, L=3, expansions
     after 8, 16, 32) and the per-slice 2-D Haar mode, 60 iterations."""
@@ -506,30 +600,27 @@ def run_cone256(args):
     ctx = wam.Context(p.geom)
     ctx.set_data(torch.from_numpy(p.d.astype(np.float32).ravel()).cuda(), p.I0)
     J, ea, tau = 60, (8, 16, 32), (0.1, 0.03, -1.0)
+    modes = [("multires_3d_haar", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=3)),
+             ("full_am", dict(levels=0, n_iters=J, full_am=True)),
+             ("multires_per_slice", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=2, zsum=True))]
+    if quick:
+        modes = modes[:2]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     res = {}
-    for name, kw in (("full_am", dict(levels=0, n_iters=J, full_am=True)),
-                     ("multires_3d_haar", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=3)),
-                     ("multires_per_slice", dict(levels=3, n_iters=J, expand_at=ea, tau=tau, dims=2, zsum=True))):
+    for name, kw in modes:
         ctx.reconstruct(**kw, device_out=True)
         (mu, hist, _, st), ms = _timed(lambda: ctx.reconstruct(**kw, device_out=True))
         # the kernel split (events only) and the work (counters only) in two more runs
-        ctx.profile(mode=wam.WAM_PROFILE_TIME)
-        ctx.reconstruct(**kw, device_out=True)
-        k = ctx.stats()
-        ctx.profile(mode=wam.WAM_PROFILE_WORK)
-        ctx.reconstruct(**kw, device_out=True)
-        kw_work = ctx.stats()
-        ctx.profile(False)
-        for n in k:
-            k[n]["work"] = kw_work[n]["work"]
+        k = profiled(ctx, lambda: ctx.reconstruct(**kw, device_out=True))
         h = hist.cpu().numpy()
         res[name] = {"ms": ms, "iters_per_s": J / (ms / 1e3), "status": st, "idiv0": float(h[0]),
-                     "idiv_final": float(h[-1]),
+                     "idiv_final": float(h[-1]), "roofline": roofline_of(k, sms, "ray-cell"),
                      "kernels": {n: {"ms": round(v["ms"], 2), "launches": v["launches"], "work": v["work"]}
                                  for n, v in k.items()}}
-    line = {"workload": "cone256: 256x256x128 @1.5 mm, 900 views x 64 rows x 768 bins, I0 5e4, 60 iterations",
-            "unit": "AM iters/s", **res}
-    print(json.dumps(line), flush=True)
+    ctx.close()
+    return {"workload": "cone256: 256x256x128 @1.5 mm, 900 views x 64 rows x 768 bins, I0 5e4, 60 iterations",
+            "unit": "AM iters/s", "iters_per_s": res["multires_3d_haar"]["iters_per_s"],
+            "roofline": res["multires_3d_haar"]["roofline"], **res}
 
 
 def profile_case(full: bool):
@@ -557,6 +648,8 @@ def main():
     ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="batch32: skip the autotuner")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the cone256 / batch32 / autograd sub-records of the default line")
     ap.add_argument("--workload", choices=("fan512", "batch32", "cone256", "autograd"), default="fan512",
                     help="fan512 (default): the benchmark line; batch32 / cone256 / autograd: secondary "
                          "measurements of the batched, 3-D cone-beam and differentiation paths "
@@ -568,14 +661,9 @@ def main():
     if args.profile_case:
         profile_case(args.profile_case == "full")
         return
-    if args.workload == "batch32":
-        run_batch32(args)
-        return
-    if args.workload == "cone256":
-        run_cone256(args)
-        return
-    if args.workload == "autograd":
-        run_autograd(args)
+    subs = {"batch32": sub_batch32, "cone256": sub_cone256, "autograd": sub_autograd}
+    if args.workload in subs:
+        print(json.dumps(subs[args.workload](args)), flush=True)
         return
 
     world = _env_int("WORLD_SIZE", 1)

@@ -1993,6 +1993,20 @@ wam_status wam_update(wam_ctx* c, int levels, const unsigned char* masks, const 
     return WAM_OK;
 }
 
+wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus, double z0,
+                        double clamp, int precision, double* delta, int* at_clamp, void* stream)
+{
+    if (n < 0 || (n > 0 && (!b || !bplus || !bminus || !delta))) return WAM_ERR_ARG;
+    if (precision != 32 && precision != 64) return WAM_ERR_ARG;
+    if (!(z0 > 0) || !std::isfinite(z0) || std::isnan(clamp)) return WAM_ERR_ARG;
+    if (launch_am_delta(precision, n, b, bplus, bminus, z0, clamp > 0 ? clamp : 30.0, delta, at_clamp,
+                        as_stream(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return WAM_ERR_CUDA;
+    }
+    return WAM_OK;
+}
+
 wam_status wam_expand(wam_ctx* c, int levels, const float* S, double tau, const unsigned char* mask_in,
                       unsigned char* mask_out, void* stream)
 {
@@ -2253,7 +2267,11 @@ wam_status sino_to_coef(wam_ctx* c, const Layout& lay, const float* s, double** 
     WST(ensure_t(c, B_TMPA, (size_t)c->N, &ta));
     WST(ensure_t(c, B_TMPB, (size_t)c->N, &tb));
     WST(ensure_t(c, B_GCOEF, (size_t)c->N, coef));
-    WCK(c, launch_backproject(g, tab, s, dirt, part, nullptr, st));
+    {
+        PROF(WAM_K_BACKPROJECT);
+        WCK(c, launch_backproject(g, tab, s, dirt, part, work_ptr(c, WAM_K_BACKPROJECT), st));
+    }
+    PROF(WAM_K_TREE);
     WCK(c, (launch_reduce_pixels<float, double>(tab, c->g.nx, c->N, part, gimg, st)));
     WCK(c, launch_haar(lay, gimg, *coef, 0, ta, tb, st));
     return WAM_OK;
@@ -2278,8 +2296,9 @@ wam_status wam_project_coef(wam_ctx* c, int levels, const float* beta, float* p,
         WST(make_geom<float>(c, &g));
         float* mut = nullptr;
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
+        PROF(WAM_K_FORWARD);
         WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr,
-                                     nullptr, st));
+                                     work_ptr(c, WAM_K_FORWARD), st));
         return WAM_OK;
     } catch (...) {
         return fail(c, WAM_ERR_OOM, "host allocation failed");
@@ -2327,10 +2346,12 @@ wam_status wam_idiv_grad(wam_ctx* c, int levels, const float* beta, float lambda
         WST(ensure_t(c, B_GRES, (size_t)c->M, &res));
         float* mut = nullptr;
         WST(ensure_t(c, B_MUT, pad_elems(c), &mut));
-        WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, static_cast<const float*>(c->buf[B_D].p),
-                                     dterm_buf<float>(c), static_cast<const float*>(c->buf[B_I0].p), qhat, nullptr,
-                                     res, cpart, nullptr,
-                                     st));
+        {
+            PROF(WAM_K_FORWARD);
+            WCK(c, launch_forward<float>(g, mu, mut, nullptr, 0, static_cast<const float*>(c->buf[B_D].p),
+                                         dterm_buf<float>(c), static_cast<const float*>(c->buf[B_I0].p), qhat,
+                                         nullptr, res, cpart, work_ptr(c, WAM_K_FORWARD), st));
+        }
         double* coef = nullptr;
         WST(sino_to_coef(c, lay, res, &coef, st));
         const int nl1 = (int)((c->N + 255) / 256);
