@@ -207,6 +207,46 @@ def run_reference(args, problem, world):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+def difference_image(problem, pair, save_dir=None):
+    """The analogue of the paper's Figs 2-4 (Results section): the images of
+    plain AM after k iterations and of multiresolution AM after the j
+    iterations it needs to reach the same I-divergence, and their difference
+    (multires minus plain).  Summaries over the true phantom's structure:
+    the edge band (pixels whose 3x3 neighbourhood in the rasterised phantom
+    spans more than 0.005 /mm) and the flat regions (the other pixels inside
+    the objects), the difference's RMS in each, and each image's mean
+    gradient magnitude in the edge band (a sharper edge has a larger one)."""
+    k, j, mu_plain, mu_mr = pair
+    g = problem.geom
+    a = mu_plain.reshape(g.ny, g.nx).astype(np.float64)
+    m = mu_mr.reshape(g.ny, g.nx).astype(np.float64)
+    t = np.asarray(problem.mu_true, dtype=np.float64).reshape(g.ny, g.nx)
+    pad = np.pad(t, 1, mode="edge")
+    win = np.stack([pad[dy:dy + g.ny, dx:dx + g.nx] for dy in range(3) for dx in range(3)])
+    edge = (win.max(axis=0) - win.min(axis=0)) > 0.005
+    flat = (~edge) & (t > 0.005)
+    diff = m - a
+
+    def grad(x):
+        gy, gx = np.gradient(x)
+        return np.hypot(gx, gy)
+
+    rms = lambda x, sel: float(np.sqrt(np.mean(x[sel] ** 2))) if sel.any() else None
+    out = {"plain_am_iters": k, "multires_iters": j, "edge_pixels": int(edge.sum()),
+           "flat_pixels": int(flat.sum()), "rms_diff_edge": rms(diff, edge), "rms_diff_flat": rms(diff, flat),
+           "rms_err_edge": {"plain_am": rms(a - t, edge), "multires": rms(m - t, edge)},
+           "rms_err_flat": {"plain_am": rms(a - t, flat), "multires": rms(m - t, flat)},
+           "mean_grad_edge": {"plain_am": float(grad(a)[edge].mean()), "multires": float(grad(m)[edge].mean()),
+                              "phantom": float(grad(t)[edge].mean())}}
+    if save_dir:
+        os.makedirs(save_dir, exist_ok=True)
+        np.savez_compressed(os.path.join(save_dir, "equal_objective_images.npz"), plain_am=a.astype(np.float32),
+                            multires=m.astype(np.float32), difference=diff.astype(np.float32),
+                            edge=edge, flat=flat)
+        out["saved"] = "equal_objective_images.npz"
+    return out
+
+
 def roofline_of(stats, sms: int, what: str = "ray-rectangle"):
     """ALU roofline of the dominant kernel class (forward or back-projector):
     its counted intersections per launch over its event-timed launch duration,
@@ -340,15 +380,18 @@ def run_wam(args, problem, world, rank, local_rank):
     # objective-versus-time comparison: time for each method to reach plain
     # AM's cost after k iterations (+1e-3), k = 10, 20, 50, 100
     curve = []
+    equal_pair = None
     for k in (10, 20, 50, 100):
         tgt = float(hist_f[k]) * (1.0 + 1e-3)
-        _, t_full = timed(lambda: step(n_iters=k, full=True, levels=0))
+        (mu_k, _, _, _), t_full = timed(lambda: step(n_iters=k, full=True, levels=0))
         jh = np.nonzero(hist_long <= tgt)[0]
         t_mr = None
         if jh.size:
-            _, t_mr = timed(lambda: step(n_iters=int(jh[0])))
+            (mu_j, _, _, _), t_mr = timed(lambda: step(n_iters=int(jh[0])))
+            equal_pair = (k, int(jh[0]), mu_k.cpu().numpy(), mu_j.cpu().numpy())
         curve.append({"full_am_iters": k, "target_idiv": tgt, "full_am_ms": t_full,
                       "multires_iters": int(jh[0]) if jh.size else None, "multires_ms": t_mr})
+    difference = difference_image(problem, equal_pair, args.save_dir) if equal_pair else None
 
     # ---- ordered subsets of views (the Conclusion's combination with ordered
     # subsets): the same schedules with S interleaved view subsets, time to
@@ -469,6 +512,7 @@ def run_wam(args, problem, world, rank, local_rank):
                         "ms_per_iter": full_ms2 / N_ITERS, "time_to_target_ms": full_ms2},
             "target_idiv": target,
             "time_to_equal_objective": curve,
+            "difference_at_equal_objective": difference,
             "ordered_subsets": ordered,
             "projector": projector,
             "clamp_hits_per_reconstruction": int(work1["update"]["work"]),
@@ -623,12 +667,14 @@ def sub_cone256(args, quick: bool = False):
             "roofline": res["multires_3d_haar"]["roofline"], **res}
 
 
-def profile_case(full: bool):
-    """A small case of the same kernels: 256x256 bag, 360 views x 512 bins."""
+def profile_case(full: bool, n: int = 256):
+    """A case of the same kernels for kernel profiling: an n x n bag with
+    n * 1.40625 views x 2n bins (256: 360 x 512; 512: 720 x 1024, the
+    benchmark's own scan)."""
     import torch
     from paper_1508_04458_gb300 import inputs as I
     from paper_1508_04458_gb300 import wam
-    p = I.problem_fan(256, 360, 512, 1e5, seed=I.SEED_BASE + 3)
+    p = I.problem_fan(256, 360, 512, 1e5, seed=I.SEED_BASE + 3) if n == 256 else I.problem_fan512()
     ctx = wam.Context(p.geom)
     ctx.set_data(p.d.astype(np.float32), p.I0)
     for _ in range(2):
@@ -648,6 +694,8 @@ def main():
     ap.add_argument("--impl", choices=("wam", "reference"), default="wam")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="batch32: skip the autotuner")
+    ap.add_argument("--save-dir", default=None,
+                    help="write the equal-objective images (plain AM, multires, difference) here as .npz")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the cone256 / batch32 / autograd sub-records of the default line")
     ap.add_argument("--workload", choices=("fan512", "batch32", "cone256", "autograd"), default="fan512",
@@ -657,9 +705,11 @@ def main():
     ap.add_argument("--profile-case", choices=("multires", "full"), default=None,
                     help="run two reconstructions (multires or plain AM) of a 256x256 fan-beam bag "
                          "(360 views x 512 bins) for kernel profiling, print nothing")
+    ap.add_argument("--profile-n", type=int, choices=(256, 512), default=256,
+                    help="image side of --profile-case (512: the benchmark's own bag and scan)")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case == "full")
+        profile_case(args.profile_case == "full", args.profile_n)
         return
     subs = {"batch32": sub_batch32, "cone256": sub_cone256, "autograd": sub_autograd}
     if args.workload in subs:

@@ -117,6 +117,17 @@ typedef struct {
                                  exact minimiser over mu >= 0 and the cost still decreases at every
                                  iteration.  0 (default) = Algorithm 1 as stated, unconstrained.
                                  WAM_ERR_ARG with a Haar tree (levels > 0 and not full_am). */
+    double lambda;            /* >= 0.  0 (default): Algorithm 1 as stated (Eq. 1.1 unregularised).
+                                 > 0: the regularised problem of Eq. 1.1 with
+                                 lambda R(mu) = lambda * sum over the detail coefficients of |beta|
+                                 (the wavelet-domain l1 roughness penalty the paper's Summary names).
+                                 With the separable surrogate of Eq. 1.8 each detail coefficient's
+                                 problem stays one-dimensional and convex: its step is the root of
+                                 Eq. 1.9 with b + lambda or b - lambda, whichever lies on its own side
+                                 of beta = 0, else beta = 0 exactly; approximations are unpenalised.
+                                 idiv_hist then holds I(d || qhat) + lambda * sum |beta_detail|, which
+                                 decreases at every iteration.  2-D contexts with levels > 0 and no
+                                 ordered subsets (else WAM_ERR_ARG). */
 } wam_schedule;
 
 typedef struct wam_ctx wam_ctx;
@@ -203,11 +214,11 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
  * history I(d || qhat^(0..j)), the schedule it ran, the geometry, CRC-32
  * fingerprints of d and I0, and the back-projector tuning value; the file ends
  * with a CRC-32 of its contents and is written to "<path>.tmp" and renamed.
- * Format (little endian): "WAMCKPT1", u32 version 2, u32 0; 22 int64 (kind,
+ * Format (little endian): "WAMCKPT1", u32 version 3, u32 0; 22 int64 (kind,
  * nx, ny, nz, n_views, n_bins, n_rows, levels, dims, zsum_criterion,
  * precision, full_am, n_expand, iterations done, expansions done, N,
- * mask bytes, history length, crc(d), crc(I0), n_subsets, nonneg); 11 double (vx, vy, vz,
- * angle0, angle_span, bin_pitch, row_pitch, sod, sdd, dmax_clamp, tuning);
+ * mask bytes, history length, crc(d), crc(I0), n_subsets, nonneg); 12 double (vx, vy, vz,
+ * angle0, angle_span, bin_pitch, row_pitch, sod, sdd, dmax_clamp, tuning, lambda);
  * int64 expand_at[n_expand]; double tau[n_expand]; double beta[N];
  * u8 masks[mask bytes]; double history[iterations done + 1]; u32 crc.
  * Errors: WAM_ERR_STATE if no reconstruction has finished on ctx since its
@@ -221,11 +232,12 @@ wam_status wam_checkpoint(wam_ctx* ctx, const char* path);
  * The context's back-projector tuning is set to the checkpoint's.  Requires
  * data set (wam_set_data) equal to the checkpoint's (CRC-32 of d and I0) and
  * an equal geometry; the continuing schedule must have the same levels, dims,
- * zsum_criterion, precision, full_am, dmax_clamp, n_subsets and nonneg, n_iters >= j, and the
+ * zsum_criterion, precision, full_am, dmax_clamp, n_subsets, nonneg and lambda, n_iters >= j, and the
  * same first expansions (those applied so far) with no other expansion at or
  * before j, else that wam_reconstruct returns WAM_ERR_STATE and the loaded
  * state stays pending.  wam_set_data discards a pending state.
  * wam_reconstruct_batch refuses contexts with a pending state (WAM_ERR_STATE).
+ * Version 2 files (11 doubles, no lambda) are read as lambda = 0.
  * Errors: WAM_ERR_IO for an unreadable, truncated or corrupt file (bad magic,
  * version or CRC); WAM_ERR_STATE for no data or a geometry or data mismatch. */
 wam_status wam_resume(wam_ctx* ctx, const char* path);
@@ -305,16 +317,22 @@ wam_status wam_update(wam_ctx* ctx, int levels, const unsigned char* masks, cons
  * (<= 0 means 30).  precision 32: the FP32 reconstruction's root, i.e.
  * bhat+- rounded to float (they are FP32 sums there), the root in FP32 on
  * inputs divided by max(|b|, bhat+, -bhat-), times an FP32 1/Z0; precision
- * 64: the FP64 root.  No context is needed.
+ * 64: the FP64 root.  lambda > 0: the step of a detail coefficient under the
+ * L1 penalty of wam_schedule.lambda, from its current value beta (where the
+ * penalised minimiser is beta = 0 exactly, Delta = -beta).  No context is
+ * needed.
  *   n         number of coefficients (0 does nothing)
  *   b, bplus, bminus   device [n] FP64
+ *   beta      device [n] FP64 current values (read only when lambda > 0; may be NULL otherwise)
+ *   lambda    >= 0
  *   z0        Z0 > 0 (Eq. 1.61)
  *   delta     device [n] FP64 output
  *   at_clamp  device [n] int output (1 where the step sits at the clamp), or NULL
  * Errors: WAM_ERR_ARG (null pointer, precision not 32/64, Z0 not positive
- * and finite), WAM_ERR_CUDA. */
-wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus, double z0,
-                        double clamp, int precision, double* delta, int* at_clamp, void* stream);
+ * and finite, lambda negative or not finite), WAM_ERR_CUDA. */
+wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus,
+                        const double* beta, double lambda, double z0, double clamp, int precision, double* delta,
+                        int* at_clamp, void* stream);
 
 /* a7, Results section: one tree expansion.  Every pixel with S > tau * max S
  * (compared in FP64; tau < 0 selects every pixel) expands its current leaf

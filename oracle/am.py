@@ -100,6 +100,39 @@ def am_root(b, bp, bm, Z0: float, clamp: float = CLAMP) -> np.ndarray:
     return t / Z0
 
 
+def am_root_l1(b, bp, bm, Z0: float, beta_hat, lam, clamp: float = CLAMP) -> np.ndarray:
+    """Delta minimising the one-coefficient surrogate of Eq. 1.8 plus an L1
+    penalty lam |beta_hat + Delta| (Eq. 1.1 with R = the l1 norm of the detail
+    coefficients, the wavelet-domain roughness penalty the Summary names).
+
+    The surrogate's derivative in Delta is g(Delta) = b - bp exp(-Z0 Delta)
+    - bm exp(Z0 Delta) (Eq. 1.9), increasing; the penalised problem is convex
+    with a kink at Delta0 = -beta_hat, where beta becomes 0.  Its minimiser:
+      g(Delta) + lam = 0  (the root with b + lam) if that root lies beyond Delta0,
+      g(Delta) - lam = 0  (the root with b - lam) if that root lies before Delta0,
+      Delta0 otherwise (beta is set to 0).
+    The decision uses the unclamped roots; the result is then clamped to
+    |Z0 Delta| <= clamp (a step between 0 and the minimiser of a convex
+    function still lowers it).  lam = 0 gives am_root."""
+    b = np.asarray(b, dtype=np.float64)
+    lam = np.broadcast_to(np.asarray(lam, dtype=np.float64), b.shape)
+    beta_hat = np.broadcast_to(np.asarray(beta_hat, dtype=np.float64), b.shape)
+    up = am_root(b + lam, bp, bm, 1.0, np.inf)          # Z0 Delta for g = -lam
+    dn = am_root(b - lam, bp, bm, 1.0, np.inf)          # Z0 Delta for g = +lam
+    t0 = -Z0 * beta_hat
+    kink = ~(up > t0) & ~(dn < t0)
+    t = np.where(up > t0, up, np.where(dn < t0, dn, t0))
+    # at the kink beta becomes exactly 0 (unless the clamp stops the step short)
+    return np.where(kink & (np.abs(t0) <= clamp), -beta_hat, np.clip(t, -clamp, clamp) / Z0)
+
+
+def l1_details(beta, nx: int, ny: int, L: int, act=None) -> float:
+    """sum over the detail coefficients of |beta| (the penalty of am_root_l1)."""
+    _, typ, _, _ = haar.coefficient_info(nx, ny, L)
+    sel = typ >= 0
+    return float(np.sum(np.abs(np.asarray(beta)[sel])))
+
+
 # ---------------------------------------------------------------------------
 # the wavelet tree
 # ---------------------------------------------------------------------------
@@ -202,9 +235,15 @@ def am_step(A, b_s, beta_s, d, I0):
 
 def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
                expand_at: Sequence[int] = (), taus: Sequence[float] = (),
-               tree0: Optional[List[np.ndarray]] = None, nz: int = 1) -> AMResult:
+               tree0: Optional[List[np.ndarray]] = None, nz: int = 1, lam: float = 0.0) -> AMResult:
     """Algorithm 1 with the tree schedule; nz > 1 runs the per-slice 2-D Haar
-    mode (one tree shared by all slices, criterion summed over slices)."""
+    mode (one tree shared by all slices, criterion summed over slices).
+
+    lam > 0 (2-D only): the regularised problem of Eq. 1.1 with
+    lam R(mu) = lam * sum over the detail coefficients of |beta|; every detail
+    coefficient takes the penalised step am_root_l1, the approximations the
+    plain one, and the cost history holds I(d || qhat) + lam * sum |beta_det|,
+    which then decreases at every iteration."""
     d = np.asarray(d, dtype=np.float64).ravel()
     Om2 = haar.basis_matrix(nx, ny, L)
     Omega = sp.block_diag([Om2] * nz, format="csc") if nz > 1 else Om2
@@ -215,12 +254,26 @@ def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
     tree = [t.copy() for t in tree0] if tree0 is not None else empty_tree(nx, ny, L)
     costs, z0s, trees, nact = [], [], [], []
     sched = dict(zip(expand_at, taus))
+    if lam > 0 and nz > 1:
+        raise ValueError("the penalised step is defined for 2-D images")
+    _, typ, _, _ = haar.coefficient_info(nx, ny, L)
+    det = typ >= 0
+    pen = (lambda be: lam * float(np.sum(np.abs(be[det])))) if lam > 0 else (lambda be: 0.0)
     A = None
     for j in range(n_iter):
         act = np.tile(active_mask(tree, nx, ny, L), nz)
         if A is None:                                    # a new tree epoch
             A = active_columns(Phi[:, act])
-        delta, cost, Z0 = am_step(A, b[act], beta[act], d, I0)
+        if lam > 0:
+            p_ = A.P @ beta[act]
+            q_ = np.broadcast_to(np.asarray(I0, dtype=np.float64), p_.shape) * np.exp(-p_)
+            cost = idiv(d, I0, p_) + pen(beta)
+            Z0 = A.Z0
+            bp_, bm_ = A.Pplus.T @ q_, A.Pminus.T @ q_
+            delta = np.where(det[act], am_root_l1(b[act], bp_, bm_, Z0, beta[act], lam),
+                             am_root(b[act], bp_, bm_, Z0))
+        else:
+            delta, cost, Z0 = am_step(A, b[act], beta[act], d, I0)
         costs.append(cost)
         z0s.append(Z0)
         nact.append(int(act.sum()))
@@ -230,7 +283,7 @@ def wavelet_am(H: sp.spmatrix, d, I0, nx: int, ny: int, L: int, n_iter: int,
             tree = expand(tree, mu.sum(axis=0), sched[j + 1])
             trees.append([t.copy() for t in tree])
             A = None
-    costs.append(idiv(d, I0, Phi @ beta))
+    costs.append(idiv(d, I0, Phi @ beta) + pen(beta))
     mu = (Omega @ beta).reshape(nz, ny, nx) if nz > 1 else (Omega @ beta).reshape(ny, nx)
     return AMResult(beta, mu, np.array(costs), np.array(z0s), tree, trees, np.array(nact))
 

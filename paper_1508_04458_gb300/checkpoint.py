@@ -15,7 +15,7 @@ INT_FIELDS = ("kind", "nx", "ny", "nz", "n_views", "n_bins", "n_rows", "levels",
               "precision", "full_am", "n_expand", "iters_done", "expansions_done", "n_coef", "mask_bytes",
               "n_hist", "crc_d", "crc_I0", "n_subsets", "nonneg")
 DBL_FIELDS = ("vx", "vy", "vz", "angle0", "angle_span", "bin_pitch", "row_pitch", "sod", "sdd", "dmax_clamp",
-              "tuning")
+              "tuning", "lambda")
 
 
 class CheckpointError(ValueError):
@@ -31,16 +31,19 @@ def parse(buf: bytes) -> dict:
     if zlib.crc32(buf[:-4]) & 0xFFFFFFFF != crc:
         raise CheckpointError("CRC mismatch")
     version, _ = struct.unpack_from("<II", buf, 8)
-    if version != 2:
+    if version not in (2, 3):
         raise CheckpointError("unsupported version %d" % version)
+    dbl = DBL_FIELDS if version == 3 else DBL_FIELDS[:-1]     # version 2 has no lambda
     at = 16
-    head = 8 * (len(INT_FIELDS) + len(DBL_FIELDS))
+    head = 8 * (len(INT_FIELDS) + len(dbl))
     if at + head > len(buf) - 4:
         raise CheckpointError("header truncated")
     out = dict(zip(INT_FIELDS, struct.unpack_from("<%dq" % len(INT_FIELDS), buf, at)))
     at += 8 * len(INT_FIELDS)
-    out.update(zip(DBL_FIELDS, struct.unpack_from("<%dd" % len(DBL_FIELDS), buf, at)))
-    at += 8 * len(DBL_FIELDS)
+    out.update(zip(dbl, struct.unpack_from("<%dd" % len(dbl), buf, at)))
+    out.setdefault("lambda", 0.0)
+    out["version"] = version
+    at += 8 * len(dbl)
     ne, n, mb, nh = out["n_expand"], out["n_coef"], out["mask_bytes"], out["n_hist"]
     if min(ne, n, mb, nh) < 0 or nh != out["iters_done"] + 1:
         raise CheckpointError("inconsistent header")

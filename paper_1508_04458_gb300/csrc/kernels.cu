@@ -328,8 +328,9 @@ __device__ __forceinline__ double flip2(double x, double s1, double s2)
 }
 
 // dirtab[v][b] = (s/dx, -c/dy, 1/dx, 1/dy) of ray (v, b), c, s = cos, sin of
-// the view: with delta the ray's offset from a block centre along u, the
-// centre-line crossings are a = delta s/dx and b = -delta c/dy.
+// the view, the ray oriented so that dx >= 0: with delta the ray's offset
+// from a block centre along u, the centre-line crossings are a = delta s/dx
+// and b = -delta c/dy.
 // Item kinds of a back-projection segment.
 enum { kBpBlock = 0, kBpSplit = 1, kBpQuad = 2 };
 
@@ -373,24 +374,28 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
         const int bhi = min(g.B - 1, (int)floor(umax * ipitch + g.ucen + T(1e-3)));
         const T kappa = fan ? (g.sod - ac) * isdd : T(1);
         // ray offset from the block centre along u, linear in the bin
-        const T delta0 = (T(blo) * g.pitch + u0) * kappa - wc, dstep = g.pitch * kappa;
+        T delta = (T(blo) * g.pitch + u0) * kappa - wc;
+        const T dstep = g.pitch * kappa;
         const T* row = sino + (size_t)v * g.B;
         const typename Vec4<T>::type* drow = TABLE ? dirtab + (size_t)v * g.B : nullptr;
-        T fk = T(0);
 #pragma unroll 1
-        for (int bb = blo; bb <= bhi; ++bb, fk += T(1)) {
-            const T delta = fma(fk, dstep, delta0);
+        for (int bb = blo; bb <= bhi; ++bb, delta += dstep) {
             typename Vec4<T>::type dd;
             if (TABLE) {
                 dd = ld4(drow + bb);
             } else {
-                // no table: the same four numbers from the ray's direction
+                // no table: the same four numbers from the ray's direction,
+                // oriented so that dx >= 0 like the table's
                 const T ub = T(bb) * g.pitch + u0;
                 T dx = c, dy = s;
                 if (fan) {
                     const T rn = rsqrt_t<T>(g.sdd * g.sdd + ub * ub);
                     dx = (-g.sdd * c - ub * s) * rn;
                     dy = (-g.sdd * s + ub * c) * rn;
+                }
+                if (signbit(dx)) {
+                    dx = -dx;
+                    dy = -dy;
                 }
                 dd.z = safe_rcp(dx);
                 dd.w = safe_rcp(dy);
@@ -403,7 +408,7 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 // pixel basis: the four pixels' chords in physical order, select-free:
                 // pixel (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) sums
                 T cll, chl, clh, chh;
-                child_chords_phys(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
+                child_chords_phys_xpos(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
                 acc[0] += q * cll;
                 acc[1] += q * chl;
                 acc[2] += q * clh;
@@ -411,16 +416,18 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 if (WORK) evals += (cll > T(0)) + (chl > T(0)) + (clh > T(0)) + (chh > T(0));
             } else if (MODE == kBpSplit) {
                 // Haar split: the block chord and the three first-minus-second
-                // half differences along the travel direction (haar_split), the
-                // halves' physical order fixed by the direction's signs
+                // half differences along the travel direction (haar_split).
+                // The travel has dx >= 0, so its first x half is the lower one;
+                // along y the first half is the lower one when 1/dy > 0
                 T A, dx, dy, dg;
-                haar_split(a, b, hx * fabs(dd.z), hy * fabs(dd.w), A, dx, dy, dg);
+                haar_split(a, b, hx * dd.z, hy * fabs(dd.w), A, dx, dy, dg);
                 const T qs = q * scale;
+                const T qy = flip(qs, dd.w);       // qs with the sign that orders the y halves
                 acc[0] += qs * A;
-                // lower half minus upper half, by the travel direction's signs
-                const T ph = qs * flip(dy, dd.w);
-                const T pv = qs * flip(dx, dd.z);
-                const T pd = qs * flip2(dg, dd.z, dd.w);
+                // lower half minus upper half
+                const T ph = qy * dy;
+                const T pv = qs * dx;
+                const T pd = qy * dg;
                 if (ph > T(0)) acc[1] += ph; else acc[2] += ph;
                 if (pv > T(0)) acc[3] += pv; else acc[4] += pv;
                 if (pd > T(0)) acc[5] += pd; else acc[6] += pd;
@@ -430,7 +437,7 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                     evals += (cFF > T(0)) + (cFS > T(0)) + (cSF > T(0)) + (cSS > T(0));
                 }
             } else {
-                const T ch = block_chord_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w));
+                const T ch = block_chord_ab(a, b, hx * dd.z, hy * fabs(dd.w));
                 acc[0] += q * scale * ch;
                 if (WORK) evals += ch > T(0);
             }
@@ -572,36 +579,28 @@ __device__ __forceinline__ long long detail_index(const Layout& lay, int level, 
 
 // Eq. 1.9 = 0 solved for Delta = beta~ - betahat.  With u = exp(-Z0 Delta):
 // bp u^2 - b u + bm = 0, bp >= 0 >= bm, whose positive root is taken in the
-// form free of cancellation for the sign of b.  No ray weight (bp = bm = 0):
-// Delta = 0.  A minimiser at +-infinity is clamped to |Z0 Delta| = clamp
-// (hit reports that the step sits at the clamp).
-__device__ __forceinline__ double am_delta(double b, double bp, double bm, double z0, double clamp, bool& hit)
+// form free of cancellation for the sign of b.  root_t returns t = Z0 Delta
+// = -ln u, or +-big where the minimiser is at +-infinity (u = 0 or u = inf);
+// no ray weight (bp = bm = 0): 0.
+__device__ __forceinline__ double root_t(double b, double bp, double bm, double big)
 {
-    double t;   // = Z0 * Delta = -ln u
     if (bp > 0.0) {
         const double disc = sqrt(b * b - 4.0 * bp * bm);
         const double u = (b >= 0.0) ? (b + disc) / (2.0 * bp) : 2.0 * bm / (b - disc);
-        t = (u > 0.0) ? -log(u) : clamp;
-    } else if (bm < 0.0) {
-        t = (b < 0.0) ? -log(bm / b) : -clamp;
-    } else {
-        t = 0.0;
+        return (u > 0.0) ? -log(u) : big;
     }
-    t = fmin(fmax(t, -clamp), clamp);
-    hit = fabs(t) >= clamp;
-    return t / z0;
+    if (bm < 0.0) return (b < 0.0) ? -log(bm / b) : -big;
+    return 0.0;
 }
 
-// The same root in FP32 (iz0 = 1 / Z0 in FP32).  The root u is a ratio, so
-// b, bp and bm are first divided by the largest of |b|, bp, -bm (at least
-// 1e-30, for q-hat underflowing behind metal): no square or product can
-// overflow, and no case needs FP64 arithmetic (GB300's FP64 rate is a small
-// fraction of its FP32 rate).  A square that underflows leaves u at most a
-// factor 2 off where -ln u > 43, i.e. beyond any clamp.
-__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp,
-                                               bool& hit)
+// The same in FP32.  The root u is a ratio, so b, bp and bm are first
+// divided by the largest of |b|, bp, -bm (at least 1e-30, for q-hat
+// underflowing behind metal): no square or product can overflow, and no case
+// needs FP64 arithmetic (GB300's FP64 rate is a small fraction of its FP32
+// rate).  A square that underflows leaves u at most a factor 2 off where
+// -ln u > 43, i.e. beyond any clamp.
+__device__ __forceinline__ float root_t32(float bf, float bp, float bm, float big)
 {
-    float bf = (float)b;
     const float sc = fmaxf(fmaxf(bp, -bm), fabsf(bf));
     float t = 0.0f;
     if (sc > 0.0f) {
@@ -612,11 +611,29 @@ __device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, dou
         if (bp > 0.0f) {
             const float disc = sqrtf(bf * bf - 4.0f * bp * bm);
             const float u = (bf >= 0.0f) ? (bf + disc) / (2.0f * bp) : 2.0f * bm / (bf - disc);
-            t = (u > 0.0f) ? -logf(u) : (float)clamp;
+            t = (u > 0.0f) ? -logf(u) : big;
         } else if (bm < 0.0f) {
-            t = (bf < 0.0f) ? -logf(bm / bf) : -(float)clamp;
+            t = (bf < 0.0f) ? -logf(bm / bf) : -big;
         }
     }
+    return t;
+}
+
+// A minimiser at +-infinity is clamped to |Z0 Delta| = clamp (hit reports
+// that the step sits at the clamp).
+__device__ __forceinline__ double am_delta(double b, double bp, double bm, double z0, double clamp, bool& hit)
+{
+    double t = root_t(b, bp, bm, clamp);   // = Z0 * Delta
+    t = fmin(fmax(t, -clamp), clamp);
+    hit = fabs(t) >= clamp;
+    return t / z0;
+}
+
+// FP32 root (iz0 = 1 / Z0 in FP32).
+__device__ __forceinline__ double am_delta_f32(double b, float bp, float bm, double z0, float iz0, double clamp,
+                                               bool& hit)
+{
+    float t = root_t32((float)b, bp, bm, (float)clamp);
     t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
     hit = fabsf(t) >= (float)clamp;
     return (double)(t * iz0);
@@ -630,6 +647,40 @@ __device__ __forceinline__ double am_step(double b, float bp, float bm, double z
 __device__ __forceinline__ double am_step(double b, double bp, double bm, double z0, float, double clamp, bool& hit)
 {
     return am_delta(b, bp, bm, z0, clamp, hit);
+}
+
+// The step with an L1 penalty lam |beta| on the coefficient (Eq. 1.1 with
+// R = the l1 norm of the detail coefficients): the minimiser of the
+// one-coefficient surrogate of Eq. 1.8 plus lam |betahat + Delta|, a convex
+// function with a kink at t0 = -Z0 betahat (beta = 0).  Eq. 1.9's left side
+// increases in Delta, so the minimiser is the root for b + lam if it lies
+// beyond the kink, the root for b - lam if it lies before it, else the kink
+// itself (zero = true: beta becomes exactly 0).  The decision uses the
+// unclamped roots; the step is then clamped like the others.
+__device__ __forceinline__ double am_step_l1(double b, double bp, double bm, double z0, float, double clamp,
+                                             double bhat, double lam, bool& hit, bool& zero)
+{
+    const double big = 1e300;
+    const double up = root_t(b + lam, bp, bm, big), dn = root_t(b - lam, bp, bm, big);
+    const double t0 = -z0 * bhat;
+    double t = up > t0 ? up : (dn < t0 ? dn : t0);
+    zero = !(up > t0) && !(dn < t0) && fabs(t0) <= clamp;
+    t = fmin(fmax(t, -clamp), clamp);
+    hit = fabs(t) >= clamp;
+    return t / z0;
+}
+
+__device__ __forceinline__ double am_step_l1(double b, float bp, float bm, double z0, float iz0, double clamp,
+                                             double bhat, double lam, bool& hit, bool& zero)
+{
+    const float big = 3e38f;
+    const float up = root_t32((float)(b + lam), bp, bm, big), dn = root_t32((float)(b - lam), bp, bm, big);
+    const float t0 = (float)(-z0 * bhat);
+    float t = up > t0 ? up : (dn < t0 ? dn : t0);
+    zero = !(up > t0) && !(dn < t0) && fabsf(t0) <= (float)clamp;
+    t = fminf(fmaxf(t, -(float)clamp), (float)clamp);
+    hit = fabsf(t) >= (float)clamp;
+    return (double)(t * iz0);
 }
 
 // Sum of one slot of an item over the view chunks c = lane, lane + G, ... of
@@ -673,7 +724,7 @@ __host__ __device__ __forceinline__ long long upd_threads(const Segment& S)
 template <typename T>
 __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
                          const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
-                         float* __restrict__ beta32, int nonneg, unsigned long long* __restrict__ hits)
+                         float* __restrict__ beta32, int nonneg, double lam, unsigned long long* __restrict__ hits)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int si = 0;
@@ -715,7 +766,16 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     const double z0 = *z0p;
     const float iz0 = 1.0f / (float)z0;
     bool hit = false;
-    double nb = beta[z] + am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    double nb;
+    if (lam > 0.0 && !pix && (cf & 3) != 0) {
+        // a detail coefficient under the L1 penalty
+        bool zero = false;
+        const double bh = beta[z];
+        nb = bh + am_step_l1(bvec[z], bp, bm, z0, iz0, clamp, bh, lam, hit, zero);
+        if (zero) nb = 0.0;
+    } else {
+        nb = beta[z] + am_step(bvec[z], bp, bm, z0, iz0, clamp, hit);
+    }
     // plain AM kept nonnegative: the pixel's step ends at mu = 0 (the
     // separable surrogate's minimiser over mu >= 0)
     if (nonneg && pix) nb = fmax(nb, 0.0);
@@ -1242,14 +1302,44 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
 
 template <typename T>
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b,
-                          const double* z0, double clamp, double* beta, float* beta32, int nonneg,
+                          const double* z0, double clamp, double* beta, float* beta32, int nonneg, double lam,
                           unsigned long long* hits, cudaStream_t st)
 {
     if (tab.total_items == 0) return cudaSuccess;
     long long threads = 0;
     for (int i = 0; i < tab.n; ++i) threads += upd_threads(tab.s[i]);
     COUNT_LAUNCH();
-    k_update<T><<<nblk(threads, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta, beta32, nonneg, hits);
+    k_update<T><<<nblk(threads, 256), 256, 0, st>>>(tab, lay, part, b, z0, clamp, beta, beta32, nonneg, lam, hits);
+    return cudaGetLastError();
+}
+
+// lam * sum of |beta| over the detail coefficients (indices from the count
+// of level-L approximations on; inactive ones are 0): one FP64 partial per
+// CTA of 256 threads, each thread summing 4 coefficients in a fixed order.
+__global__ void k_l1_sum(const double* __restrict__ beta, long long first, long long n, double lam,
+                         double* __restrict__ part)
+{
+    double s = 0.0;
+    const long long base = first + ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) s += fabs(beta[base + k]);
+    s = block_reduce(s, OpSum(), 0.0);
+    if (threadIdx.x == 0) part[blockIdx.x] = lam * s;
+}
+
+int l1_parts(const Layout& lay)
+{
+    const long long nA = (long long)lay.gw[lay.L] * lay.gh[lay.L];
+    const long long nd = (long long)lay.nx * lay.ny - nA;
+    return (int)std::max(1LL, (nd + 1023) / 1024);
+}
+
+cudaError_t launch_l1_sum(const Layout& lay, const double* beta, double lam, double* part, cudaStream_t st)
+{
+    const long long nA = (long long)lay.gw[lay.L] * lay.gh[lay.L];
+    COUNT_LAUNCH();
+    k_l1_sum<<<l1_parts(lay), 256, 0, st>>>(beta, nA, (long long)lay.nx * lay.ny, lam, part);
     return cudaGetLastError();
 }
 
@@ -1400,28 +1490,39 @@ __global__ void k_update_dense(Layout lay, const uint8_t* __restrict__ mask, con
 
 // a6 per coefficient on flat arrays, with the same root the reconstruction's
 // k_update<T> applies (am_step: FP32 on normalised inputs for T = float, FP64
-// for T = double): the step-level view of the AM update.
+// for T = double; am_step_l1 where lam > 0): the step-level view of the AM
+// update.
 template <typename T>
 __global__ void k_am_delta(long long n, const double* __restrict__ bvec, const double* __restrict__ bp,
-                           const double* __restrict__ bm, double z0, double clamp, double* __restrict__ delta,
-                           int* __restrict__ at_clamp)
+                           const double* __restrict__ bm, const double* __restrict__ bhat, double lam, double z0,
+                           double clamp, double* __restrict__ delta, int* __restrict__ at_clamp)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool hit = false;
-    delta[i] = am_step(bvec[i], (T)bp[i], (T)bm[i], z0, 1.0f / (float)z0, clamp, hit);
+    const float iz0 = 1.0f / (float)z0;
+    double dl;
+    if (lam > 0.0) {
+        bool zero = false;
+        dl = am_step_l1(bvec[i], (T)bp[i], (T)bm[i], z0, iz0, clamp, bhat[i], lam, hit, zero);
+        if (zero) dl = -bhat[i];
+    } else {
+        dl = am_step(bvec[i], (T)bp[i], (T)bm[i], z0, iz0, clamp, hit);
+    }
+    delta[i] = dl;
     if (at_clamp) at_clamp[i] = hit ? 1 : 0;
 }
 
 cudaError_t launch_am_delta(int precision, long long n, const double* b, const double* bp, const double* bm,
-                            double z0, double clamp, double* delta, int* at_clamp, cudaStream_t st)
+                            const double* bhat, double lam, double z0, double clamp, double* delta, int* at_clamp,
+                            cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     COUNT_LAUNCH();
     if (precision == 32)
-        k_am_delta<float><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, z0, clamp, delta, at_clamp);
+        k_am_delta<float><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, bhat, lam, z0, clamp, delta, at_clamp);
     else
-        k_am_delta<double><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, z0, clamp, delta, at_clamp);
+        k_am_delta<double><<<nblk(n, 256), 256, 0, st>>>(n, b, bp, bm, bhat, lam, z0, clamp, delta, at_clamp);
     return cudaGetLastError();
 }
 
@@ -1447,7 +1548,8 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
     template cudaError_t launch_backproject<T>(const Geom<T>&, const SegTable&, const T*, const void*, T*,       \
                                                unsigned long long*, cudaStream_t);                              \
     template cudaError_t launch_update<T>(const SegTable&, const Layout&, const T*, const double*, const double*, \
-                                          double, double*, float*, int, unsigned long long*, cudaStream_t);      \
+                                          double, double*, float*, int, double, unsigned long long*,             \
+                                          cudaStream_t);                                                         \
     template cudaError_t launch_split_out<T>(const SegTable&, const Layout&, const T*, double*, double*,         \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_synth<T>(const Layout&, const uint8_t*, const double*, T*, cudaStream_t);        \

@@ -49,6 +49,7 @@ struct RunRecord {
     std::vector<double> tau;
     int iters_done = 0, expansions_done = 0, n_subsets = 1, nonneg = 0;
     double tuning = 32.0;
+    double lambda = 0.0;
     std::vector<double> beta, hist;     // host copies (loaded state only)
     std::vector<uint8_t> mask;
 };
@@ -170,6 +171,7 @@ void record_run(wam_ctx* c, const wam_schedule* sc, int iters, int expansions)
     r.expansions_done = expansions;
     r.n_subsets = std::max(1, sc->n_subsets);
     r.nonneg = sc->nonneg != 0;
+    r.lambda = sc->lambda;
     r.tuning = c->back_ctas_per_sm;
     c->pending = RunRecord{};
 }
@@ -183,7 +185,7 @@ wam_status check_resume(wam_ctx* c, const wam_schedule* sc)
     const int L = sc->full_am ? 0 : sc->levels;
     if (L != r.levels || sc->full_am != r.full_am || sc->precision != r.precision || eff_dims(c, sc) != r.dims ||
         sc->zsum_criterion != r.zsum || eff_clamp(sc) != r.clamp || std::max(1, sc->n_subsets) != r.n_subsets ||
-        (sc->nonneg != 0) != (r.nonneg != 0))
+        (sc->nonneg != 0) != (r.nonneg != 0) || sc->lambda != r.lambda)
         return fail(c, WAM_ERR_STATE, "resume: the schedule's method differs from the checkpoint's");
     if (sc->n_iters < r.iters_done) return fail(c, WAM_ERR_STATE, "resume: n_iters is below the iterations done");
     if (L > 0) {
@@ -406,7 +408,9 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
 
 // Per ray (s/dx, -c/dy, 1/dx, 1/dy): the reciprocal unit direction and its
 // products with the view's sin and -cos, computed in FP64 on the host once
-// per context and precision.
+// per context and precision.  Every ray is taken in the orientation with
+// dx >= 0 (a line's two orientations cross the same voxels), so the
+// back-projector's first x half along the travel is always the lower one.
 template <typename T>
 wam_status dir_table(wam_ctx* c, const void** out, const std::vector<int>* order = nullptr)
 {
@@ -435,6 +439,10 @@ wam_status dir_table(wam_ctx* c, const void** out, const std::vector<int>* order
                 const double rn = 1.0 / std::sqrt(w.sdd * w.sdd + ub * ub);
                 dx = (-w.sdd * cs - ub * sn) * rn;
                 dy = (-w.sdd * sn + ub * cs) * rn;
+            }
+            if (std::signbit(dx)) {
+                dx = -dx;
+                dy = -dy;
             }
             const double ix = rcp(dx), iy = rcp(dy);
             T* e = &h[4 * ((size_t)k * w.n_bins + b)];
@@ -575,7 +583,9 @@ struct Run {
     wam_ctx* c = nullptr;
     const wam_schedule* sc = nullptr;
     int L = 0, J = 0, np = 0, npc = 0;   // partial buffer size; cost partials of one forward
+    int nl1 = 0;                // lam > 0: partials of the penalty after the forward's
     double clamp = 30.0;
+    double lam = 0.0;           // L1 penalty on the detail coefficients (0: Algorithm 1 as stated)
     long long N = 0, M = 0;
     Layout lay{};
     Geom<T> g{};
@@ -629,6 +639,7 @@ struct Run {
         L = sc->full_am ? 0 : sc->levels;
         J = sc->n_iters;
         clamp = sc->dmax_clamp > 0 ? sc->dmax_clamp : 30.0;
+        lam = sc->lambda;
         WST(make_layout(c, L, &lay));
         WST(make_geom<T>(c, &g));
         N = c->N;
@@ -648,7 +659,8 @@ struct Run {
         WST(ensure_t(c, B_COUNTER, 1, &counter));
         np = forward_parts(g.V, g.B);
         npc = forward_cost_parts(g.V, g.B);
-        WST(ensure_t(c, B_COSTPART, (size_t)np, &cpart));
+        nl1 = lam > 0 ? l1_parts(lay) : 0;
+        WST(ensure_t(c, B_COSTPART, (size_t)std::max(np, npc + nl1), &cpart));
         if (L > 0) {
             WST(ensure_t(c, B_MASK_A, (size_t)lay.mask_bytes, &mask));
             WST(ensure_t(c, B_MASK_B, (size_t)lay.mask_bytes, &mask2));
@@ -857,7 +869,7 @@ struct Run {
                                           work_ptr(c, WAM_K_BACKPROJECT), st));
             }
             PROF(WAM_K_UPDATE);
-            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, beta32, sc->nonneg,
+            WCK(c, launch_update(tab, lay, part, bsub + (size_t)ss * N, z0sub + ss, clamp, beta, beta32, sc->nonneg, 0.0,
                                  work_ptr(c, WAM_K_UPDATE), st));
         }
         return WAM_OK;
@@ -900,8 +912,7 @@ struct Run {
             else
                 WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, synth_src(), fwd_lam, mut, dsino, dterm, I0, q,
                                            (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
-            if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
-            else WCK(c, launch_sum_final(cpart, npc, costs + j, st));
+            WST(cost_out(costs + j, use_counter, st));
         }
         {
             PROF(WAM_K_BACKPROJECT);                                                        // a4
@@ -909,7 +920,7 @@ struct Run {
         }
         {
             PROF(WAM_K_UPDATE);                                                             // a6
-            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, beta32, sc->nonneg, work_ptr(c, WAM_K_UPDATE),
+            WCK(c, launch_update(tab, lay, part, bvec, z0, clamp, beta, beta32, sc->nonneg, lam, work_ptr(c, WAM_K_UPDATE),
                                  st));
         }
         return WAM_OK;
@@ -952,9 +963,18 @@ struct Run {
             else
                 WCK(c, launch_forward_tree(g, lay, L > 0 ? leaf : nullptr, synth_src(), fwd_lam, mut, dsino, dterm,
                                            I0, q, (T*)nullptr, (T*)nullptr, cpart, work_ptr(c, WAM_K_FORWARD), st));
-            if (use_counter) WCK(c, launch_sum_at(cpart, npc, costs, counter, st));
-            else WCK(c, launch_sum_final(cpart, npc, costs + J, st));
+            WST(cost_out(costs + J, use_counter, st));
         }
+        return WAM_OK;
+    }
+
+    // the forward's cost partials (and, with lam > 0, the penalty of the same
+    // beta) summed into `at`, or into costs[*counter] with use_counter
+    wam_status cost_out(double* at, bool use_counter, cudaStream_t st)
+    {
+        if (nl1 > 0) WCK(c, launch_l1_sum(lay, beta, lam, cpart + npc, st));
+        if (use_counter) WCK(c, launch_sum_at(cpart, npc + nl1, costs, counter, st));
+        else WCK(c, launch_sum_final(cpart, npc + nl1, at, st));
         return WAM_OK;
     }
 
@@ -1689,6 +1709,10 @@ wam_status wam_reconstruct(wam_ctx* c, const wam_schedule* sc, void* mu_out, dou
     if (sc->nonneg != 0 && sc->nonneg != 1) return fail(c, WAM_ERR_ARG, "nonneg must be 0 or 1");
     if (sc->nonneg && !sc->full_am && sc->levels != 0)
         return fail(c, WAM_ERR_ARG, "nonneg applies to plain AM (full_am or levels = 0) only");
+    if (!(sc->lambda >= 0.0) || !std::isfinite(sc->lambda)) return fail(c, WAM_ERR_ARG, "lambda must be finite and >= 0");
+    if (sc->lambda > 0.0 && (sc->full_am || sc->levels == 0 || sc->n_subsets > 1 ||
+                             c->g.kind == WAM_CONE3D_FLAT_CIRCULAR))
+        return fail(c, WAM_ERR_ARG, "lambda > 0 needs a 2-D Haar tree (levels > 0) without ordered subsets");
     if (sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c, WAM_ERR_ARG, "expand_at/tau missing");
     for (int k = 0; k < sc->n_expand; ++k) {
@@ -1727,7 +1751,7 @@ wam_status wam_checkpoint(wam_ctx* c, const char* path)
         const wam_geometry& g = c->g;
         CkptWriter w;
         w.raw(kCkptMagic, 8);
-        const uint32_t version = 2, zero = 0;
+        const uint32_t version = 3, zero = 0;
         w.raw(&version, 4);
         w.raw(&zero, 4);
         const long long ints[22] = {g.kind, g.nx, g.ny, g.nz, g.n_views, g.n_bins, g.n_rows, r.levels, r.dims,
@@ -1735,8 +1759,8 @@ wam_status wam_checkpoint(wam_ctx* c, const char* path)
                                     r.expansions_done, c->N, (long long)mb, (long long)hist.size(), cd, ci,
                                     r.n_subsets, r.nonneg};
         for (long long v : ints) w.i64(v);
-        const double dbl[11] = {g.vx, g.vy, g.vz, g.angle0, g.angle_span, g.bin_pitch, g.row_pitch, g.sod, g.sdd,
-                                r.clamp, r.tuning};
+        const double dbl[12] = {g.vx, g.vy, g.vz, g.angle0, g.angle_span, g.bin_pitch, g.row_pitch, g.sod, g.sdd,
+                                r.clamp, r.tuning, r.lambda};
         for (double v : dbl) w.f64(v);
         for (int v : r.expand_at) w.i64(v);
         for (double v : r.tau) w.f64(v);
@@ -1787,14 +1811,14 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         CkptReader rd{buf.data(), buf.size() - 4};
         rd.at = 8;
         uint32_t version = 0, zero = 0;
-        if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || version != 2)
+        if (!rd.raw(&version, 4) || !rd.raw(&zero, 4) || (version != 2 && version != 3))
             return fail(c, WAM_ERR_IO, "unsupported checkpoint version");
         long long v[22];
-        double d[11];
+        double d[12] = {0};                   // version 2 files carry no lambda (0)
         for (long long& x : v)
             if (!rd.i64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
-        for (double& x : d)
-            if (!rd.f64(&x)) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
+        for (int k = 0; k < (version == 3 ? 12 : 11); ++k)
+            if (!rd.f64(&d[k])) return fail(c, WAM_ERR_IO, "checkpoint header truncated");
         const wam_geometry& g = c->g;
         const bool same_geom = v[0] == g.kind && v[1] == g.nx && v[2] == g.ny && v[3] == g.nz && v[4] == g.n_views &&
                                v[5] == g.n_bins && v[6] == g.n_rows && d[0] == g.vx && d[1] == g.vy &&
@@ -1818,11 +1842,13 @@ wam_status wam_resume(wam_ctx* c, const char* path)
         r.nonneg = (int)v[21];
         r.clamp = d[9];
         r.tuning = d[10];
+        r.lambda = d[11];
         const size_t mb = r.levels > 0 ? wam_mask_bytes_dims(c, r.levels, r.dims) : 0;
         if (r.levels < 0 || r.levels > WAM_MAX_LEVELS || n_expand < 0 || n_expand > 4096 || r.iters_done < 0 ||
             r.expansions_done < 0 || r.expansions_done > n_expand || v[15] != c->N || v[16] != (long long)mb ||
             v[17] != (long long)r.iters_done + 1 || !(r.tuning >= 0.25 && r.tuning <= 256.0) || r.n_subsets < 1 ||
-            r.n_subsets > c->g.n_views || (r.nonneg != 0 && r.nonneg != 1))
+            r.n_subsets > c->g.n_views || (r.nonneg != 0 && r.nonneg != 1) || !(r.lambda >= 0.0) ||
+            !std::isfinite(r.lambda))
             return fail(c, WAM_ERR_IO, "checkpoint header is inconsistent with this context");
         r.expand_at.resize((size_t)n_expand);
         r.tau.resize((size_t)n_expand);
@@ -1993,13 +2019,15 @@ wam_status wam_update(wam_ctx* c, int levels, const unsigned char* masks, const 
     return WAM_OK;
 }
 
-wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus, double z0,
-                        double clamp, int precision, double* delta, int* at_clamp, void* stream)
+wam_status wam_am_delta(long long n, const double* b, const double* bplus, const double* bminus,
+                        const double* beta, double lambda, double z0, double clamp, int precision, double* delta,
+                        int* at_clamp, void* stream)
 {
     if (n < 0 || (n > 0 && (!b || !bplus || !bminus || !delta))) return WAM_ERR_ARG;
     if (precision != 32 && precision != 64) return WAM_ERR_ARG;
     if (!(z0 > 0) || !std::isfinite(z0) || std::isnan(clamp)) return WAM_ERR_ARG;
-    if (launch_am_delta(precision, n, b, bplus, bminus, z0, clamp > 0 ? clamp : 30.0, delta, at_clamp,
+    if (!(lambda >= 0.0) || !std::isfinite(lambda) || (lambda > 0.0 && n > 0 && !beta)) return WAM_ERR_ARG;
+    if (launch_am_delta(precision, n, b, bplus, bminus, beta, lambda, z0, clamp > 0 ? clamp : 30.0, delta, at_clamp,
                         as_stream(stream)) != cudaSuccess) {
         cudaGetLastError();
         return WAM_ERR_CUDA;
@@ -2098,6 +2126,8 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
     if (sc->nonneg != 0 && sc->nonneg != 1) return fail(c0, WAM_ERR_ARG, "nonneg must be 0 or 1");
     if (sc->nonneg && !sc->full_am && sc->levels != 0)
         return fail(c0, WAM_ERR_ARG, "nonneg applies to plain AM (full_am or levels = 0) only");
+    if (!(sc->lambda >= 0.0) || !std::isfinite(sc->lambda) || (sc->lambda > 0.0 && (sc->full_am || sc->levels == 0)))
+        return fail(c0, WAM_ERR_ARG, "lambda must be finite and >= 0, and > 0 only with a Haar tree");
     if (sc->n_iters < 0 || sc->n_expand < 0 || (sc->n_expand > 0 && (!sc->expand_at || !sc->tau)))
         return fail(c0, WAM_ERR_ARG, "bad schedule");
     for (int k = 0; k < sc->n_expand; ++k)

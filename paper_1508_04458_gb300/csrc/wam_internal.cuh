@@ -327,6 +327,21 @@ __device__ __forceinline__ void child_chords_phys(T a, T b, T Hx, T Hy, T ix, T 
     chh = fmax(fmin(xh1, yh1) - fmax(xh0, yh0), T(0));
 }
 
+// The same for a ray taken with dx >= 0 (ix = 1/dx >= 0): the lower-x child
+// spans [a - 2 Hx ix, a] and the upper one [a, a + 2 Hx ix].
+template <typename T>
+__device__ __forceinline__ void child_chords_phys_xpos(T a, T b, T Hx, T Hy, T ix, T iy, T& cll, T& chl, T& clh,
+                                                       T& chh)
+{
+    const T uy = fabs(iy) + iy, wy = fabs(iy) - iy;
+    const T xl0 = fma(-2 * Hx, ix, a), xh1 = fma(2 * Hx, ix, a);
+    const T yl0 = fma(-Hy, uy, b), yl1 = fma(Hy, wy, b), yh0 = fma(-Hy, wy, b), yh1 = fma(Hy, uy, b);
+    cll = fmax(fmin(a, yl1) - fmax(xl0, yl0), T(0));
+    chl = fmax(fmin(xh1, yl1) - fmax(a, yl0), T(0));
+    clh = fmax(fmin(a, yh1) - fmax(xl0, yh0), T(0));
+    chh = fmax(fmin(xh1, yh1) - fmax(a, yh0), T(0));
+}
+
 // The Haar split of a ray through a block without its four child chords:
 // with [lo, hi] the ray's parameter interval inside the block (a, b, Ax, Ay
 // as in child_chords_ab) and ca, cb the centre-line crossings clamped to it,

@@ -57,10 +57,14 @@ cudaError_t launch_backproject(const Geom<T>& g, const SegTable& tab, const T* s
                                unsigned long long* work, cudaStream_t st);
 template <typename T>
 // beta32 (optional): the float copy of beta, rewritten for every updated
-// coefficient; nonneg: pixel coefficients end their step at 0 (plain AM)
+// coefficient; nonneg: pixel coefficients end their step at 0 (plain AM);
+// lam > 0: detail coefficients take the L1-penalised step
 cudaError_t launch_update(const SegTable& tab, const Layout& lay, const T* part, const double* b, const double* z0,
-                          double clamp, double* beta, float* beta32, int nonneg, unsigned long long* hits,
+                          double clamp, double* beta, float* beta32, int nonneg, double lam, unsigned long long* hits,
                           cudaStream_t st);
+// lam * sum |beta| over the detail coefficients as l1_parts(lay) FP64 partials
+int l1_parts(const Layout& lay);
+cudaError_t launch_l1_sum(const Layout& lay, const double* beta, double lam, double* part, cudaStream_t st);
 template <typename T>
 cudaError_t launch_split_out(const SegTable& tab, const Layout& lay, const T* part, double* bp, double* bm,
                              cudaStream_t st);
@@ -88,9 +92,11 @@ cudaError_t launch_update_dense(const Layout& lay, const uint8_t* mask, const do
                                 const double* bm, const double* z0, double clamp, double* beta, cudaStream_t st);
 
 // Eq. 1.9's step per coefficient on flat arrays with the reconstruction's own
-// root (precision 32: bp, bm rounded to float and the FP32 root; 64: FP64)
+// root (precision 32: bp, bm rounded to float and the FP32 root; 64: FP64;
+// lam > 0: the L1-penalised step from the current values bhat)
 cudaError_t launch_am_delta(int precision, long long n, const double* b, const double* bp, const double* bm,
-                            double z0, double clamp, double* delta, int* at_clamp, cudaStream_t st);
+                            const double* bhat, double lam, double z0, double clamp, double* delta, int* at_clamp,
+                            cudaStream_t st);
 
 unsigned long long kernel_launches();
 // kernels run by graph replays (counted once when captured)

@@ -53,7 +53,7 @@ class wam_schedule(ctypes.Structure):
                 ("n_expand", ctypes.c_int), ("expand_at", ctypes.POINTER(ctypes.c_int)),
                 ("tau", ctypes.POINTER(ctypes.c_double)), ("zsum_criterion", ctypes.c_int),
                 ("precision", ctypes.c_int), ("full_am", ctypes.c_int), ("dmax_clamp", ctypes.c_double),
-                ("n_subsets", ctypes.c_int), ("nonneg", ctypes.c_int)]
+                ("n_subsets", ctypes.c_int), ("nonneg", ctypes.c_int), ("lambda_", ctypes.c_double)]
 
 
 WAM_K_FORWARD, WAM_K_BACKPROJECT, WAM_K_UPDATE, WAM_K_Z0, WAM_K_SYNTH, WAM_K_TREE = range(6)
@@ -92,7 +92,7 @@ _PROTOS = {
     "wam_z0": (_S, [_P, _I, _P, _P, _P]),
     "wam_update": (_S, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "wam_expand": (_S, [_P, _I, _P, _D, _P, _P, _P]),
-    "wam_am_delta": (_S, [ctypes.c_longlong, _P, _P, _P, _D, _D, _I, _P, _P, _P]),
+    "wam_am_delta": (_S, [ctypes.c_longlong, _P, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P]),
     "wam_project_coef": (_S, [_P, _I, _P, _P, _P]),
     "wam_backproject_coef": (_S, [_P, _I, _P, _P, _P]),
     "wam_idiv_grad": (_S, [_P, _I, _P, ctypes.c_float, _P, _P, _P, _P]),
@@ -151,7 +151,7 @@ def geometry(g) -> wam_geometry:
 
 def schedule(levels: int, n_iters: int, expand_at: Sequence[int] = (), tau: Sequence[float] = (),
              precision: int = 32, full_am: bool = False, clamp: float = 30.0, dims: int = 2,
-             zsum: bool = False, n_subsets: int = 1, nonneg: bool = False):
+             zsum: bool = False, n_subsets: int = 1, nonneg: bool = False, lam: float = 0.0):
     """wam_schedule plus the arrays it points to (keep the tuple alive)."""
     ea = (ctypes.c_int * max(1, len(expand_at)))(*expand_at)
     ta = (ctypes.c_double * max(1, len(tau)))(*tau)
@@ -159,7 +159,7 @@ def schedule(levels: int, n_iters: int, expand_at: Sequence[int] = (), tau: Sequ
                      expand_at=ctypes.cast(ea, ctypes.POINTER(ctypes.c_int)),
                      tau=ctypes.cast(ta, ctypes.POINTER(ctypes.c_double)), zsum_criterion=1 if zsum else 0,
                      precision=precision, full_am=1 if full_am else 0, dmax_clamp=clamp, n_subsets=n_subsets,
-                     nonneg=1 if nonneg else 0)
+                     nonneg=1 if nonneg else 0, lambda_=float(lam))
     return s, (ea, ta)
 
 
@@ -212,14 +212,16 @@ class Context:
 
     def reconstruct(self, levels: int, n_iters: int, expand_at=(), tau=(), precision: int = 32,
                     full_am: bool = False, device_out: bool = False, stream: Optional[int] = None,
-                    dims: int = 2, zsum: bool = False, n_subsets: int = 1, nonneg: bool = False):
+                    dims: int = 2, zsum: bool = False, n_subsets: int = 1, nonneg: bool = False,
+                    lam: float = 0.0):
         """Run the method; returns (mu, idiv history, masks, status).  Cone-beam
         contexts: dims = 3 (3-D Haar) or dims = 2 with zsum (per-slice Haar).
         n_subsets > 1: ordered subsets of views (2-D).  nonneg: plain AM with
-        mu >= 0 (each pixel's step ends at 0)."""
+        mu >= 0 (each pixel's step ends at 0).  lam > 0: the L1 penalty on the
+        detail coefficients (wam_schedule.lambda)."""
         import torch
         sc, keep = schedule(levels, n_iters, expand_at, tau, precision, full_am, dims=dims, zsum=zsum,
-                            n_subsets=n_subsets, nonneg=nonneg)
+                            n_subsets=n_subsets, nonneg=nonneg, lam=lam)
         L = 0 if full_am else levels
         N = self.geom.nx * self.geom.ny * max(1, getattr(self.geom, "nz", 1))
         s = current_stream() if stream is None else stream

@@ -59,3 +59,22 @@ def test_null_context_is_rejected_without_gpu(lib):
     lib.wam_create.restype = ctypes.c_int
     out = ctypes.c_void_p()
     assert lib.wam_create(None, ctypes.byref(out)) == -1
+
+
+def test_every_binding_call_passes_the_declared_argument_count():
+    # each call of a C-ABI function in the tests, the benchmark and the
+    # package passes as many arguments as its ctypes prototype (the header's)
+    import ast
+    import glob
+    from paper_1508_04458_gb300 import wam
+    files = glob.glob(os.path.join(ROOT, "tests", "*.py")) + [os.path.join(ROOT, "bench.py")] + \
+        glob.glob(os.path.join(ROOT, "paper_1508_04458_gb300", "*.py"))
+    bad = []
+    for f in files:
+        for node in ast.walk(ast.parse(open(f).read())):
+            if isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute) and node.func.attr in wam._PROTOS:
+                if any(isinstance(a, ast.Starred) for a in node.args):
+                    continue
+                if len(node.args) != len(wam._PROTOS[node.func.attr][1]):
+                    bad.append((os.path.basename(f), node.lineno, node.func.attr))
+    assert not bad, bad

@@ -11,8 +11,9 @@ from paper_1508_04458_gb300 import checkpoint as ck
 
 
 def _assemble(ints, dbls, expand_at, tau, beta, masks, hist):
-    b = bytearray(b"WAMCKPT1") + struct.pack("<II", 2, 0)
-    b += struct.pack("<22q", *ints) + struct.pack("<11d", *dbls)
+    version = 3 if len(dbls) == 12 else 2          # version 3 adds lambda after tuning
+    b = bytearray(b"WAMCKPT1") + struct.pack("<II", version, 0)
+    b += struct.pack("<22q", *ints) + struct.pack("<%dd" % len(dbls), *dbls)
     b += struct.pack("<%dq" % len(expand_at), *expand_at) + struct.pack("<%dd" % len(tau), *tau)
     b += np.asarray(beta, "<f8").tobytes() + np.asarray(masks, np.uint8).tobytes()
     b += np.asarray(hist, "<f8").tobytes()
@@ -29,7 +30,7 @@ def _example():
     masks = (rng.random(mb) < 0.5).astype(np.uint8)
     hist = np.sort(rng.random(7))[::-1] * 1e5
     ints = [1, nx, ny, 1, 30, 41, 1, L, 2, 0, 32, 0, 2, 6, 1, N, mb, 7, 123456789, 987654321, 4, 0]
-    dbls = [1.0, 1.0, 1.0, 0.0, 6.283185307179586, 1.2, 1.0, 500.0, 800.0, 30.0, 32.0]
+    dbls = [1.0, 1.0, 1.0, 0.0, 6.283185307179586, 1.2, 1.0, 500.0, 800.0, 30.0, 32.0, 0.25]
     return _assemble(ints, dbls, [3, 9], [0.1, -1.0], beta, masks, hist), beta, masks, hist
 
 
@@ -39,7 +40,7 @@ def test_round_trip():
     assert (c["nx"], c["ny"], c["levels"], c["iters_done"], c["expansions_done"]) == (16, 8, 2, 6, 1)
     assert c["expand_at"] == [3, 9] and c["tau"] == [0.1, -1.0]
     assert c["crc_d"] == 123456789 and c["sdd"] == 800.0 and c["tuning"] == 32.0 and c["n_subsets"] == 4
-    assert c["nonneg"] == 0
+    assert c["nonneg"] == 0 and c["lambda"] == 0.25 and c["version"] == 3
     np.testing.assert_array_equal(c["beta"], beta)
     np.testing.assert_array_equal(c["masks"], masks)
     np.testing.assert_array_equal(c["hist"], hist)
@@ -73,3 +74,15 @@ def test_version_and_nonneg_field():
     old += struct.pack("<I", zlib.crc32(bytes(old)) & 0xFFFFFFFF)
     with pytest.raises(ck.CheckpointError):
         ck.parse(bytes(old))
+
+
+def test_version_2_layout_reads_as_lambda_zero():
+    # the earlier layout: 11 doubles (no lambda); it still decodes, with lambda = 0
+    rng = np.random.default_rng(1)
+    nx, ny, L = 8, 8, 1
+    N, mb = nx * ny, (nx >> 1) * (ny >> 1)
+    ints = [1, nx, ny, 1, 10, 17, 1, L, 2, 0, 32, 0, 0, 2, 0, N, mb, 3, 1, 2, 1, 0]
+    dbls = [1.0, 1.0, 1.0, 0.0, 6.283185307179586, 1.2, 1.0, 500.0, 800.0, 30.0, 32.0]
+    buf = _assemble(ints, dbls, [], [], rng.normal(size=N), np.zeros(mb, np.uint8), [3.0, 2.0, 1.0])
+    c = ck.parse(buf)
+    assert c["version"] == 2 and c["lambda"] == 0.0 and c["tuning"] == 32.0

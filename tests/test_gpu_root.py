@@ -70,7 +70,7 @@ def _run(b, bp, bm, z0, precision):
     tb, tp, tm = dev(b), dev(bp), dev(bm)
     delta = torch.empty_like(tb)
     hit = torch.empty(len(b), dtype=torch.int32, device="cuda")
-    rc = wam.wam_am_delta(len(b), wam.ptr(tb), wam.ptr(tp), wam.ptr(tm), z0, CLAMP, precision,
+    rc = wam.wam_am_delta(len(b), wam.ptr(tb), wam.ptr(tp), wam.ptr(tm), 0, 0.0, z0, CLAMP, precision,
                           wam.ptr(delta), wam.ptr(hit), wam.current_stream())
     assert rc == wam.WAM_OK
     torch.cuda.synchronize()
@@ -106,7 +106,9 @@ def test_root_rejects_bad_arguments():
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
     p = wam.ptr(x)
     st = wam.current_stream()
-    assert wam.wam_am_delta(4, p, p, p, 0.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG     # Z0 = 0
-    assert wam.wam_am_delta(4, p, p, p, 1.0, CLAMP, 16, p, 0, st) == wam.WAM_ERR_ARG     # precision
-    assert wam.wam_am_delta(4, 0, p, p, 1.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG     # null
-    assert wam.wam_am_delta(0, 0, 0, 0, 1.0, CLAMP, 32, 0, 0, st) == wam.WAM_OK          # empty
+    assert wam.wam_am_delta(4, p, p, p, 0, 0.0, 0.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG     # Z0 = 0
+    assert wam.wam_am_delta(4, p, p, p, 0, 0.0, 1.0, CLAMP, 16, p, 0, st) == wam.WAM_ERR_ARG     # precision
+    assert wam.wam_am_delta(4, 0, p, p, 0, 0.0, 1.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG     # null
+    assert wam.wam_am_delta(4, p, p, p, 0, 1.0, 1.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG     # no beta
+    assert wam.wam_am_delta(4, p, p, p, p, -1.0, 1.0, CLAMP, 32, p, 0, st) == wam.WAM_ERR_ARG    # lambda < 0
+    assert wam.wam_am_delta(0, 0, 0, 0, 0, 0.0, 1.0, CLAMP, 32, 0, 0, st) == wam.WAM_OK          # empty

@@ -350,3 +350,67 @@ def test_nonneg_plain_am_minimises_the_surrogate_over_nonnegative_images():
                       options=dict(ftol=1e-15, gtol=1e-12, maxiter=5000))
     np.testing.assert_allclose(res.x, step, atol=2e-6 * max(1.0, np.abs(step).max()))
     assert np.any((step == 0.0) & (mu_hat + delta < 0.0))   # the bound is active somewhere
+
+
+# ---------------------------------------------------------------------------
+# the L1-penalised step (Eq. 1.1 with R = l1 norm of the detail coefficients)
+# ---------------------------------------------------------------------------
+
+def _penalised_1d(delta, b, bp, bm, Z0, beta_hat, lam):
+    """The one-coefficient surrogate of Eq. 1.8 (up to a constant) plus the
+    penalty: b D + (bp exp(-Z0 D) - bm exp(Z0 D)) / Z0 + lam |beta_hat + D|;
+    its derivative in D is Eq. 1.9 plus lam sign(beta_hat + D)."""
+    return b * delta + (bp * math.exp(-Z0 * delta) - bm * math.exp(Z0 * delta)) / Z0 + lam * abs(beta_hat + delta)
+
+
+def test_l1_root_minimises_the_penalised_surrogate():
+    rng = np.random.default_rng(12)
+    n = 300
+    Z0 = 20.0
+    b = rng.standard_normal(n) * 10.0 ** rng.uniform(-1, 2, n)
+    bp = rng.uniform(0.1, 1, n) * 10.0 ** rng.uniform(-1, 2, n)
+    bm = -rng.uniform(0.1, 1, n) * 10.0 ** rng.uniform(-1, 2, n)
+    beta_hat = rng.normal(0, 0.05, n)
+    beta_hat[::7] = 0.0
+    lam = 10.0 ** rng.uniform(-2, 2, n)
+    got = am.am_root_l1(b, bp, bm, Z0, beta_hat, lam, clamp=np.inf)
+    for i in range(n):
+        f = lambda x: _penalised_1d(x, b[i], bp[i], bm[i], Z0, beta_hat[i], lam[i])
+        ref = so.minimize_scalar(f, bounds=(-3.0, 3.0), method="bounded",
+                                 options={"xatol": 1e-13, "maxiter": 2000}).x
+        assert f(got[i]) <= f(ref) + 1e-10 * (1 + abs(f(ref)))
+        # the kink: beta lands exactly on 0 when neither one-sided root is admissible
+        if abs(beta_hat[i] + got[i]) < 1e-300:
+            assert beta_hat[i] + got[i] == 0.0
+    # lam = 0 is the unpenalised root of Eq. 1.9
+    np.testing.assert_allclose(am.am_root_l1(b, bp, bm, Z0, beta_hat, 0.0), am.am_root(b, bp, bm, Z0),
+                               rtol=1e-14, atol=1e-300)
+
+
+def test_l1_root_soft_threshold_at_zero():
+    # from beta_hat = 0 with |g(0)| = |b - bp - bm| <= lam the coefficient stays 0
+    Z0 = 5.0
+    b, bp, bm = np.array([1.0, 1.0, 1.0]), np.array([0.8, 0.8, 0.8]), np.array([-0.1, -0.1, -0.1])
+    g0 = 1.0 - 0.8 + 0.1
+    d = am.am_root_l1(b, bp, bm, Z0, 0.0, np.array([g0 * 1.01, g0 * 0.5, 0.0]))
+    assert d[0] == 0.0
+    assert d[1] < 0.0 and d[1] > d[2]          # shrunk toward 0 relative to the unpenalised step
+
+
+def test_penalised_wavelet_am_decreases_its_objective():
+    p, H = _small(nx=32, ny=32, V=36, B=53)
+    L = 3
+    for lam in (1.0, 30.0):
+        r = am.wavelet_am(H, p.d, p.I0, 32, 32, L, 14, expand_at=(3, 6, 9), taus=(0.1, 0.03, -1.0), lam=lam)
+        assert np.all(np.diff(r.cost) <= 1e-12 * r.cost[:-1])
+        # the reported objective is the data term plus the penalty of the same beta
+        Phi = H @ haar.basis_matrix(32, 32, L)
+        want = am.idiv(p.d, p.I0, Phi @ r.beta) + lam * am.l1_details(r.beta, 32, 32, L)
+        assert r.cost[-1] == pytest.approx(want, rel=1e-12)
+    r0 = am.wavelet_am(H, p.d, p.I0, 32, 32, L, 6, expand_at=(3,), taus=(0.1,), lam=0.0)
+    r1 = am.wavelet_am(H, p.d, p.I0, 32, 32, L, 6, expand_at=(3,), taus=(0.1,))
+    assert np.array_equal(r0.beta, r1.beta)
+    # a penalty larger than every detail gradient keeps every detail at 0
+    big = am.wavelet_am(H, p.d, p.I0, 32, 32, L, 8, expand_at=(2,), taus=(-1.0,), lam=1e12)
+    _, typ, _, _ = haar.coefficient_info(32, 32, L)
+    assert np.all(big.beta[typ >= 0] == 0.0)
