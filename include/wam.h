@@ -71,7 +71,8 @@ typedef enum {
     WAM_ERR_ARG = -1,      /* invalid argument; nothing was launched */
     WAM_ERR_OOM = -2,      /* device allocation failed */
     WAM_ERR_CUDA = -3,     /* a CUDA call failed */
-    WAM_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    WAM_ERR_TIMEOUT = -4,  /* a bounded device wait gave up (a shared-memory image copy of the
+                              forward projector did not complete in time); results are invalid */
     WAM_ERR_STATE = -5,    /* call order violated (e.g. no data set) */
     WAM_ERR_IO = -6,       /* a checkpoint file could not be written, read or verified */
     WAM_WARN_NONMONOTONE = 1 /* reconstruction finished, but the cost rose

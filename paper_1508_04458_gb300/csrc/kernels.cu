@@ -4,9 +4,12 @@
 #include "wam_internal.cuh"
 #include "wam_kernels.h"
 
+#include <cuda.h>
 #include <math.h>
 
 #include <atomic>
+#include <mutex>
+#include <type_traits>
 
 namespace wam {
 
@@ -64,9 +67,10 @@ struct OpMax {
 // ---------------------------------------------------------------------------
 // The two apron-padded copies the pixel walk reads, on the grid of cells of
 // 2^lam x 2^lam pixels (mu constant on each cell; lam = 0: the pixels):
-// py = the cell values with a zero border ((ny + 2) rows of nx + 2, nx, ny
-// counted in cells), px = its transpose with a zero border ((nx + 2) rows of
-// ny + 2).  A cell's value is read at its first pixel; nxf is mu's row
+// py = the cell values with a zero border ((ny + 2) rows of nx + 2 used
+// elements at the stride pad_row(nx); nx, ny counted in cells), px = its
+// transpose with a zero border ((nx + 2) rows of ny + 2 at the stride
+// pad_row(ny)).  A cell's value is read at its first pixel; nxf is mu's row
 // length.  One thread per padded cell (x, y) in [-1, nx] x [-1, ny]; both
 // writes coalesced through a 32x32 shared tile.
 template <typename T>
@@ -80,12 +84,12 @@ __global__ void k_pad2(const T* __restrict__ mu, int nxf, int lam, int nx, int n
         T v = T(0);
         if (x >= 0 && x < nx && y >= 0 && y < ny) v = mu[((size_t)y << lam) * nxf + ((size_t)x << lam)];
         tile[k][threadIdx.x] = v;
-        if (x <= nx && y <= ny) py[(size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
+        if (x <= nx && y <= ny) py[(size_t)(y + 1) * pad_row(nx) + (x + 1)] = v;
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int y = y0 + threadIdx.x, x = x0 + k;
-        if (x <= nx && y <= ny) px[(size_t)(x + 1) * (ny + 2) + (y + 1)] = tile[threadIdx.x][k];
+        if (x <= nx && y <= ny) px[(size_t)(x + 1) * pad_row(ny) + (y + 1)] = tile[threadIdx.x][k];
     }
 }
 
@@ -121,6 +125,46 @@ __device__ __forceinline__ float cost_term(float2 dt, float d, float p, float q)
     return __fadd_rn(s2, __fadd_rn(__fadd_rn(dt.y, pl), __fadd_rn(e1, e2)));
 }
 
+// The epilogue of a ray's projection p = acc: p (optional), qhat = I0 e^-p,
+// the residual d - qhat (optional), and the ray's cost term.
+template <typename T>
+__device__ __forceinline__ CostAcc<T> forward_ray_out(const Geom<T>& g, int v, int b, T acc, const float* __restrict__ d,
+                                                      const typename CostTerm<T>::type* __restrict__ dterm,
+                                                      const float* __restrict__ I0, T* __restrict__ qhat,
+                                                      T* __restrict__ p_out, T* __restrict__ resid)
+{
+    CostAcc<T> term = 0;
+    const size_t y = (size_t)v * g.B + b;
+    if (p_out) p_out[y] = acc;
+    if (qhat || resid) {
+        const T q = T(I0[y]) * exp(-acc);
+        if (qhat) qhat[y] = q;
+        if (resid) resid[y] = T(d[y]) - q;   // dI/dp = d - q
+        // d log(d/q) - d + q = [d (log d - log I0) - d] + d p + q
+        term = cost_term(dterm[y], d[y], acc, q);
+    }
+    return term;
+}
+
+// One cost partial per CTA: warp sums, then the warps in a fixed order (a
+// CTA's slot frees only when its last warp ends, so the barrier costs no
+// occupancy).  Every thread of the CTA must call it.
+template <typename V>
+__device__ __forceinline__ void forward_cost_partial(V term, double* __restrict__ cost_part)
+{
+    if (!cost_part) return;
+    __shared__ V wsum[kFwdTPB / 32];
+    term = warp_reduce(term, OpSum());
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = term;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = wsum[0];
+#pragma unroll
+        for (int w = 1; w < kFwdTPB / 32; ++w) t += wsum[w];
+        cost_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
 template <typename T, bool PIX, bool WORK>
 __global__ void __launch_bounds__(kFwdTPB)
 k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
@@ -141,7 +185,7 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
                 // of the padded transpose.  Loads run one strip ahead of their
                 // use; the sum keeps the walk's order.
                 const bool ymaj = strip_major_y(g, r);
-                const T* img = ymaj ? pad : pad + (size_t)(g.nx + 2) * (g.ny + 2);
+                const T* img = ymaj ? pad : pad + (size_t)pad_row(g.nx) * (g.ny + 2);
                 T pca = T(0), pva = T(0), pcb = T(0), pvb = T(0);
                 traverse_strips(g, r, ymaj, [&](int la, T ca, int lb, T cb) {
                     const T va = __ldg(img + la), vb = __ldg(img + lb);
@@ -160,32 +204,279 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
                 });
             }
         }
-        const size_t y = (size_t)v * g.B + b;
-        if (p_out) p_out[y] = acc;
-        if (qhat || resid) {
-            const T q = T(I0[y]) * exp(-acc);
-            if (qhat) qhat[y] = q;
-            if (resid) resid[y] = T(d[y]) - q;   // dI/dp = d - q
-            // d log(d/q) - d + q = [d (log d - log I0) - d] + d p + q
-            term = cost_term(dterm[y], d[y], acc, q);
-        }
+        term = forward_ray_out(g, v, b, acc, d, dterm, I0, qhat, p_out, resid);
     }
     if (WORK) add_work(work, steps);
-    if (cost_part) {
-        // one partial per CTA: warp sums, then the warps in a fixed order (a
-        // CTA's slot frees only when its last warp ends, so the barrier costs
-        // no occupancy)
-        __shared__ CostAcc<T> wsum[kFwdTPB / 32];
-        term = warp_reduce(term, OpSum());
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = term;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = wsum[0];
-#pragma unroll
-            for (int w = 1; w < kFwdTPB / 32; ++w) t += wsum[w];
-            cost_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    forward_cost_partial(term, cost_part);
+}
+
+// ---------------------------------------------------------------------------
+// a2 + a3 with the image band staged in shared memory by the tensor memory
+// accelerator.  The 128 rays of a CTA (consecutive bins of one view) come
+// from one source (or are parallel), so they never cross inside the image:
+// at every strip of the walk their cells lie between those of the CTA's
+// first and last ray.  When all the CTA's rays share the walk's major axis,
+// the CTA copies its band kStageRows strips at a time (a window of
+// kStageCols cells, double buffered, one cp.async.bulk.tensor per stage on an
+// mbarrier) and every ray walks its strips of that stage from shared memory.
+// The walk, its chords and the order of its sums are those of
+// traverse_strips, so the result equals the unstaged kernel's bit for bit.
+// A ray's partial first and last strips are read from global memory, its
+// interior strips stage by stage; a ray whose columns in a stage would leave
+// the window reads that stage from global memory instead; CTAs with mixed
+// major axes, or bands wider than the window, walk global memory throughout.
+// Staging removes the long-scoreboard stalls of the unstaged walk (L1 misses
+// on the image rows) but adds per-stage bookkeeping; on the 512 x 512 scan
+// the two come out about even (a few per cent faster at full resolution).
+// ---------------------------------------------------------------------------
+constexpr int kStageRows = 24;               // 16 and 32 measured slower (per-stage work; occupancy)
+constexpr int kStageCols = 160;               // 640 B: a multiple of 16 B
+constexpr int kMaxStages = 64;                // bands of up to 1536 strips
+constexpr long long kWaitCycles = 1LL << 31;  // ~1 s at 2 GHz: a copy that takes longer is an error
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with this parity to complete, for at most kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// 2-D tile (x = column, y = row, in elements) of the tensor into shared memory.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <bool WORK>
+__global__ void __launch_bounds__(kFwdTPB, 10)
+k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_constant__ CUtensorMap tmy,
+                 const __grid_constant__ CUtensorMap tmx, const float* __restrict__ d,
+                 const float2* __restrict__ dterm, const float* __restrict__ I0, float* __restrict__ qhat,
+                 float* __restrict__ p_out, float* __restrict__ resid, double* __restrict__ cost_part,
+                 unsigned long long* __restrict__ work, int* __restrict__ err)
+{
+    __shared__ __align__(128) float buf[2][kStageRows * kStageCols];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_x0[kMaxStages];
+    __shared__ int s_jlo, s_jhi, s_staged;
+    __shared__ float s_line[2][2];            // (n0, slope) of the CTA's first and last ray
+
+    const int v = blockIdx.y;
+    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    const int bl = min(b, g.B - 1);           // rays past the last bin still give the band's edge
+    Ray<float> r;
+    const bool inside = make_ray(g, v, bl, r);
+    const bool hit = inside && b < g.B;
+    const bool ymaj = strip_major_y(g, r);
+    const int allY = __syncthreads_and(!hit || ymaj);
+    const int allX = __syncthreads_and(!hit || !ymaj);
+    const bool Y = allY ? true : (allX ? false : ymaj);
+    const bool uniform = allY || allX;
+
+    // the walk of traverse_strips, in the frame of the major axis
+    const float pm = Y ? r.py : r.px, pn = Y ? r.px : r.py;
+    const float dm = Y ? r.dy : r.dx, dn = Y ? r.dx : r.dy;
+    const float vm = Y ? g.vy : g.vx, vn = Y ? g.vx : g.vy;
+    const float ivm = Y ? g.ivy : g.ivx, ivn = Y ? g.ivx : g.ivy;
+    const float M0 = Y ? g.Y0 : g.X0, N0 = Y ? g.X0 : g.Y0;
+    const int nm = Y ? g.ny : g.nx, nn = Y ? g.nx : g.ny;
+    const float sec = fabsf(Y ? r.idy : r.idx);
+    const float vk = vn * fabsf(Y ? r.idx : r.idy);
+    const float slope = dn * (Y ? r.idy : r.idx);
+    const float s_in = pm + r.tin * dm, s_out = pm + r.tout * dm;
+    const float s_lo = fminf(s_in, s_out), s_hi = fmaxf(s_in, s_out);
+    const float n0 = pn - pm * slope;
+    const bool up = slope >= 0.0f;
+    const int j0 = clampi((int)floorf((s_lo - M0) * ivm), 0, nm - 1);
+    const int j1 = clampi((int)floorf((s_hi - M0) * ivm), 0, nm - 1);
+    const int c0 = clampi((int)floorf((fmaf(s_lo, slope, n0) - N0) * ivn), 0, nn - 1);
+    const float Nc = fmaf((float)c0, vn, N0);
+    const float G = fabsf(slope) * ivn;
+    const float U0 = (up ? n0 - Nc : Nc - n0) * ivn;
+    const int sM = pad_row(nn), dlin = up ? 1 : -1;
+    const float A = fmaf(G, M0, U0), D = G * vm;
+    const float full = vm * sec;
+    const float* img = Y ? pad : pad + (size_t)pad_row(g.nx) * (g.ny + 2);
+
+    if (threadIdx.x == 0) {
+        s_jlo = 1 << 30;
+        s_jhi = -1;
+        s_staged = uniform ? 1 : 0;
+    }
+    if (threadIdx.x == 0 || b == g.B - 1 || threadIdx.x == kFwdTPB - 1) {
+        // the band's edges: the CTA's first ray and its last ray within the scan
+        const int k = threadIdx.x == 0 ? 0 : 1;
+        if (k == 0 || b == g.B - 1 || (threadIdx.x == kFwdTPB - 1 && b < g.B)) {
+            s_line[k][0] = n0;
+            s_line[k][1] = slope;
         }
     }
+    __syncthreads();
+    if (hit) {
+        atomicMin(&s_jlo, j0);
+        atomicMax(&s_jhi, j1);
+    }
+    __syncthreads();
+    const int Jlo = s_jlo, Jhi = s_jhi;
+    const int nst = Jhi >= Jlo ? (Jhi - Jlo) / kStageRows + 1 : 0;
+    if (threadIdx.x < 32 && s_staged) {
+        // each stage's window: the cells of the two edge rays over its strips, 2 cells of margin
+        bool ok = nst <= kMaxStages;
+        for (int st = threadIdx.x; ok && st < nst; st += 32) {
+            const int ja = Jlo + st * kStageRows, jb = min(Jhi, ja + kStageRows - 1);
+            const float Ma = fmaf((float)ja, vm, M0), Mb = fmaf((float)(jb + 1), vm, M0);
+            float lo = 3e38f, hi = -3e38f;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float na = fmaf(Ma, s_line[k][1], s_line[k][0]), nb = fmaf(Mb, s_line[k][1], s_line[k][0]);
+                lo = fminf(lo, fminf(na, nb));
+                hi = fmaxf(hi, fmaxf(na, nb));
+            }
+            const float clo = fmaxf((lo - N0) * ivn, -8.0f), chi = fminf((hi - N0) * ivn, (float)nn + 8.0f);
+            const int x0 = ((int)floorf(clo) + 1 - 2) & ~3;              // padded column, 16-byte aligned
+            const int x1 = (int)floorf(chi) + 1 + 2;
+            if (x1 - x0 >= kStageCols) ok = false;
+            else s_x0[st] = x0;
+        }
+        if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) s_staged = 0;
+    }
+    if (threadIdx.x == 0 && s_staged && nst > 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const CUtensorMap* tm = Y ? &tmy : &tmx;
+        for (int st = 0; st < min(2, nst); ++st) {
+            mbar_expect_tx(&bar[st], kStageRows * kStageCols * sizeof(float));
+            tma_load_2d(buf[st], tm, s_x0[st], Jlo + st * kStageRows + 1, &bar[st]);
+        }
+    }
+    __syncthreads();
+    const bool staged = s_staged != 0;
+
+    float acc = 0.0f;
+    unsigned steps = 0;
+    // walk state: the padded column colp of the next strip's first cell, the
+    // next oriented minor grid line fbo
+    int colp = c0 + 1;
+    float fbo = up ? 1.0f : 0.0f;
+    auto strip = [&](const float* base, int rs, int& p, float chord, float u) {
+        const float e = u - fbo;
+        const bool cross = e >= 0.0f;
+        const float cb = cross ? fminf(e * vk, chord) : 0.0f;
+        const int pb = cross ? p + dlin : p;
+        const float ca = chord - cb;
+        acc += ca * base[p];
+        acc += cb * base[pb];
+        if (WORK) steps += (ca > 0.0f) + (cb > 0.0f);
+        fbo = cross ? fbo + 1.0f : fbo;
+        p = pb + rs;
+    };
+    // interior strips ja..jb (full chords) from base (row stride rs), p the
+    // index of strip ja's first cell; returns the index one row past jb
+    auto interior = [&](const float* base, int rs, int p, int ja, int jb) {
+        float fj = (float)ja;
+#pragma unroll 4
+        for (int jj = ja; jj <= jb; ++jj) {
+            fj += 1.0f;
+            strip(base, rs, p, full, fmaf(fj, D, A));
+        }
+        return p;
+    };
+    // the partial first strip (the whole walk when it is one strip), from global memory
+    if (hit) {
+        int p = (j0 + 1) * sM + colp;
+        if (j0 == j1) strip(img, sM, p, (s_hi - s_lo) * sec, fmaf(s_hi, G, U0));
+        else strip(img, sM, p, fmaxf(fmaf((float)(j0 + 1), vm, M0) - s_lo, 0.0f) * sec, fmaf((float)(j0 + 1), D, A));
+        colp = p - (j0 + 2) * sM;
+    }
+    const int i0 = j0 + 1, i1 = j1 - 1;          // the interior strips
+    if (!staged) {
+        if (hit && i0 <= i1) {
+            const int pe = interior(img, sM, (i0 + 1) * sM + colp, i0, i1);
+            colp = pe - (i1 + 2) * sM;
+        }
+    } else {
+        const CUtensorMap* tm = Y ? &tmy : &tmx;
+        int failed = -1;                      // the stage whose copy timed out
+        for (int st = 0; st < nst; ++st) {
+            const int bi = st & 1;
+            const int ra = Jlo + st * kStageRows, rb = min(Jhi, ra + kStageRows - 1);
+            const bool timed_out = !mbar_wait_bounded(&bar[bi], (st >> 1) & 1);
+            const int ja = max(i0, ra), jb = min(i1, rb);
+            if (hit && ja <= jb && !timed_out) {
+                // the columns this ray reaches in the stage: its column now and
+                // after the crossings up to strip jb (at most one per strip)
+                const int ncross = max(0, (int)floorf(fmaf((float)(jb + 1), D, A)) - (int)fbo + 1);
+                const int cend = colp + dlin * ncross;
+                const int x0 = s_x0[st];
+                if (min(colp, cend) - 2 >= x0 && max(colp, cend) + 2 < x0 + kStageCols) {
+                    const int pe = interior(buf[bi], kStageCols, (ja - ra) * kStageCols + (colp - x0), ja, jb);
+                    colp = pe - (jb + 1 - ra) * kStageCols + x0;
+                } else {
+                    const int pe = interior(img, sM, (ja + 1) * sM + colp, ja, jb);
+                    colp = pe - (jb + 2) * sM;
+                }
+            }
+            // the stage's barrier, and a vote that every thread takes alike
+            if (__syncthreads_or(timed_out)) {
+                failed = st;
+                break;
+            }
+            if (threadIdx.x == 0 && st + 2 < nst) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bar[bi], kStageRows * kStageCols * sizeof(float));
+                tma_load_2d(buf[bi], tm, s_x0[st + 2], Jlo + (st + 2) * kStageRows + 1, &bar[bi]);
+            }
+        }
+        if (failed >= 0 && threadIdx.x == 0) {
+            // record the failure; wait (bounded) for this CTA's copies still in
+            // flight, stages `failed` and failed + 1, before the CTA ends
+            atomicOr(err, 1);
+            for (int st = failed; st < min(nst, failed + 2); ++st) mbar_wait_bounded(&bar[st & 1], (st >> 1) & 1);
+        }
+    }
+    // the partial last strip, from global memory
+    if (hit && j1 > j0) {
+        int p = (j1 + 1) * sM + colp;
+        strip(img, sM, p, fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec, fmaf(s_hi, G, U0));
+    }
+    CostAcc<float> term = 0;
+    if (b < g.B) term = forward_ray_out(g, v, b, inside ? acc : 0.0f, d, dterm, I0, qhat, p_out, resid);
+    if (WORK) add_work(work, steps);
+    forward_cost_partial(term, cost_part);
 }
 
 // Sum n partials in a fixed order (one CTA of 256 threads).
@@ -911,12 +1202,12 @@ __global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf,
                            : (T)synth_at(lay, beta, ix, iy, leaf ? (int)leaf[(long long)iy * lay.nx + ix] : 0);
         }
         tile[k][threadIdx.x] = v;
-        if (x <= nx && y <= ny) py[(size_t)(y + 1) * (nx + 2) + (x + 1)] = v;
+        if (x <= nx && y <= ny) py[(size_t)(y + 1) * pad_row(nx) + (x + 1)] = v;
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int y = y0 + threadIdx.x, x = x0 + k;
-        if (x <= nx && y <= ny) px[(size_t)(x + 1) * (ny + 2) + (y + 1)] = tile[threadIdx.x][k];
+        if (x <= nx && y <= ny) px[(size_t)(x + 1) * pad_row(ny) + (y + 1)] = tile[threadIdx.x][k];
     }
 }
 
@@ -1177,6 +1468,95 @@ template cudaError_t launch_permute_rows<float>(const float*, float*, const int*
 template cudaError_t launch_permute_rows<double>(const double*, double*, const int*, int, int, cudaStream_t);
 template cudaError_t launch_permute_rows<float2>(const float2*, float2*, const int*, int, int, cudaStream_t);
 
+// ---- the staged forward's host side -----------------------------------------
+
+// Raised by a staged forward whose tensor copy did not complete in time; one
+// word per device, read and cleared by the driver after a reconstruction.
+__device__ int g_stage_err;
+
+int* stage_error_word()
+{
+    static int* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!addr[dev] && cudaGetSymbolAddress((void**)&addr[dev], g_stage_err) != cudaSuccess) {
+        cudaGetLastError();
+        addr[dev] = nullptr;
+    }
+    return addr[dev];
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The tensor map of one apron-padded copy: rows of `cols` used elements at
+// the stride pad_row(cols - 2), `rows` rows; tiles of kStageRows x kStageCols,
+// out-of-range elements read as zero.
+static bool pad_map(CUtensorMap* m, const float* base, int cols, int rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pad_row(cols - 2) * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)kStageRows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The strip walk over the padded copies in pad (cell grid gc): staged when the
+// tensor maps can be made, else from global memory.  FP32 only.
+template <typename T>
+static void launch_strip_walk(const Geom<T>& gc, T* pad, const float* d, const typename CostTerm<T>::type* dterm,
+                              const float* I0, T* qhat, T* p_out, T* resid, double* cost_part,
+                              unsigned long long* work, cudaStream_t st)
+{
+    const dim3 grid(nblk(gc.B, kFwdTPB), gc.V);
+    if constexpr (std::is_same<T, float>::value) {
+        CUtensorMap my, mx;
+        int* err = stage_error_word();
+        if (err && pad_map(&my, pad, gc.nx + 2, gc.ny + 2) &&
+            pad_map(&mx, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2), gc.ny + 2, gc.nx + 2)) {
+            COUNT_LAUNCH();
+            if (work)
+                k_forward_staged<true><<<grid, kFwdTPB, 0, st>>>(gc, pad, my, mx, d, dterm, I0, qhat, p_out, resid,
+                                                                cost_part, work, err);
+            else
+                k_forward_staged<false><<<grid, kFwdTPB, 0, st>>>(gc, pad, my, mx, d, dterm, I0, qhat, p_out, resid,
+                                                                 cost_part, work, err);
+            return;
+        }
+    }
+    COUNT_LAUNCH();
+    if (work)
+        k_forward<T, true, true><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out, resid,
+                                                           cost_part, work);
+    else
+        k_forward<T, true, false><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out,
+                                                            resid, cost_part, work);
+}
+
 template <typename T>
 cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t* leaf, int lam, const float* d,
                            const typename CostTerm<T>::type* dterm, const float* I0, T* qhat, T* p_out, T* resid,
@@ -1204,14 +1584,8 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
         gc.ivy = g.ivy / T(1 << lam);
         COUNT_LAUNCH();
         k_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
-            mu, g.nx, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
-        COUNT_LAUNCH();
-        if (work)
-            k_forward<T, true, true><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid,
-                                                               cost_part, work);
-        else
-            k_forward<T, true, false><<<grid, kFwdTPB, 0, st>>>(gc, mu, pad, leaf, d, dterm, I0, qhat, p_out,
-                                                                resid, cost_part, work);
+            mu, g.nx, lam, gc.nx, gc.ny, pad, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2));
+        launch_strip_walk(gc, pad, d, dterm, I0, qhat, p_out, resid, cost_part, work, st);
     }
     return cudaGetLastError();
 }
@@ -1233,15 +1607,8 @@ cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8
     gc.ivy = g.ivy / T(1 << lam);
     COUNT_LAUNCH();
     k_synth_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
-        lay, leaf, beta, lam, gc.nx, gc.ny, pad, pad + (size_t)(gc.nx + 2) * (gc.ny + 2));
-    COUNT_LAUNCH();
-    const dim3 grid(nblk(g.B, kFwdTPB), g.V);
-    if (work)
-        k_forward<T, true, true><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out,
-                                                           resid, cost_part, work);
-    else
-        k_forward<T, true, false><<<grid, kFwdTPB, 0, st>>>(gc, nullptr, pad, nullptr, d, dterm, I0, qhat, p_out,
-                                                            resid, cost_part, work);
+        lay, leaf, beta, lam, gc.nx, gc.ny, pad, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2));
+    launch_strip_walk(gc, pad, d, dterm, I0, qhat, p_out, resid, cost_part, work, st);
     return cudaGetLastError();
 }
 

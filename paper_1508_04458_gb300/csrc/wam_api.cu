@@ -142,8 +142,10 @@ const typename CostTerm<T>::type* dterm_buf(const wam_ctx* c)
 // (cone beam) copies.
 size_t pad_elems(const wam_ctx* c)
 {
-    const size_t nz2 = c->g.kind == WAM_CONE3D_FLAT_CIRCULAR ? (size_t)(c->g.nz + 2) : 1;
-    return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2) * nz2;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR)
+        return 2 * (size_t)(c->g.nx + 2) * (size_t)(c->g.ny + 2) * (size_t)(c->g.nz + 2);
+    // row-major copy (ny + 2 rows) and transposed copy (nx + 2 rows), rows at 16-byte strides
+    return (size_t)pad_row(c->g.nx) * (c->g.ny + 2) + (size_t)pad_row(c->g.ny) * (c->g.nx + 2);
 }
 
 // --- run state ---------------------------------------------------------------
@@ -1000,6 +1002,20 @@ struct Run {
     }
 };
 
+// A staged forward whose shared-memory copy did not complete within its wait
+// budget raised the device's stage-error word: the run's results are invalid.
+// Reads and clears the word (the stream has been synchronised).
+wam_status check_stage_error(wam_ctx* c)
+{
+    int* w = stage_error_word();
+    if (!w) return WAM_OK;
+    int v = 0;
+    WCK(c, cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v == 0) return WAM_OK;
+    WCK(c, cudaMemset(w, 0, sizeof(int)));
+    return fail(c, WAM_ERR_TIMEOUT, "a staged image copy of the forward projector did not complete in time");
+}
+
 // Iterations j0 .. J-1 of a run by tree epochs: the iterations between two
 // expansions launch the same kernels (the cost slot comes from the device
 // counter), so one of them is captured in a CUDA graph and the graph is
@@ -1080,6 +1096,7 @@ wam_status reconstruct_impl(wam_ctx* c, const wam_schedule* sc, void* mu_out, do
     std::vector<double> h;
     WST(run.copy_out(mu_out, hist, mask_out, on_device, &h, st));
     WCK(c, cudaStreamSynchronize(st));
+    WST(check_stage_error(c));
     if (c->prof || c->prof_work) WST(prof_resolve(c));
     record_run(c, sc, run.J, (int)run.next_exp);
     return run.monotone(h);
@@ -2253,6 +2270,8 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             cleanup();
             return fail(c0, WAM_ERR_CUDA, "synchronisation failed");
         }
+        s = check_stage_error(c0);
+        if (s != WAM_OK) { cleanup(); return s; }
         for (int i = 0; i < n; ++i) {
             record_run(ctxs[i], sc, J, (int)runs[i].next_exp);
             if (runs[i].monotone(hs[i]) != WAM_OK) ret = WAM_WARN_NONMONOTONE;

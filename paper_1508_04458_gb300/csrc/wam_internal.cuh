@@ -224,12 +224,18 @@ __device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& 
 // interior strips have the constant chord v_major / |d_major|.
 //
 // Pixels are addressed in an image with a one-pixel zero apron on every side,
-// (nm + 2) strips of (nn + 2): lin = (j + 1)(nn + 2) + (c + 1).  A step
+// (nm + 2) strips of sM = pad_row(nn): lin = (j + 1) sM + (c + 1).  A step
 // across the image's minor edge (possible only in the exit strip, where the
 // ray leaves through that edge) lands on the apron and reads 0, so the walk
 // needs no range test; the apron also keeps any index the walk can form
 // inside the allocation.  visit(la, ca, lb, cb) once per strip: first pixel
 // and chord, second pixel and chord (cb = 0, lb = la for a one-pixel strip).
+// Row length of an apron-padded copy with n cells per row: n + 2 rounded up
+// to a multiple of 4 elements, so that every row starts on a 16-byte
+// boundary (the tensor-memory-access copies of the staged forward need it).
+// The elements past n + 2 are never read by a walk.
+__host__ __device__ __forceinline__ int pad_row(int n) { return (n + 2 + 3) & ~3; }
+
 template <typename T>
 __device__ __forceinline__ bool strip_major_y(const Geom<T>& g, const Ray<T>& r)
 {
@@ -258,7 +264,7 @@ __device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& 
     const T Nc = fma(T(c0), vn, N0);                   // lower edge of the entry pixel
     const T G = fabs(slope) * ivn;                     // oriented minor units per unit major
     const T U0 = (up ? n0 - Nc : Nc - n0) * ivn;       // u at major 0
-    const int sM = nn + 2, dlin = up ? 1 : -1;
+    const int sM = pad_row(nn), dlin = up ? 1 : -1;
     T fbo = up ? T(1) : T(0);                          // next minor grid line, oriented
     int lin = (j0 + 1) * sM + c0 + 1;
     auto strip = [&](T chord, T u) {

@@ -98,6 +98,11 @@ cudaError_t launch_am_delta(int precision, long long n, const double* b, const d
                             const double* bhat, double lam, double z0, double clamp, double* delta, int* at_clamp,
                             cudaStream_t st);
 
+// Device word raised by a staged forward whose shared-memory copy did not
+// complete within its wait budget (then its results are invalid); null if
+// the word cannot be located on the current device.
+int* stage_error_word();
+
 unsigned long long kernel_launches();
 // kernels run by graph replays (counted once when captured)
 void add_launches(unsigned long long n);
