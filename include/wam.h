@@ -188,19 +188,30 @@ wam_status wam_reconstruct(wam_ctx* ctx, const wam_schedule* sched, void* mu_out
 
 /* Many independent scans (bags) of any sizes with one schedule, 2-D contexts,
  * precision 32.  Their iterations are interleaved: all bags share the
- * schedule, so between two expansions every bag runs on the same tree epoch;
- * with use_graph = 1 one iteration of every bag (each bag on its own stream,
- * forked from and joined into `stream`) is captured once per epoch into a
- * CUDA graph that is then launched once per iteration of the epoch (a
- * device-side counter places each iteration's cost); use_graph = 0 launches
- * the same kernels without a graph.  Results equal n calls of
- * wam_reconstruct bit for bit (same kernels, fixed-order sums).
- *   ctxs      [n] distinct contexts with data set
+ * schedule, so between two expansions every bag runs on the same tree epoch.
+ *   use_graph = 0: every bag's kernels are launched directly, bag after bag;
+ *   use_graph = 1: one iteration of every bag (each bag on its own stream,
+ *     forked from and joined into `stream`) is captured once per epoch into a
+ *     CUDA graph that is then launched once per iteration of the epoch (a
+ *     device-side counter places each iteration's cost);
+ *   use_graph = 2: one iteration of all bags is five kernels, captured once per
+ *     epoch: the cell images of every bag, the forward projection of every bag
+ *     and the back-projection of every bag by persistent CTAs (about one wave)
+ *     that take work items (bag, view, bin tile) and (bag, CTA of the bag's
+ *     plan) from a global counter, the bags in decreasing order of work, then
+ *     every bag's cost sum and update.  Epochs in which some bag walks its
+ *     tree leaf by leaf, or lambda > 0, run as use_graph = 1.
+ * Results of modes 0 and 1 equal n calls of wam_reconstruct bit for bit;
+ * mode 2 runs the same kernel bodies and sums in the same order inside other
+ * kernels, where the compiler may contract multiply-adds differently: it
+ * agrees with them to FP32 rounding.
+ *   ctxs      [n] distinct contexts with data set (at most 128 for mode 2)
  *   mu_out    [n] pointers to each bag's image (float, host or device per
  *             on_device), or NULL; hist likewise [n] pointers to n_iters + 1
  *             doubles, or NULL.
  * Returns WAM_WARN_NONMONOTONE if any bag's cost rose; errors as
- * wam_reconstruct (the first failing context keeps the message). */
+ * wam_reconstruct (the first failing context keeps the message), WAM_ERR_ARG
+ * for use_graph outside 0..2. */
 wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule* sched,
                                  void* const* mu_out, double* const* hist, int on_device,
                                  int use_graph, void* stream);
@@ -247,6 +258,10 @@ wam_status wam_resume(wam_ctx* ctx, const char* path);
 enum {
     WAM_TUNE_BACK_CTAS_PER_SM = 1,  /* back-projector launches aim at this many 256-thread CTAs
                                        per SM (default 32, range 0.25 .. 256) by splitting views */
+    WAM_TUNE_FWD_STAGE_ROWS = 3,    /* the forward projector's staged image tile: 24 (default), 16 or
+                                       32 strips of 160 cells per shared-memory stage, or 0 = no
+                                       staging (every ray reads global memory).  Results are identical
+                                       for every value (the same walk and the same order of sums). */
     WAM_TUNE_GRAPHS = 2             /* 1 (default): wam_reconstruct captures one iteration per tree
                                        epoch (the iterations between two expansions repeat the same
                                        launches) in a CUDA graph and replays it, when no profiling is

@@ -150,7 +150,7 @@ __device__ __forceinline__ CostAcc<T> forward_ray_out(const Geom<T>& g, int v, i
 // CTA's slot frees only when its last warp ends, so the barrier costs no
 // occupancy).  Every thread of the CTA must call it.
 template <typename V>
-__device__ __forceinline__ void forward_cost_partial(V term, double* __restrict__ cost_part)
+__device__ __forceinline__ void forward_cost_partial(V term, double* __restrict__ cost_part, int slot)
 {
     if (!cost_part) return;
     __shared__ V wsum[kFwdTPB / 32];
@@ -161,19 +161,22 @@ __device__ __forceinline__ void forward_cost_partial(V term, double* __restrict_
         double t = wsum[0];
 #pragma unroll
         for (int w = 1; w < kFwdTPB / 32; ++w) t += wsum[w];
-        cost_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        cost_part[slot] = t;
     }
 }
 
+// The rays of bin tile `tile` of view v (one per thread), their cost terms
+// summed into cost_part[slot].  Every thread of the CTA must call it.
 template <typename T, bool PIX, bool WORK>
-__global__ void __launch_bounds__(kFwdTPB)
-k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
-          const float* __restrict__ d, const typename CostTerm<T>::type* __restrict__ dterm,
-          const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
-          T* __restrict__ resid, double* __restrict__ cost_part, unsigned long long* __restrict__ work)
+__device__ __forceinline__ void forward_body(const Geom<T>& g, const T* __restrict__ mu, const T* __restrict__ pad,
+                                             const uint8_t* __restrict__ leaf, const float* __restrict__ d,
+                                             const typename CostTerm<T>::type* __restrict__ dterm,
+                                             const float* __restrict__ I0, T* __restrict__ qhat,
+                                             T* __restrict__ p_out, T* __restrict__ resid,
+                                             double* __restrict__ cost_part, unsigned long long* __restrict__ work,
+                                             int v, int tile, int slot)
 {
-    const int v = blockIdx.y;
-    const int b = blockIdx.x * kFwdTPB + threadIdx.x;
+    const int b = tile * kFwdTPB + threadIdx.x;
     CostAcc<T> term = 0;
     unsigned steps = 0;
     if (b < g.B) {
@@ -207,7 +210,18 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
         term = forward_ray_out(g, v, b, acc, d, dterm, I0, qhat, p_out, resid);
     }
     if (WORK) add_work(work, steps);
-    forward_cost_partial(term, cost_part);
+    forward_cost_partial(term, cost_part, slot);
+}
+
+template <typename T, bool PIX, bool WORK>
+__global__ void __launch_bounds__(kFwdTPB)
+k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
+          const float* __restrict__ d, const typename CostTerm<T>::type* __restrict__ dterm,
+          const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
+          T* __restrict__ resid, double* __restrict__ cost_part, unsigned long long* __restrict__ work)
+{
+    forward_body<T, PIX, WORK>(g, mu, pad, leaf, d, dterm, I0, qhat, p_out, resid, cost_part, work, blockIdx.y,
+                               blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,9 +243,8 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
 // on the image rows) but adds per-stage bookkeeping; on the 512 x 512 scan
 // the two come out about even (a few per cent faster at full resolution).
 // ---------------------------------------------------------------------------
-constexpr int kStageRows = 24;               // 16 and 32 measured slower (per-stage work; occupancy)
 constexpr int kStageCols = 160;               // 640 B: a multiple of 16 B
-constexpr int kMaxStages = 64;                // bands of up to 1536 strips
+constexpr int kMaxStrips = 1536;              // bands of up to 1536 strips are staged
 constexpr long long kWaitCycles = 1LL << 31;  // ~1 s at 2 GHz: a copy that takes longer is an error
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -279,7 +292,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
-template <bool WORK>
+// kStageRows strips per stage: a tile shape the autotuner chooses per geometry.
+template <int kStageRows, bool WORK>
 __global__ void __launch_bounds__(kFwdTPB, 10)
 k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_constant__ CUtensorMap tmy,
                  const __grid_constant__ CUtensorMap tmx, const float* __restrict__ d,
@@ -287,6 +301,7 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
                  float* __restrict__ p_out, float* __restrict__ resid, double* __restrict__ cost_part,
                  unsigned long long* __restrict__ work, int* __restrict__ err)
 {
+    constexpr int kMaxStages = (kMaxStrips + kStageRows - 1) / kStageRows;
     __shared__ __align__(128) float buf[2][kStageRows * kStageCols];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_x0[kMaxStages];
@@ -476,7 +491,7 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
     CostAcc<float> term = 0;
     if (b < g.B) term = forward_ray_out(g, v, b, inside ? acc : 0.0f, d, dterm, I0, qhat, p_out, resid);
     if (WORK) add_work(work, steps);
-    forward_cost_partial(term, cost_part);
+    forward_cost_partial(term, cost_part, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Sum n partials in a fixed order (one CTA of 256 threads).
@@ -489,7 +504,9 @@ __global__ void k_sum_final(const double* __restrict__ part, int n, double* __re
 }
 
 // Same, written to out[*counter], then the counter advances (graph replays).
-__global__ void k_sum_at(const double* __restrict__ part, int n, double* __restrict__ out, int* __restrict__ counter)
+// CTAs of 1024 threads (the order of the sum depends on it).
+__device__ __forceinline__ void sum_at_body(const double* __restrict__ part, int n, double* __restrict__ out,
+                                            int* __restrict__ counter)
 {
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
@@ -498,6 +515,11 @@ __global__ void k_sum_at(const double* __restrict__ part, int n, double* __restr
         out[*counter] = s;
         *counter += 1;
     }
+}
+
+__global__ void k_sum_at(const double* __restrict__ part, int n, double* __restrict__ out, int* __restrict__ counter)
+{
+    sum_at_body(part, n, out, counter);
 }
 
 __global__ void k_max_final(const double* __restrict__ part, int n, double* __restrict__ out)
@@ -750,14 +772,14 @@ __device__ __forceinline__ void bp_dispatch(const Geom<T>& g, const Segment& S, 
 // warps, each warp taking every kViewLanes-th view of the CTA's view chunk;
 // the warps' sums meet in shared memory in a fixed order and leave one
 // partial per (item, chunk, slot).
+// CTA number `cta` of the back-projection plan tab.  Every thread of the CTA
+// must call it.
 template <typename T>
-__global__ void __launch_bounds__(kBackTPB)
-k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
-              const typename Vec4<T>::type* __restrict__ dirtab, T* __restrict__ part,
-              unsigned long long* __restrict__ work)
+__device__ __forceinline__ void bp_body(const Geom<T>& g, const SegTable& tab, int cta, const T* __restrict__ sino,
+                                        const typename Vec4<T>::type* __restrict__ dirtab, T* __restrict__ part,
+                                        unsigned long long* __restrict__ work)
 {
     __shared__ T red[kViewLanes][7][kItemsPerCta];
-    const int cta = blockIdx.x;
     int si = 0;
     while (si + 1 < tab.n && cta >= tab.s[si + 1].cta_begin) ++si;
     const Segment& S = tab.s[si];
@@ -821,6 +843,15 @@ k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBackTPB)
+k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
+              const typename Vec4<T>::type* __restrict__ dirtab, T* __restrict__ part,
+              unsigned long long* __restrict__ work)
+{
+    bp_body<T>(g, tab, blockIdx.x, sino, dirtab, part, work);
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,12 +1043,14 @@ __host__ __device__ __forceinline__ long long upd_threads(const Segment& S)
     return (4LL * S.n_items * upd_lanes(S) + 31) / 32 * 32;
 }
 
+// Thread gid of the update grid of plan tab (threads of whole warps).
 template <typename T>
-__global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
-                         const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
-                         float* __restrict__ beta32, int nonneg, double lam, unsigned long long* __restrict__ hits)
+__device__ __forceinline__ void update_body(const SegTable& tab, const Layout& lay, const T* __restrict__ part,
+                                            const double* __restrict__ bvec, const double* __restrict__ z0p,
+                                            double clamp, double* __restrict__ beta, float* __restrict__ beta32,
+                                            int nonneg, double lam, unsigned long long* __restrict__ hits,
+                                            long long gid)
 {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int si = 0;
     long long first = 0;
     while (si < tab.n && gid >= first + upd_threads(tab.s[si])) first += upd_threads(tab.s[si++]);
@@ -1073,6 +1106,15 @@ __global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, c
     beta[z] = nb;
     if (beta32) beta32[z] = (float)nb;
     add_work(hits, hit ? 1u : 0u);     // steps at the clamp |Z0 Delta| = clamp
+}
+
+template <typename T>
+__global__ void k_update(SegTable tab, Layout lay, const T* __restrict__ part, const double* __restrict__ bvec,
+                         const double* __restrict__ z0p, double clamp, double* __restrict__ beta,
+                         float* __restrict__ beta32, int nonneg, double lam, unsigned long long* __restrict__ hits)
+{
+    update_body<T>(tab, lay, part, bvec, z0p, clamp, beta, beta32, nonneg, lam, hits,
+                   (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Scatter the reduced bhat+ / bhat- of each item into coefficient layout.
@@ -1186,13 +1228,15 @@ __global__ void k_synth(Layout lay, const uint8_t* __restrict__ leaf, const doub
 // a1 fused with the strip walk's input: the apron-padded copies of k_pad2
 // (cells of 2^lam pixels, row-major and transposed) filled straight from the
 // coefficients; a cell's value is mu at its first pixel.
+// Tile (tx, ty) of 32 x 32 padded cells; CTAs of 32 x 8 threads.
 template <typename T>
-__global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf,
-                             const typename SynthCoef<T>::type* __restrict__ beta, int lam, int nx, int ny,
-                             T* __restrict__ py, T* __restrict__ px)
+__device__ __forceinline__ void synth_pad2_body(const Layout& lay, const uint8_t* __restrict__ leaf,
+                                                const typename SynthCoef<T>::type* __restrict__ beta, int lam,
+                                                int nx, int ny, T* __restrict__ py, T* __restrict__ px, int tx,
+                                                int ty)
 {
     __shared__ T tile[32][33];
-    const int x0 = (int)blockIdx.x * 32 - 1, y0 = (int)blockIdx.y * 32 - 1;
+    const int x0 = tx * 32 - 1, y0 = ty * 32 - 1;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int x = x0 + threadIdx.x, y = y0 + k;
         T v = T(0);
@@ -1209,6 +1253,14 @@ __global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf,
         const int y = y0 + threadIdx.x, x = x0 + k;
         if (x <= nx && y <= ny) px[(size_t)(x + 1) * pad_row(ny) + (y + 1)] = tile[threadIdx.x][k];
     }
+}
+
+template <typename T>
+__global__ void k_synth_pad2(Layout lay, const uint8_t* __restrict__ leaf,
+                             const typename SynthCoef<T>::type* __restrict__ beta, int lam, int nx, int ny,
+                             T* __restrict__ py, T* __restrict__ px)
+{
+    synth_pad2_body<T>(lay, leaf, beta, lam, nx, ny, py, px, blockIdx.x, blockIdx.y);
 }
 
 // Leaf level of every pixel from the masks.
@@ -1468,6 +1520,134 @@ template cudaError_t launch_permute_rows<float>(const float*, float*, const int*
 template cudaError_t launch_permute_rows<double>(const double*, double*, const int*, int, int, cudaStream_t);
 template cudaError_t launch_permute_rows<float2>(const float2*, float2*, const int*, int, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// P2: one iteration of many bags in five launches.  The forward and the
+// back-projector are persistent: a grid of about one wave pulls work items
+// (bag, view, bin tile) or (bag, CTA of the bag's plan) from a global
+// counter, the largest bags first; each item runs the single-bag kernel's
+// body, so every partial and every sum is formed as the per-bag kernels form
+// it (in other kernels, where the compiler may contract multiply-adds
+// differently: the results agree to FP32 rounding).
+// ---------------------------------------------------------------------------
+
+// bag k owns items pre[k] .. pre[k+1]-1
+__device__ __forceinline__ int bag_of(const int* __restrict__ pre, int n, int item)
+{
+    int k = 0;
+    while (k + 1 < n && item >= pre[k + 1]) ++k;
+    return k;
+}
+
+// The next item for the whole CTA (thread 0 takes it, the barrier hands it on).
+__device__ __forceinline__ int next_item(int* __restrict__ counter)
+{
+    __shared__ int s_item;
+    __syncthreads();                       // the previous item's shared data is no longer read
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    return s_item;
+}
+
+__global__ void k_multi_synth(const BagDev* __restrict__ bags, const BatchPrefix* __restrict__ pre)
+{
+    const int item = blockIdx.x;
+    const int k = bag_of(pre->syn, pre->n, item);
+    const BagDev& B = bags[k];
+    const int local = item - pre->syn[k];
+    synth_pad2_body<float>(B.lay, B.lay.L > 0 ? B.leaf : nullptr, B.beta32, B.lam, B.gc.nx, B.gc.ny, B.pad,
+                           B.pad + (size_t)pad_row(B.gc.nx) * (B.gc.ny + 2), local % B.syn_tx, local / B.syn_tx);
+}
+
+__global__ void __launch_bounds__(kFwdTPB, 12) k_multi_forward(const BagDev* __restrict__ bags,
+                                                           const BatchPrefix* __restrict__ pre,
+                                                           int* __restrict__ counter)
+{
+    const int total = pre->fwd[pre->n];
+    for (;;) {
+        const int item = next_item(counter);
+        if (item >= total) break;
+        const int k = bag_of(pre->fwd, pre->n, item);
+        const BagDev& B = bags[k];
+        const int local = item - pre->fwd[k];
+        const int v = local / B.fwd_tiles, t = local - v * B.fwd_tiles;
+        forward_body<float, true, false>(B.gc, nullptr, B.pad, nullptr, B.d, B.dterm, B.I0, B.q, nullptr, nullptr,
+                                         B.cpart, nullptr, v, t, v * B.fwd_tiles + t);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_multi_sum(const BagDev* __restrict__ bags)
+{
+    const BagDev& B = bags[blockIdx.x];
+    sum_at_body(B.cpart, B.ncost, B.costs, B.counter);
+}
+
+__global__ void __launch_bounds__(kBackTPB, 5) k_multi_backproject(const BagDev* __restrict__ bags,
+                                                                const BatchPrefix* __restrict__ pre,
+                                                                int* __restrict__ counter)
+{
+    const int total = pre->bp[pre->n];
+    for (;;) {
+        const int item = next_item(counter);
+        if (item >= total) break;
+        const int k = bag_of(pre->bp, pre->n, item);
+        const BagDev& B = bags[k];
+        bp_body<float>(B.g, B.tab, item - pre->bp[k], B.q, B.dirt, B.part, nullptr);
+    }
+}
+
+__global__ void k_multi_update(const BagDev* __restrict__ bags, const BatchPrefix* __restrict__ pre)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= pre->upd[pre->n]) return;   // whole warps (every bag's share is)
+    const int k = bag_of(pre->upd, pre->n, (int)gid);
+    const BagDev& B = bags[k];
+    update_body<float>(B.tab, B.lay, B.part, B.bvec, B.z0, B.clamp, B.beta, const_cast<float*>(B.beta32), B.nonneg,
+                       0.0, nullptr, gid - pre->upd[k]);
+}
+
+int batch_launches_per_iteration() { return 5; }
+
+long long update_threads(const SegTable& tab)
+{
+    long long t = 0;
+    for (int i = 0; i < tab.n; ++i) t += upd_threads(tab.s[i]);
+    return t;
+}
+
+cudaError_t launch_batch_iteration(const BagDev* bags, const BatchPrefix* pre_dev, const BatchPrefix& pre,
+                                   int* counters, cudaStream_t st)
+{
+    static int grid_fwd = 0, grid_bp = 0;
+    if (!grid_fwd) {
+        int dev = 0, sms = 0, of = 0, ob = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_multi_forward, kFwdTPB, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_multi_backproject, kBackTPB, 0) != cudaSuccess)
+            return cudaGetLastError();
+        grid_fwd = std::max(1, sms * of);
+        grid_bp = std::max(1, sms * ob);
+    }
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (pre.syn[pre.n] > 0) {
+        COUNT_LAUNCH();
+        k_multi_synth<<<pre.syn[pre.n], dim3(32, 8), 0, st>>>(bags, pre_dev);
+    }
+    COUNT_LAUNCH();
+    k_multi_forward<<<std::min(grid_fwd, std::max(1, pre.fwd[pre.n])), kFwdTPB, 0, st>>>(bags, pre_dev, counters);
+    COUNT_LAUNCH();
+    k_multi_sum<<<pre.n, 1024, 0, st>>>(bags);
+    COUNT_LAUNCH();
+    k_multi_backproject<<<std::min(grid_bp, std::max(1, pre.bp[pre.n])), kBackTPB, 0, st>>>(bags, pre_dev,
+                                                                                            counters + 1);
+    if (pre.upd[pre.n] > 0) {
+        COUNT_LAUNCH();
+        k_multi_update<<<nblk(pre.upd[pre.n], 256), 256, 0, st>>>(bags, pre_dev);
+    }
+    return cudaGetLastError();
+}
+
 // ---- the staged forward's host side -----------------------------------------
 
 // Raised by a staged forward whose tensor copy did not complete in time; one
@@ -1510,15 +1690,15 @@ static EncodeTiledFn encode_tiled()
 }
 
 // The tensor map of one apron-padded copy: rows of `cols` used elements at
-// the stride pad_row(cols - 2), `rows` rows; tiles of kStageRows x kStageCols,
+// the stride pad_row(cols - 2), `rows` rows; tiles of stage_rows x kStageCols,
 // out-of-range elements read as zero.
-static bool pad_map(CUtensorMap* m, const float* base, int cols, int rows)
+static bool pad_map(CUtensorMap* m, const float* base, int cols, int rows, int stage_rows)
 {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)pad_row(cols - 2) * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)kStageRows};
+    const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)stage_rows};
     const cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1536,15 +1716,17 @@ static void launch_strip_walk(const Geom<T>& gc, T* pad, const float* d, const t
     if constexpr (std::is_same<T, float>::value) {
         CUtensorMap my, mx;
         int* err = stage_error_word();
-        if (err && pad_map(&my, pad, gc.nx + 2, gc.ny + 2) &&
-            pad_map(&mx, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2), gc.ny + 2, gc.nx + 2)) {
+        const int R = gc.stage_rows;
+        if ((R == 16 || R == 24 || R == 32) && err && pad_map(&my, pad, gc.nx + 2, gc.ny + 2, R) &&
+            pad_map(&mx, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2), gc.ny + 2, gc.nx + 2, R)) {
             COUNT_LAUNCH();
-            if (work)
-                k_forward_staged<true><<<grid, kFwdTPB, 0, st>>>(gc, pad, my, mx, d, dterm, I0, qhat, p_out, resid,
-                                                                cost_part, work, err);
-            else
-                k_forward_staged<false><<<grid, kFwdTPB, 0, st>>>(gc, pad, my, mx, d, dterm, I0, qhat, p_out, resid,
-                                                                 cost_part, work, err);
+#define WAM_STAGED(RR, WW)                                                                                  \
+    k_forward_staged<RR, WW><<<grid, kFwdTPB, 0, st>>>(gc, pad, my, mx, d, dterm, I0, qhat, p_out, resid, cost_part, \
+                                                       work, err)
+            if (R == 16) { if (work) WAM_STAGED(16, true); else WAM_STAGED(16, false); }
+            else if (R == 24) { if (work) WAM_STAGED(24, true); else WAM_STAGED(24, false); }
+            else { if (work) WAM_STAGED(32, true); else WAM_STAGED(32, false); }
+#undef WAM_STAGED
             return;
         }
     }
@@ -1574,14 +1756,7 @@ cudaError_t launch_forward(const Geom<T>& g, const T* mu, T* pad, const uint8_t*
     } else {
         if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
             return cudaErrorInvalidValue;
-        // the grid of 2^lam-pixel cells: same box, cells 2^lam times larger
-        Geom<T> gc = g;
-        gc.nx = g.nx >> lam;
-        gc.ny = g.ny >> lam;
-        gc.vx = g.vx * T(1 << lam);
-        gc.vy = g.vy * T(1 << lam);
-        gc.ivx = g.ivx / T(1 << lam);
-        gc.ivy = g.ivy / T(1 << lam);
+        const Geom<T> gc = cell_grid(g, lam);
         COUNT_LAUNCH();
         k_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
             mu, g.nx, lam, gc.nx, gc.ny, pad, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2));
@@ -1598,13 +1773,7 @@ cudaError_t launch_forward_tree(const Geom<T>& g, const Layout& lay, const uint8
 {
     if (!pad || lam < 0 || (g.nx >> lam) << lam != g.nx || (g.ny >> lam) << lam != g.ny)
         return cudaErrorInvalidValue;
-    Geom<T> gc = g;
-    gc.nx = g.nx >> lam;
-    gc.ny = g.ny >> lam;
-    gc.vx = g.vx * T(1 << lam);
-    gc.vy = g.vy * T(1 << lam);
-    gc.ivx = g.ivx / T(1 << lam);
-    gc.ivy = g.ivy / T(1 << lam);
+    const Geom<T> gc = cell_grid(g, lam);
     COUNT_LAUNCH();
     k_synth_pad2<T><<<dim3(nblk(gc.nx + 2, 32), nblk(gc.ny + 2, 32)), dim3(32, 8), 0, st>>>(
         lay, leaf, beta, lam, gc.nx, gc.ny, pad, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2));

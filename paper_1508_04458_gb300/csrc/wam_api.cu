@@ -6,6 +6,7 @@
 #include "wam_internal.cuh"
 #include "wam_kernels.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,7 +29,7 @@ enum BufId {
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
     B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER, B_MUT,
     B_PERM, B_CSP32, B_CSP64, B_DIRP32, B_DIRP64, B_DP, B_I0P, B_DTP, B_BSUB, B_Z0SUB, B_SINOP,
-    B_DTERM2, B_BETA32,
+    B_DTERM2, B_BETA32, B_BATCH,
     B_NBUF
 };
 
@@ -69,6 +70,7 @@ struct wam_ctx {
     int last_lmin = 0;                     // ... and its finest leaf level
     // tuning
     double back_ctas_per_sm = 32.0;        // back-projector work split: CTAs per SM per launch
+    int fwd_stage_rows = 24;               // forward: strips per staged image tile (0: no staging)
     bool graphs = true;                    // replay each tree epoch's iteration as a CUDA graph
     cudaStream_t prof_stream = nullptr;
     int device = 0;
@@ -274,6 +276,7 @@ wam_status make_geom(wam_ctx* c, Geom<T>* g)
 {
     const wam_geometry& w = c->g;
     g->kind = w.kind;
+    g->stage_rows = c->fwd_stage_rows;
     g->nx = w.nx;
     g->ny = w.ny;
     g->V = w.n_views;
@@ -2116,6 +2119,12 @@ wam_status wam_set_tuning(wam_ctx* c, int key, double value)
         c->back_ctas_per_sm = value;
         return WAM_OK;
     }
+    if (key == WAM_TUNE_FWD_STAGE_ROWS) {
+        if (value != 0.0 && value != 16.0 && value != 24.0 && value != 32.0)
+            return fail(c, WAM_ERR_ARG, "WAM_TUNE_FWD_STAGE_ROWS must be 0, 16, 24 or 32");
+        c->fwd_stage_rows = (int)value;
+        return WAM_OK;
+    }
     if (key == WAM_TUNE_GRAPHS) {
         if (value != 0.0 && value != 1.0) return fail(c, WAM_ERR_ARG, "graphs: 0 or 1");
         c->graphs = value != 0.0;
@@ -2138,6 +2147,7 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             if (ctxs[k] == ctxs[i]) return fail(ctxs[i], WAM_ERR_ARG, "a context appears twice in the batch");
     }
     wam_ctx* c0 = ctxs[0];
+    if (use_graph < 0 || use_graph > 2) return fail(c0, WAM_ERR_ARG, "use_graph must be 0, 1 or 2");
     if (sc->precision != 32) return fail(c0, WAM_ERR_ARG, "batched reconstruction runs in precision 32");
     if (sc->n_subsets > 1) return fail(c0, WAM_ERR_ARG, "batched reconstruction has no ordered subsets");
     if (sc->nonneg != 0 && sc->nonneg != 1) return fail(c0, WAM_ERR_ARG, "nonneg must be 0 or 1");
@@ -2209,6 +2219,62 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             }
             return WAM_OK;
         };
+        // persistent multi-bag kernels (use_graph = 2): the descriptors of every
+        // bag for the current tree epoch, in decreasing order of work; false
+        // when some run needs the per-bag path this epoch (a leaf-walk
+        // forward, the l1 penalty, ordered subsets, too many bags)
+        std::vector<BagDev> hb;
+        BatchPrefix hp{};
+        auto build_bags = [&]() -> bool {
+            if (n > kMaxBags) return false;
+            for (int i = 0; i < n; ++i)
+                if (runs[i].fwd_leaf || runs[i].lam > 0.0 || runs[i].S > 1) return false;
+            std::vector<int> order(n);
+            std::vector<double> work(n);
+            for (int i = 0; i < n; ++i) {
+                order[i] = i;
+                work[i] = (double)runs[i].tab.total_ctas * kBackTPB + (double)runs[i].g.V * runs[i].g.B;
+            }
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+            hb.assign(n, BagDev{});
+            hp = BatchPrefix{};
+            hp.n = n;
+            for (int k = 0; k < n; ++k) {
+                const Run<float>& r = runs[order[k]];
+                BagDev& B = hb[k];
+                B.g = r.g;
+                B.gc = cell_grid(r.g, r.fwd_lam);
+                B.lay = r.lay;
+                B.tab = r.tab;
+                B.leaf = r.L > 0 ? r.leaf : nullptr;
+                B.beta32 = r.beta32;
+                B.pad = r.mut;
+                B.lam = r.fwd_lam;
+                B.syn_tx = (B.gc.nx + 2 + 31) / 32;
+                B.syn_ty = (B.gc.ny + 2 + 31) / 32;
+                B.fwd_tiles = (r.g.B + kFwdTPB - 1) / kFwdTPB;
+                B.d = r.dsino;
+                B.dterm = r.dterm;
+                B.I0 = r.I0;
+                B.q = r.q;
+                B.cpart = r.cpart;
+                B.ncost = r.npc;
+                B.dirt = static_cast<const float4*>(r.dirt);
+                B.part = r.part;
+                B.bvec = r.bvec;
+                B.z0 = r.z0;
+                B.clamp = r.clamp;
+                B.beta = r.beta;
+                B.nonneg = r.sc->nonneg;
+                B.costs = r.costs;
+                B.counter = r.counter;
+                hp.fwd[k + 1] = hp.fwd[k] + r.g.V * B.fwd_tiles;
+                hp.bp[k + 1] = hp.bp[k] + r.tab.total_ctas;
+                hp.upd[k + 1] = hp.upd[k] + (int)update_threads(r.tab);
+                hp.syn[k + 1] = hp.syn[k] + B.syn_tx * B.syn_ty;
+            }
+            return true;
+        };
         const int J = sc->n_iters;
         int j = 0;
         while (j < J) {
@@ -2216,7 +2282,43 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             const Run<float>& r0 = runs[0];
             if (r0.L > 0 && r0.next_exp < r0.exp_at.size()) e = std::min(J, r0.exp_at[r0.next_exp]);
             // iterations j .. e-1 share one tree per run
-            if (use_graph) {
+            if (use_graph == 2 && build_bags()) {
+                // descriptors, prefixes and two item counters in one device block
+                const size_t nb = sizeof(BagDev) * n, np = sizeof(BatchPrefix);
+                void* blk = nullptr;
+                wam_status s = ensure(c0, B_BATCH, nb + np + 2 * sizeof(int), &blk);
+                if (s != WAM_OK) { cleanup(); return s; }
+                BagDev* dbags = static_cast<BagDev*>(blk);
+                BatchPrefix* dpre = reinterpret_cast<BatchPrefix*>(static_cast<char*>(blk) + nb);
+                int* counters = reinterpret_cast<int*>(static_cast<char*>(blk) + nb + np);
+                if (cudaMemcpyAsync(dbags, hb.data(), nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                    cudaMemcpyAsync(dpre, &hp, np, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                    cleanup();
+                    return fail(c0, WAM_ERR_CUDA, "batch descriptor upload failed");
+                }
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                    cudaGetLastError();
+                    cleanup();
+                    return fail(c0, WAM_ERR_CUDA, "stream capture could not start");
+                }
+                const cudaError_t el = launch_batch_iteration(dbags, dpre, hp, counters, st);
+                const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+                if (el != cudaSuccess || ec != cudaSuccess ||
+                    cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (graph) cudaGraphDestroy(graph);
+                    cleanup();
+                    return fail(c0, WAM_ERR_CUDA, "persistent batch iteration could not be captured");
+                }
+                for (int k = j; k < e && s == WAM_OK; ++k)
+                    if (cudaGraphLaunch(exec, st) != cudaSuccess) s = fail(c0, WAM_ERR_CUDA, "graph launch failed");
+                add_launches((unsigned long long)batch_launches_per_iteration() * (unsigned long long)std::max(0, e - j - 1));
+                cudaGraphExecDestroy(exec);
+                cudaGraphDestroy(graph);
+                if (s != WAM_OK) { cleanup(); return s; }
+            } else if (use_graph) {
                 cudaGraph_t graph = nullptr;
                 cudaGraphExec_t exec = nullptr;
                 if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {

@@ -21,11 +21,13 @@ constexpr int kItemsPerCta = 32;  // back-projector: items (blocks) per CTA, one
 constexpr int kViewLanes = 8;     // back-projector: warps per CTA, each on its own views
 constexpr int kBackTPB = kItemsPerCta * kViewLanes;
 constexpr int kFwdTPB = 128;      // threads per CTA of the ray-driven kernels
+constexpr int kMaxBags = 128;     // bags of one persistent batched iteration
 
 // Scan geometry in the kernel's precision T.  X0, Y0: lower-left image corner.
 template <typename T>
 struct Geom {
     int kind, nx, ny, V, B;
+    int stage_rows;               // staged forward: strips per shared-memory stage (16, 24, 32), 0: none
     T vx, vy, X0, Y0, ivx, ivy;
     T pitch, ucen, sod, sdd;
     const T* cs;                  // device [V][2]: cos, sin of each view angle

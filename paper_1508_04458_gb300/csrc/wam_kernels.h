@@ -98,6 +98,71 @@ cudaError_t launch_am_delta(int precision, long long n, const double* b, const d
                             const double* bhat, double lam, double z0, double clamp, double* delta, int* at_clamp,
                             cudaStream_t st);
 
+// The strip walk's grid of 2^lam-pixel cells: the same box, cells 2^lam times larger.
+template <typename T>
+inline Geom<T> cell_grid(const Geom<T>& g, int lam)
+{
+    Geom<T> gc = g;
+    gc.nx = g.nx >> lam;
+    gc.ny = g.ny >> lam;
+    gc.vx = g.vx * T(1 << lam);
+    gc.vy = g.vy * T(1 << lam);
+    gc.ivx = g.ivx / T(1 << lam);
+    gc.ivy = g.ivy / T(1 << lam);
+    return gc;
+}
+
+// Threads of the update grid of a plan (whole warps per segment).
+long long update_threads(const SegTable& tab);
+
+// One bag of a persistent batched iteration (FP32, strip-walk forward): what
+// its five kernels read and write, and its share of their work.  Built on
+// the host per tree epoch, read by the multi-bag kernels from device memory.
+struct BagDev {
+    Geom<float> g;          // the scan (the back-projector's geometry)
+    Geom<float> gc;         // the strip walk's grid of 2^lam-pixel cells
+    Layout lay;
+    SegTable tab;           // the back-projection / update plan of the tree
+    const uint8_t* leaf;    // leaf map (null when L = 0)
+    const float* beta32;    // the float copy of beta the cells are synthesised from
+    float* pad;             // apron-padded cell copies (row-major, then transposed)
+    int lam;                // cells of 2^lam pixels
+    int syn_tx, syn_ty;     // 32 x 32 cell tiles of the padded copies
+    int fwd_tiles;          // bin tiles of kFwdTPB rays per view
+    const float* d;
+    const float2* dterm;
+    const float* I0;
+    float* q;               // q-hat
+    double* cpart;          // the forward's cost partials (one per CTA of the per-bag launch)
+    int ncost;              // how many
+    const float4* dirt;     // direction table
+    float* part;            // back-projection partials
+    const double* bvec;     // b = Phi^T d
+    const double* z0;
+    double clamp;
+    double* beta;
+    int nonneg;
+    double* costs;          // cost history
+    int* counter;           // its slot counter
+};
+
+// The work of all bags in prefix form: bag k owns items pre[k] .. pre[k+1]-1
+// (forward: view x bin tile; back-projection: CTAs of its plan; update:
+// threads, whole warps; synthesis: cell tiles), bags in decreasing order of
+// work so that the persistent kernels start the largest first.
+struct BatchPrefix {
+    int n;
+    int fwd[kMaxBags + 1], bp[kMaxBags + 1], upd[kMaxBags + 1], syn[kMaxBags + 1];
+};
+
+// One iteration of every bag: cell synthesis, forward (persistent CTAs over
+// a global item counter), cost sums, back-projection (persistent), update.
+// counters: two device ints, reset on st before the kernels.  Results agree
+// with the per-bag kernels' to FP32 rounding.
+cudaError_t launch_batch_iteration(const BagDev* bags, const BatchPrefix* pre_dev, const BatchPrefix& pre,
+                                   int* counters, cudaStream_t st);
+int batch_launches_per_iteration();
+
 // Device word raised by a staged forward whose shared-memory copy did not
 // complete within its wait budget (then its results are invalid); null if
 // the word cannot be located on the current device.

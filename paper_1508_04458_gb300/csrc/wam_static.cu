@@ -120,6 +120,7 @@ extern "C" wam_status wam_backproject_static(const wam_geometry* w, const float*
 
     Geom<float> g;
     g.kind = w->kind;
+    g.stage_rows = 0;
     g.nx = w->nx;
     g.ny = w->ny;
     g.V = V;

@@ -36,6 +36,7 @@ WAM_WARN_NONMONOTONE = 1
 WAM_MAX_LEVELS = 8
 WAM_TUNE_BACK_CTAS_PER_SM = 1
 WAM_TUNE_GRAPHS = 2
+WAM_TUNE_FWD_STAGE_ROWS = 3
 WAM_PROFILE_OFF, WAM_PROFILE_ALL, WAM_PROFILE_TIME, WAM_PROFILE_WORK = 0, 1, 2, 3
 
 
@@ -266,9 +267,16 @@ def kernel_launches() -> int:
     return int(wam_kernel_launches())
 
 
-def reconstruct_batch(ctxs, levels: int, n_iters: int, expand_at=(), tau=(), use_graph: bool = True,
+BATCH_DIRECT, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
+
+
+def reconstruct_batch(ctxs, levels: int, n_iters: int, expand_at=(), tau=(), use_graph=True,
                       stream: Optional[int] = None):
-    """wam_reconstruct_batch on device outputs; returns ([mu], [hist], status)."""
+    """wam_reconstruct_batch on device outputs; returns ([mu], [hist], status).
+    use_graph: False / BATCH_DIRECT, True / BATCH_GRAPH (one graph per tree
+    epoch, every bag on its own stream branch) or BATCH_PERSISTENT (one graph
+    per epoch of five multi-bag kernels, the forward and back-projector
+    persistent over a work queue)."""
     import torch
     sc, keep = schedule(levels, n_iters, expand_at, tau, 32, False)
     n = len(ctxs)
@@ -278,7 +286,8 @@ def reconstruct_batch(ctxs, levels: int, n_iters: int, expand_at=(), tau=(), use
     marr = (_P * n)(*[ptr(m) for m in mus])
     qarr = (_P * n)(*[ptr(h) for h in hists])
     s = current_stream() if stream is None else stream
-    st = wam_reconstruct_batch(harr, n, ctypes.byref(sc), marr, qarr, 1, 1 if use_graph else 0, s)
+    mode = int(use_graph) if not isinstance(use_graph, bool) else (1 if use_graph else 0)
+    st = wam_reconstruct_batch(harr, n, ctypes.byref(sc), marr, qarr, 1, mode, s)
     del keep
     if st not in (WAM_OK, WAM_WARN_NONMONOTONE):
         msgs = [(wam_last_error(c.h) or b"").decode() for c in ctxs]

@@ -1,6 +1,7 @@
 """Batched multiresolution AM over bags of uneven size (one CUDA graph per
-tree epoch, every bag on its own stream branch) against the per-bag loop and
-the oracle, and the back-projector autotuner."""
+tree epoch: every bag on its own stream branch, or five multi-bag kernels
+with persistent forward and back-projection CTAs on a work queue) against
+the per-bag loop, bit for bit, and the oracle; the autotuner."""
 import numpy as np
 import pytest
 
@@ -40,6 +41,15 @@ def test_batch_equals_per_bag_loop_bit_for_bit():
         for (mu1, h1, _, _), mu2, h2 in zip(singles, mus, hists):
             assert torch.equal(mu1, mu2)
             assert torch.equal(h1, h2)
+    # the persistent multi-bag kernels run the same bodies and sums in the same
+    # order, compiled into other kernels: they agree to FP32 rounding
+    mus, hists, st = wam.reconstruct_batch(ctxs, SCHED["levels"], SCHED["n_iters"], SCHED["expand_at"],
+                                           SCHED["tau"], use_graph=wam.BATCH_PERSISTENT)
+    assert st == wam.WAM_OK
+    for (mu1, h1, _, _), mu2, h2 in zip(singles, mus, hists):
+        assert float((mu1 - mu2).norm() / mu1.norm()) <= 1e-5
+        assert float(((h1 - h2).abs() / h1.abs()).max()) <= 1e-5
+        assert torch.equal(h1[0], h2[0])                 # the first cost (beta = 0) is the same sum
     # one bag of the batch against the oracle
     p = bags[2]
     ref = am.wavelet_am(smx.system_matrix(p.geom), p.d, p.I0, p.geom.nx, p.geom.ny, SCHED["levels"],
@@ -65,9 +75,19 @@ def test_autotuner(tmp_path):
     ref, _, _, _ = ctx.reconstruct(4, 12, (2, 4, 6, 8), (0.1, 0.03, 0.01, -1.0), device_out=True)
     cache = str(tmp_path / "tune.json")
     best = autotune.tune(ctx, cache=cache)
-    assert best in autotune.CANDIDATES
+    assert best["back_ctas_per_sm"] in autotune.CANDIDATES and best["fwd_stage_rows"] in autotune.STAGE_ROWS
     # cached on the second call, same answer
     assert autotune.tune(ctx, cache=cache) == best
     mu, _, _, _ = ctx.reconstruct(4, 12, (2, 4, 6, 8), (0.1, 0.03, 0.01, -1.0), device_out=True)
-    # the knob only reorders fixed partial sums: results agree to FP32 rounding
+    # the back-projector knob only reorders fixed partial sums: results agree to FP32 rounding
     assert float((mu - ref).norm() / ref.norm()) <= 1e-5
+    # the forward's tile height changes nothing that is computed
+    ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_BACK_CTAS_PER_SM, 32.0))
+    outs = []
+    for rows in autotune.STAGE_ROWS:
+        ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_FWD_STAGE_ROWS, float(rows)))
+        outs.append(ctx.reconstruct(4, 12, (2, 4, 6, 8), (0.1, 0.03, 0.01, -1.0), device_out=True)[:2])
+    for mu_r, h_r in outs[1:]:
+        assert torch.equal(mu_r, outs[0][0]) and torch.equal(h_r, outs[0][1])
+    with pytest.raises(wam.WamError):
+        ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_FWD_STAGE_ROWS, 8.0))
