@@ -294,6 +294,13 @@ def run_wam(args, problem, world, rank, local_rank):
     ctx = wam.Context(g)
     d_dev = torch.from_numpy(problem.d.astype(np.float32).ravel()).to(dev)
     ctx.set_data(d_dev, problem.I0)
+    # the tile shapes for this geometry class (the autotuner's cached choice)
+    tuned = None
+    if not args.no_tune:
+        from paper_1508_04458_gb300 import autotune
+        cache = os.path.join(ROOT, "_build", "tune.json")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuned = autotune.tune(ctx, cache=cache)
 
     def step(n_iters=N_ITERS, levels=L_LEVELS, full=False, n_subsets=1):
         return ctx.reconstruct(levels, n_iters, () if full else EXPAND_AT, () if full else TAU,
@@ -501,7 +508,8 @@ def run_wam(args, problem, world, rank, local_rank):
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps,
             "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64"),
+            "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64",
+                           tile_shapes=tuned),
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
             "roofline": roofline, "cpu_baseline": cpu, "err_vs_oracle": err_vs_oracle,
             "multires": {"final_idiv": float(hist_mr[-1]), "ms_per_iter": dev_ms_max / args.steps / N_ITERS,

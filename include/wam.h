@@ -258,10 +258,12 @@ wam_status wam_resume(wam_ctx* ctx, const char* path);
 enum {
     WAM_TUNE_BACK_CTAS_PER_SM = 1,  /* back-projector launches aim at this many 256-thread CTAs
                                        per SM (default 32, range 0.25 .. 256) by splitting views */
-    WAM_TUNE_FWD_STAGE_ROWS = 3,    /* the forward projector's staged image tile: 24 (default), 16 or
-                                       32 strips of 160 cells per shared-memory stage, or 0 = no
-                                       staging (every ray reads global memory).  Results are identical
-                                       for every value (the same walk and the same order of sums). */
+    WAM_TUNE_FWD_STAGE_ROWS = 3,    /* the forward projector's staged image tile: 16, 24 or 32 strips
+                                       of 160 cells per shared-memory stage (copied by the tensor
+                                       memory accelerator), or 0 (default) = no staging, every ray
+                                       reads global memory.  Results are identical for every value
+                                       (the same walk and the same order of sums); which is faster
+                                       depends on the geometry (an autotuner picks it). */
     WAM_TUNE_GRAPHS = 2             /* 1 (default): wam_reconstruct captures one iteration per tree
                                        epoch (the iterations between two expansions repeat the same
                                        launches) in a CUDA graph and replays it, when no profiling is

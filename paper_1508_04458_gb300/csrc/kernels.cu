@@ -240,8 +240,10 @@ k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const 
 // the window reads that stage from global memory instead; CTAs with mixed
 // major axes, or bands wider than the window, walk global memory throughout.
 // Staging removes the long-scoreboard stalls of the unstaged walk (L1 misses
-// on the image rows) but adds per-stage bookkeeping; on the 512 x 512 scan
-// the two come out about even (a few per cent faster at full resolution).
+// on the image rows) but adds per-stage bookkeeping and holds 21-41 KB of
+// shared memory per CTA; on the 512 x 512 scan the two come out about even,
+// on scans whose bands overflow the window it is slower, so it is a tuning
+// choice per geometry (off by default).
 // ---------------------------------------------------------------------------
 constexpr int kStageCols = 160;               // 640 B: a multiple of 16 B
 constexpr int kMaxStrips = 1536;              // bands of up to 1536 strips are staged
@@ -1538,14 +1540,26 @@ __device__ __forceinline__ int bag_of(const int* __restrict__ pre, int n, int it
     return k;
 }
 
-// The next item for the whole CTA (thread 0 takes it, the barrier hands it on).
-__device__ __forceinline__ int next_item(int* __restrict__ counter)
+// A CTA's walk over the work queue: thread 0 takes the next item from the
+// counter while the CTA works on the current one (the atomic's latency
+// overlaps the work), and a barrier hands it on.  body(item) must contain a
+// CTA barrier after its last read of shared memory.
+template <typename F>
+__device__ __forceinline__ void for_each_item(int* __restrict__ counter, int total, F&& body)
 {
     __shared__ int s_item;
-    __syncthreads();                       // the previous item's shared data is no longer read
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
-    return s_item;
+    int cur = s_item;
+    while (cur < total) {
+        int nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(counter, 1);
+        body(cur);
+        __syncthreads();                   // every thread has read s_item and finished the item
+        if (threadIdx.x == 0) s_item = nxt;
+        __syncthreads();
+        cur = s_item;
+    }
 }
 
 __global__ void k_multi_synth(const BagDev* __restrict__ bags, const BatchPrefix* __restrict__ pre)
@@ -1558,21 +1572,18 @@ __global__ void k_multi_synth(const BagDev* __restrict__ bags, const BatchPrefix
                            B.pad + (size_t)pad_row(B.gc.nx) * (B.gc.ny + 2), local % B.syn_tx, local / B.syn_tx);
 }
 
-__global__ void __launch_bounds__(kFwdTPB, 12) k_multi_forward(const BagDev* __restrict__ bags,
+__global__ void __launch_bounds__(kFwdTPB) k_multi_forward(const BagDev* __restrict__ bags,
                                                            const BatchPrefix* __restrict__ pre,
                                                            int* __restrict__ counter)
 {
-    const int total = pre->fwd[pre->n];
-    for (;;) {
-        const int item = next_item(counter);
-        if (item >= total) break;
+    for_each_item(counter, pre->fwd[pre->n], [&](int item) {
         const int k = bag_of(pre->fwd, pre->n, item);
         const BagDev& B = bags[k];
         const int local = item - pre->fwd[k];
         const int v = local / B.fwd_tiles, t = local - v * B.fwd_tiles;
         forward_body<float, true, false>(B.gc, nullptr, B.pad, nullptr, B.d, B.dterm, B.I0, B.q, nullptr, nullptr,
                                          B.cpart, nullptr, v, t, v * B.fwd_tiles + t);
-    }
+    });
 }
 
 __global__ void __launch_bounds__(1024) k_multi_sum(const BagDev* __restrict__ bags)
@@ -1581,18 +1592,15 @@ __global__ void __launch_bounds__(1024) k_multi_sum(const BagDev* __restrict__ b
     sum_at_body(B.cpart, B.ncost, B.costs, B.counter);
 }
 
-__global__ void __launch_bounds__(kBackTPB, 5) k_multi_backproject(const BagDev* __restrict__ bags,
+__global__ void __launch_bounds__(kBackTPB) k_multi_backproject(const BagDev* __restrict__ bags,
                                                                 const BatchPrefix* __restrict__ pre,
                                                                 int* __restrict__ counter)
 {
-    const int total = pre->bp[pre->n];
-    for (;;) {
-        const int item = next_item(counter);
-        if (item >= total) break;
+    for_each_item(counter, pre->bp[pre->n], [&](int item) {
         const int k = bag_of(pre->bp, pre->n, item);
         const BagDev& B = bags[k];
         bp_body<float>(B.g, B.tab, item - pre->bp[k], B.q, B.dirt, B.part, nullptr);
-    }
+    });
 }
 
 __global__ void k_multi_update(const BagDev* __restrict__ bags, const BatchPrefix* __restrict__ pre)

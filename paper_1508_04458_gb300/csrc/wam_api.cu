@@ -70,7 +70,7 @@ struct wam_ctx {
     int last_lmin = 0;                     // ... and its finest leaf level
     // tuning
     double back_ctas_per_sm = 32.0;        // back-projector work split: CTAs per SM per launch
-    int fwd_stage_rows = 24;               // forward: strips per staged image tile (0: no staging)
+    int fwd_stage_rows = 0;                // forward: strips per staged image tile (0: no staging)
     bool graphs = true;                    // replay each tree epoch's iteration as a CUDA graph
     cudaStream_t prof_stream = nullptr;
     int device = 0;

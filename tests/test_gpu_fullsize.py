@@ -6,11 +6,13 @@ outputs and against properties that hold at any size:
 * H^T s on 48 sampled pixels (the oracle builds H in chunks of 60 views and
   keeps the sampled columns);
 * Algorithm 1 with the benchmark's schedule (L = 4, 100 iterations,
-  expansions after 8, 16, 32, 64 with tau 0.1, 0.03, 0.01, every leaf): a
+  expansions after 8, 16, 32, 64 with tau 0.1, 0.03, 0.01, every leaf),
+  with the forward's image band staged in shared memory or not: a
   finite, non-increasing I-divergence history (each AM step minimises a
   separable majoriser, Eq. 1.8-1.9, so the exact cost cannot rise; the FP32
   projections allow a 1e-6 relative rise), a valid tree, and bit-identical
-  results on a second run (every reduction has a fixed order).
+  results on a second run (every reduction has a fixed order) and with
+  every staged tile height.
 
 FP32 bounds as in the small-case parity tests: max <= 1e-4 and RMS <= 1e-5 of
 the largest reference entry.  At this size the rays that graze a pixel edge
@@ -85,6 +87,13 @@ def test_fan512_multires_schedule():
     assert st == wam.WAM_OK
     mu2, h2, m2, _ = ctx.reconstruct(*sched, precision=32, device_out=True)
     assert torch.equal(mu1, mu2) and torch.equal(h1, h2) and torch.equal(m1, m2)
+    # the forward with its image band staged in shared memory (every tile
+    # height) walks and sums exactly as the unstaged one
+    for rows in (16, 24, 32):
+        ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_FWD_STAGE_ROWS, float(rows)))
+        mu3, h3, m3, _ = ctx.reconstruct(*sched, precision=32, device_out=True)
+        assert torch.equal(mu1, mu3) and torch.equal(h1, h3) and torch.equal(m1, m3), rows
+    ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_FWD_STAGE_ROWS, 0.0))
     h = h1.cpu().numpy()
     assert np.all(np.isfinite(h))
     assert np.all(h[1:] <= h[:-1] * (1 + 1e-6)), np.max(h[1:] / h[:-1])
