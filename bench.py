@@ -42,7 +42,8 @@ TTT_MAX_ITERS = 300                 # multires iterations allowed to reach the t
 def workload_config():
     """The benchmark workload, the same for the GPU arm and the reference arm."""
     return {"workload": WORKLOAD, "levels": L_LEVELS, "iterations": N_ITERS, "expand_after": list(EXPAND_AT),
-            "tau": list(TAU), "seed": 1509}
+            "tau": list(TAU), "seed": 1509, "l2": "flushed between steps (256 MiB write)",
+            "cost_precision": "f64"}
 K_MIN = 10                          # FP32 instructions per ray-rectangle intersection (floor)
 
 
@@ -508,8 +509,7 @@ def run_wam(args, problem, world, rank, local_rank):
             "warmup": max(3, args.warmup), "ms_per_step": dev_ms_max / args.steps,
             "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(), l2="flushed between steps (256 MiB write)", cost_precision="f64",
-                           tile_shapes=tuned),
+            "config": workload_config(), "tile_shapes": tuned,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
             "roofline": roofline, "cpu_baseline": cpu, "err_vs_oracle": err_vs_oracle,
             "multires": {"final_idiv": float(hist_mr[-1]), "ms_per_iter": dev_ms_max / args.steps / N_ITERS,
