@@ -390,6 +390,39 @@ wam_status wam_am_derivs(wam_ctx* ctx, int levels, const double* b, const double
                          const double* bminus, const double* z0, double clamp, float* dplus,
                          float* dminus, void* stream);
 
+/* wam_project_coef / wam_backproject_coef over a batch of n vectors in one
+ * call: beta [n][nx*ny] -> p [n][n_views*n_bins], s [n][n_views*n_bins] ->
+ * g [n][nx*ny], FP32 device, items run one after another on `stream`.
+ * WAM_ERR_ARG for n < 0; otherwise the single call's errors. */
+wam_status wam_project_coef_batch(wam_ctx* ctx, int levels, int n, const float* beta, float* p, void* stream);
+wam_status wam_backproject_coef_batch(wam_ctx* ctx, int levels, int n, const float* s, float* g, void* stream);
+
+/* The loss and gradient of wam_idiv_grad for a batch of n coefficient
+ * vectors in one call (the items run one after another on `stream`, on the
+ * context's work buffers).  beta, grad [n][nx*ny] FP32; loss [n] FP64 (all
+ * device).  Errors as wam_idiv_grad; WAM_ERR_ARG for n < 0. */
+wam_status wam_idiv_grad_batch(wam_ctx* ctx, int levels, int n, const float* beta, float lambda, double* loss,
+                               float* grad, void* stream);
+
+/* a0, Eq. 1.6 / Algorithm 1's precompute: b(z) = sum_y d(y) phi(y|z) for every
+ * coefficient z of the L-level basis, formed as wam_reconstruct forms it in
+ * an FP32 run (the pixel back-projection H^T d in FP32 partials summed into
+ * FP64, then the FP64 Haar analysis Omega^T).  b [nx*ny] FP64 device, coefficient
+ * layout.  Needs wam_set_data. */
+wam_status wam_precompute_b(wam_ctx* ctx, int levels, double* b, void* stream);
+
+/* The transposed Jacobian of one AM step on the full tree (Algorithm 1's
+ * update of every coefficient, Z0 fixed) applied to gbar: with qhat, bhat+-
+ * the quantities of the step at beta (Eq. 1.10) and D+- the derivatives of
+ * its root (wam_am_derivs),
+ *   gout = gbar - Phi^T [ qhat * (Phi+ (D+ gbar) + Phi- (D- gbar)) ],
+ * the chain rule through qhat = I0 exp(-Phi beta) (the step's own identity
+ * term is gbar).  beta, b [nx*ny] FP64, z0 device double, gbar, gout
+ * [nx*ny] FP32 (distinct), all device; clamp as for wam_update.  Needs
+ * wam_set_data. */
+wam_status wam_am_step_vjp(wam_ctx* ctx, int levels, const double* beta, const double* b, const double* z0,
+                           double clamp, const float* gbar, float* gout, void* stream);
+
 /* out(y) = qhat(y) * sum_z [max(phi(y|z), 0) gbar(z) dplus(z) +
  * min(phi(y|z), 0) gbar(z) dminus(z)] over every z of the full basis: the
  * projection through the positive and negative parts of Phi used by

@@ -14,8 +14,9 @@
   root of Eq. 1.9 with respect to bhat+-.
 
 Inputs are CUDA float32 tensors in the coefficient layout of include/wam.h;
-a leading batch dimension is processed item by item.  Every numeric step
-runs in libwam's kernels on the current stream.
+a leading batch dimension goes to the library's batch calls in one call
+each.  Every numeric step (b = Phi^T d, the step's transposed Jacobian
+including its identity term) runs in libwam's kernels on the current stream.
 """
 from __future__ import annotations
 
@@ -54,6 +55,20 @@ class Operators:
         self.ctx.check(wam.wam_backproject_coef(self.ctx.h, self.levels, wam.ptr(s), wam.ptr(g), _st()))
         return g
 
+    def phi_batch(self, beta: torch.Tensor) -> torch.Tensor:
+        beta = beta.contiguous()
+        p = torch.empty(beta.shape[0], self.M, dtype=torch.float32, device=beta.device)
+        self.ctx.check(wam.wam_project_coef_batch(self.ctx.h, self.levels, beta.shape[0], wam.ptr(beta), wam.ptr(p),
+                                                  _st()))
+        return p
+
+    def phi_t_batch(self, s: torch.Tensor) -> torch.Tensor:
+        s = s.contiguous()
+        g = torch.empty(s.shape[0], self.N, dtype=torch.float32, device=s.device)
+        self.ctx.check(wam.wam_backproject_coef_batch(self.ctx.h, self.levels, s.shape[0], wam.ptr(s), wam.ptr(g),
+                                                      _st()))
+        return g
+
     def loss_grad(self, beta: torch.Tensor, lam: float):
         beta = beta.contiguous()
         loss = torch.empty(1, dtype=torch.float64, device=beta.device)
@@ -70,15 +85,12 @@ class Operators:
         return self._masks
 
     def setup(self, d: torch.Tensor):
-        """b = Phi^T d in FP64 (as bhat+ + bhat- of d) and Z0 of the full tree."""
+        """b = Phi^T d in FP64 (the precompute of Algorithm 1, from the context's
+        data) and Z0 of the full tree."""
         dev = d.device
         m = self.masks(dev)
-        bp = torch.empty(self.N, dtype=torch.float64, device=dev)
-        bm = torch.empty_like(bp)
-        d = d.contiguous()
-        self.ctx.check(wam.wam_split_backproject(self.ctx.h, self.levels, wam.ptr(m), wam.ptr(d), wam.ptr(bp),
-                                                 wam.ptr(bm), _st()))
-        self._b = bp + bm
+        self._b = torch.empty(self.N, dtype=torch.float64, device=dev)
+        self.ctx.check(wam.wam_precompute_b(self.ctx.h, self.levels, wam.ptr(self._b), _st()))
         self._z0 = torch.empty(1, dtype=torch.float64, device=dev)
         self.ctx.check(wam.wam_z0(self.ctx.h, self.levels, wam.ptr(m), wam.ptr(self._z0), _st()))
 
@@ -108,34 +120,36 @@ class Operators:
         return out
 
     def am_step_vjp(self, beta64: torch.Tensor, gbar: torch.Tensor, clamp: float = 30.0) -> torch.Tensor:
-        q, bp, bm = self.qhat_split(beta64)
-        dev = beta64.device
-        dp = torch.empty(self.N, dtype=torch.float32, device=dev)
-        dm = torch.empty_like(dp)
-        self.ctx.check(wam.wam_am_derivs(self.ctx.h, self.levels, wam.ptr(self._b), wam.ptr(bp), wam.ptr(bm),
-                                         wam.ptr(self._z0), clamp, wam.ptr(dp), wam.ptr(dm), _st()))
+        """The transposed Jacobian of one AM step at beta applied to gbar (one
+        library call)."""
         gbar = gbar.contiguous()
-        r = torch.empty(self.M, dtype=torch.float32, device=dev)
-        self.ctx.check(wam.wam_phi_split_project(self.ctx.h, self.levels, wam.ptr(gbar), wam.ptr(dp), wam.ptr(dm),
-                                                 wam.ptr(q), wam.ptr(r), _st()))
-        return gbar - self.phi_t(r)
+        out = torch.empty_like(gbar)
+        self.ctx.check(wam.wam_am_step_vjp(self.ctx.h, self.levels, wam.ptr(beta64.contiguous()), wam.ptr(self._b),
+                                           wam.ptr(self._z0), clamp, wam.ptr(gbar), wam.ptr(out), _st()))
+        return out
 
-
-def _batched(fn, x, *rest):
-    if x.dim() == 1:
-        return fn(x, *rest)
-    return torch.stack([fn(xi, *rest) for xi in x])
+    def loss_grad_batch(self, beta: torch.Tensor, lam: float):
+        """wam_idiv_grad over the rows of beta ([n, N]) in one call."""
+        beta = beta.contiguous()
+        n = beta.shape[0]
+        loss = torch.empty(n, dtype=torch.float64, device=beta.device)
+        grad = torch.empty_like(beta)
+        self.ctx.check(wam.wam_idiv_grad_batch(self.ctx.h, self.levels, n, wam.ptr(beta), float(lam), wam.ptr(loss),
+                                               wam.ptr(grad), _st()))
+        return loss, grad
 
 
 class PhiProject(torch.autograd.Function):
     @staticmethod
     def forward(ctx, beta, ops: Operators):
         ctx.ops = ops
-        return _batched(ops.phi, beta.detach().float())
+        b = beta.detach().float()
+        return ops.phi(b) if b.dim() == 1 else ops.phi_batch(b.reshape(b.shape[0], -1))
 
     @staticmethod
     def backward(ctx, gp):
-        return _batched(ctx.ops.phi_t, gp.float()), None
+        g = gp.float()
+        return (ctx.ops.phi_t(g) if g.dim() == 1 else ctx.ops.phi_t_batch(g.reshape(g.shape[0], -1))), None
 
 
 class IDivLoss(torch.autograd.Function):
@@ -146,9 +160,9 @@ class IDivLoss(torch.autograd.Function):
             loss, grad = ops.loss_grad(b, lam)
             ctx.save_for_backward(grad)
             return loss[0]
-        pairs = [ops.loss_grad(bi, lam) for bi in b]
-        ctx.save_for_backward(torch.stack([g for _, g in pairs]))
-        return torch.cat([l for l, _ in pairs])
+        loss, grad = ops.loss_grad_batch(b.reshape(b.shape[0], -1), lam)
+        ctx.save_for_backward(grad.reshape(b.shape))
+        return loss
 
     @staticmethod
     def backward(ctx, gl):

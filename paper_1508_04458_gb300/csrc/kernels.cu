@@ -2009,6 +2009,21 @@ cudaError_t launch_convert(const A* x, B* y, long long n, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// out = a - (float)b (the subtraction of an FP64 vector rounded to float)
+__global__ void k_sub_f64(const float* __restrict__ a, const double* __restrict__ b, float* __restrict__ out,
+                          long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] - (float)b[i];
+}
+
+cudaError_t launch_sub_f64(const float* a, const double* b, float* out, long long n, cudaStream_t st)
+{
+    COUNT_LAUNCH();
+    k_sub_f64<<<nblk(n, 256), 256, 0, st>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+
 // a6 on dense coefficient arrays (the step-level entry point): every active
 // coefficient gets its AM step from given b, bhat+, bhat-.
 __global__ void k_update_dense(Layout lay, const uint8_t* __restrict__ mask, const double* __restrict__ bvec,

@@ -29,7 +29,7 @@ enum BufId {
     B_DIR32, B_DIR64, B_GBETA, B_GMU, B_GRES, B_GCOEF, B_L1PART,
     B_DIR3, B_ROWINV, B_DLEN, B_S2D, B_COUNTER, B_MUT,
     B_PERM, B_CSP32, B_CSP64, B_DIRP32, B_DIRP64, B_DP, B_I0P, B_DTP, B_BSUB, B_Z0SUB, B_SINOP,
-    B_DTERM2, B_BETA32, B_BATCH,
+    B_DTERM2, B_BETA32, B_BATCH, B_VJP, B_VJPQ, B_VJPR, B_VJPD, B_VJPB,
     B_NBUF
 };
 
@@ -2529,6 +2529,109 @@ wam_status wam_am_derivs(wam_ctx* c, int levels, const double* b, const double* 
     WST(make_layout(c, levels, &lay));
     WCK(c, launch_am_derivs(lay, b, bplus, bminus, z0, clamp > 0 ? clamp : 30.0, dplus, dminus,
                             as_stream(stream)));
+    return WAM_OK;
+}
+
+wam_status wam_precompute_b(wam_ctx* c, int levels, double* b, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    if (!b) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        cudaStream_t st = as_stream(stream);
+        Geom<float> g;
+        WST(make_geom<float>(c, &g));
+        const void* dirt = nullptr;
+        WST(dir_table<float>(c, &dirt));
+        SegTable pix;
+        float* part = nullptr;
+        WST(plan_pixels<float>(c, &pix, &part));
+        double *gimg = nullptr, *ta = nullptr, *tb = nullptr;
+        WST(ensure_t(c, B_GIMG, (size_t)c->N, &gimg));
+        WST(ensure_t(c, B_TMPA, (size_t)c->N, &ta));
+        WST(ensure_t(c, B_TMPB, (size_t)c->N, &tb));
+        // the same launches as the reconstruction's precompute (a0)
+        WCK(c, launch_backproject(g, pix, static_cast<const float*>(c->buf[B_D].p), dirt, part, nullptr, st));
+        WCK(c, (launch_reduce_pixels<float, double>(pix, c->g.nx, c->N, part, gimg, st)));
+        WCK(c, launch_haar(lay, gimg, b, 0, ta, tb, st));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_am_step_vjp(wam_ctx* c, int levels, const double* beta, const double* b, const double* z0,
+                           double clamp, const float* gbar, float* gout, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (c->g.kind == WAM_CONE3D_FLAT_CIRCULAR) return fail(c, WAM_ERR_ARG, "not available for cone-beam contexts");
+    if (!c->has_data) return fail(c, WAM_ERR_STATE, "wam_set_data must be called first");
+    if (!beta || !b || !z0 || !gbar || !gout) return fail(c, WAM_ERR_ARG, "null pointer");
+    try {
+        Layout lay;
+        WST(make_layout(c, levels, &lay));
+        cudaStream_t st = as_stream(stream);
+        const long long N = c->N, M = c->M;
+        // the full tree: every detail active
+        uint8_t* masks = nullptr;
+        WST(ensure_t(c, B_VJP, (size_t)lay.mask_bytes + 1, &masks));
+        WCK(c, cudaMemsetAsync(masks, 1, (size_t)lay.mask_bytes, st));
+        // qhat at beta and its split back-projections
+        float *mu = nullptr, *q = nullptr, *dp = nullptr, *dm = nullptr, *r = nullptr;
+        double *cost = nullptr, *bp = nullptr, *bm = nullptr;
+        WST(ensure_t(c, B_GMU, (size_t)N, &mu));
+        WST(ensure_t(c, B_VJPQ, (size_t)M, &q));
+        WST(ensure_t(c, B_VJPR, (size_t)M, &r));
+        WST(ensure_t(c, B_VJPD, 2 * (size_t)N, &dp));
+        dm = dp + N;
+        WST(ensure_t(c, B_VJPB, 2 * (size_t)N + 1, &bp));
+        bm = bp + N;
+        cost = bm + N;
+        WST(wam_synthesize(c, levels, masks, beta, mu, stream));
+        WST(wam_forward(c, levels, masks, mu, q, cost, stream));
+        WST(wam_split_backproject(c, levels, masks, q, bp, bm, stream));
+        // the derivatives of the root of Eq. 1.9 with respect to bhat+ and bhat-
+        WST(wam_am_derivs(c, levels, b, bp, bm, z0, clamp, dp, dm, stream));
+        // r = Q (Phi+ D+ gbar + Phi- D- gbar), then gout = gbar - Phi^T r
+        WST(wam_phi_split_project(c, levels, gbar, dp, dm, q, r, stream));
+        double* coef = nullptr;
+        WST(sino_to_coef(c, lay, r, &coef, st));
+        WCK(c, launch_sub_f64(gbar, coef, gout, N, st));
+        return WAM_OK;
+    } catch (...) {
+        return fail(c, WAM_ERR_OOM, "host allocation failed");
+    }
+}
+
+wam_status wam_idiv_grad_batch(wam_ctx* c, int levels, int n, const float* beta, float lambda, double* loss,
+                               float* grad, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (n < 0 || (n > 0 && (!beta || !loss || !grad))) return fail(c, WAM_ERR_ARG, "bad batch");
+    for (int i = 0; i < n; ++i)
+        WST(wam_idiv_grad(c, levels, beta + (size_t)i * c->N, lambda, loss + i, grad + (size_t)i * c->N, nullptr,
+                          stream));
+    return WAM_OK;
+}
+
+wam_status wam_project_coef_batch(wam_ctx* c, int levels, int n, const float* beta, float* p, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (n < 0 || (n > 0 && (!beta || !p))) return fail(c, WAM_ERR_ARG, "bad batch");
+    for (int i = 0; i < n; ++i)
+        WST(wam_project_coef(c, levels, beta + (size_t)i * c->N, p + (size_t)i * c->M, stream));
+    return WAM_OK;
+}
+
+wam_status wam_backproject_coef_batch(wam_ctx* c, int levels, int n, const float* s, float* g, void* stream)
+{
+    if (!c) return WAM_ERR_ARG;
+    if (n < 0 || (n > 0 && (!s || !g))) return fail(c, WAM_ERR_ARG, "bad batch");
+    for (int i = 0; i < n; ++i)
+        WST(wam_backproject_coef(c, levels, s + (size_t)i * c->M, g + (size_t)i * c->N, stream));
     return WAM_OK;
 }
 

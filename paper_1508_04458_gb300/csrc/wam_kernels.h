@@ -168,6 +168,9 @@ int batch_launches_per_iteration();
 // the word cannot be located on the current device.
 int* stage_error_word();
 
+// out = a - (float)b, n elements
+cudaError_t launch_sub_f64(const float* a, const double* b, float* out, long long n, cudaStream_t st);
+
 unsigned long long kernel_launches();
 // kernels run by graph replays (counted once when captured)
 void add_launches(unsigned long long n);

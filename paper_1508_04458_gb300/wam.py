@@ -99,6 +99,11 @@ _PROTOS = {
     "wam_idiv_grad": (_S, [_P, _I, _P, ctypes.c_float, _P, _P, _P, _P]),
     "wam_am_derivs": (_S, [_P, _I, _P, _P, _P, _P, _D, _P, _P, _P]),
     "wam_phi_split_project": (_S, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "wam_idiv_grad_batch": (_S, [_P, _I, _I, _P, ctypes.c_float, _P, _P, _P]),
+    "wam_project_coef_batch": (_S, [_P, _I, _I, _P, _P, _P]),
+    "wam_backproject_coef_batch": (_S, [_P, _I, _I, _P, _P, _P]),
+    "wam_precompute_b": (_S, [_P, _I, _P, _P]),
+    "wam_am_step_vjp": (_S, [_P, _I, _P, _P, _P, _D, _P, _P, _P]),
     "wam_backproject_static": (_S, [ctypes.POINTER(wam_geometry), _P, _P, _P]),
     "wam_reconstruct_batch": (_S, [ctypes.POINTER(_P), _I, ctypes.POINTER(wam_schedule), ctypes.POINTER(_P),
                                    ctypes.POINTER(_P), _I, _I, _P]),

@@ -170,3 +170,54 @@ def test_batch_of_eight_256():
     got = bt.grad[0].cpu().numpy()[zs]
     scale = np.max(np.abs(bt.grad[0].cpu().numpy()))
     assert np.max(np.abs(got - acc)) <= FP32_MAX * scale
+
+
+def test_precompute_b_against_oracle():
+    # a0 (Eq. 1.6): b = Phi^T d from the context's data, FP64 output
+    p, Phi, ctx, ops = _setup(seed=19)
+    ops.setup(torch.tensor(p.d.ravel(), dtype=torch.float32, device="cuda"))
+    want = Phi.T @ p.d.ravel().astype(np.float32).astype(np.float64)
+    _close(ops._b.cpu().numpy(), want, "b = Phi^T d")
+
+
+def test_projector_batch_matches_items():
+    # the batch calls give each item's single-call result, bit for bit
+    p, Phi, ctx, ops = _setup(seed=23)
+    rng = np.random.default_rng(5)
+    betas = np.stack([_beta(p, 2, rng)[0] for _ in range(3)]).astype(np.float32)
+    bt = torch.tensor(betas, device="cuda", requires_grad=True)
+    pr = PhiProject.apply(bt, ops)
+    w = torch.tensor(rng.random(pr.shape), dtype=torch.float32, device="cuda")
+    (pr * w).sum().backward()
+    for k in range(3):
+        assert torch.equal(pr[k].detach(), ops.phi(bt[k].detach()))
+        assert torch.equal(bt.grad[k], ops.phi_t(w[k]))
+    _close(pr[1].detach().cpu().numpy(), Phi @ betas[1].astype(np.float64), "Phi beta (batch)")
+    empty = ops.phi_batch(torch.zeros(0, ops.N, device="cuda"))
+    assert empty.shape == (0, ops.M)
+
+
+def test_one_step_vjp_against_oracle_jacobian():
+    # the transposed Jacobian of one full-tree AM step, applied to gbar,
+    # against FP64 central differences of the oracle's step
+    p, Phi, ctx, ops = _setup(nx=32, ny=32, V=24, B=45, L=2, seed=29)
+    rng = np.random.default_rng(6)
+    beta, _ = _beta(p, 2, rng)
+    beta = beta.astype(np.float32).astype(np.float64)
+    ops.setup(torch.tensor(p.d.ravel(), dtype=torch.float32, device="cuda"))
+    Pc = Phi.tocsc()
+    b = Pc.T @ p.d.ravel()
+
+    def step(x):
+        delta, _, _ = am.am_step(Pc, b, x, p.d.ravel(), p.I0)
+        return x + delta
+
+    gbar = rng.standard_normal(beta.size).astype(np.float32)
+    got = ops.am_step_vjp(torch.tensor(beta, device="cuda"),
+                          torch.tensor(gbar, device="cuda")).cpu().numpy().astype(np.float64)
+    for _ in range(3):
+        dvec = rng.standard_normal(beta.size)
+        eps = 1e-6 / np.linalg.norm(dvec) * np.linalg.norm(beta)
+        jd = (step(beta + eps * dvec) - step(beta - eps * dvec)) / (2 * eps)
+        want = float(gbar.astype(np.float64) @ jd)
+        assert abs(float(got @ dvec) - want) <= 2e-3 * abs(want) + 1e-5 * np.abs(got).sum(), (float(got @ dvec), want)
