@@ -624,6 +624,9 @@ __device__ __forceinline__ double4_16a ld4(const double4_16a* p)
     return r;
 }
 
+__device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
@@ -663,30 +666,40 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
     const int bsz = 1 << S.level;
     const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
     const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
-    const T scale = MODE == kBpQuad ? T(1) : T(1) / T(bsz);
+    // the block scale 2^-level is applied once after the loops (exact)
     const int v0 = chunk * S.vpc;
     const int v1 = min(g.V, v0 + S.vpc);
     const bool fan = g.kind != 0;
     const T isdd = T(1) / g.sdd, ipitch = T(1) / g.pitch;
     const T u0 = -g.ucen * g.pitch;
+    // detector coordinate -> bin: u * ku + ucen (fan: u = sdd w / (sod - a))
+    const T ku = fan ? g.sdd * ipitch : ipitch;
     for (int v = v0 + wv; v < v1; v += kViewLanes) {
-        const T c = __ldg(g.cs + 2 * v), s = __ldg(g.cs + 2 * v + 1);
+        const auto csv = ld2(g.cs + 2 * v);
+        const T c = csv.x, s = csv.y;
         const T ac = cx * c + cy * s;        // block centre along e
         const T wc = -cx * s + cy * c;       // ... along u
-        // shadow of the block: detector coordinates of its four corners
-        T umin = T(1e30), umax = T(-1e30);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T ox = (k & 1) ? hx : -hx, oy = (k & 2) ? hy : -hy;
-            const T wu = wc - ox * s + oy * c;
-            const T uu = fan ? fast_div(g.sdd * wu, g.sod - (ac + ox * c + oy * s)) : wu;
-            umin = fmin(umin, uu);
-            umax = fmax(umax, uu);
+        // shadow of the block from its four corners (+-hx, +-hy): along u the
+        // corners sit at wc +- (hy c - hx s) and wc +- (hx s + hy c), along e
+        // at ac +- (hx c + hy s) and ac +- (hx c - hy s) respectively
+        const T w1 = hy * c - hx * s, e1 = hx * c + hy * s;
+        const T w2 = hx * s + hy * c, e2 = hx * c - hy * s;
+        T umin, umax;
+        if (fan) {
+            const T D = g.sod - ac;
+            const T r0 = fast_div(wc - w1, D + e1), r1 = fast_div(wc + w1, D - e1);
+            const T r2 = fast_div(wc - w2, D - e2), r3 = fast_div(wc + w2, D + e2);
+            umin = fmin(fmin(r0, r1), fmin(r2, r3));
+            umax = fmax(fmax(r0, r1), fmax(r2, r3));
+        } else {
+            const T e = fmax(fabs(w1), fabs(w2));
+            umin = wc - e;
+            umax = wc + e;
         }
         // the rays through the shadow (umin, umax); a margin of 1e-3 bin
         // covers the fast division's rounding (~1e-4 bin at the detector edge)
-        const int blo = max(0, (int)ceil(umin * ipitch + g.ucen - T(1e-3)));
-        const int bhi = min(g.B - 1, (int)floor(umax * ipitch + g.ucen + T(1e-3)));
+        const int blo = max(0, (int)ceil(fma(umin, ku, g.ucen - T(1e-3))));
+        const int bhi = min(g.B - 1, (int)floor(fma(umax, ku, g.ucen + T(1e-3))));
         const T kappa = fan ? (g.sod - ac) * isdd : T(1);
         // ray offset from the block centre along u, linear in the bin
         T delta = (T(blo) * g.pitch + u0) * kappa - wc;
@@ -736,16 +749,16 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 // along y the first half is the lower one when 1/dy > 0
                 T A, dx, dy, dg;
                 haar_split(a, b, hx * dd.z, hy * fabs(dd.w), A, dx, dy, dg);
-                const T qs = q * scale;
-                const T qy = flip(qs, dd.w);       // qs with the sign that orders the y halves
-                acc[0] += qs * A;
-                // lower half minus upper half
-                const T ph = qy * dy;
-                const T pv = qs * dx;
-                const T pd = qy * dg;
-                if (ph > T(0)) acc[1] += ph; else acc[2] += ph;
-                if (pv > T(0)) acc[3] += pv; else acc[4] += pv;
-                if (pd > T(0)) acc[5] += pd; else acc[6] += pd;
+                const T qy = flip(q, dd.w);        // q with the sign that orders the y halves
+                acc[0] = fma(q, A, acc[0]);
+                // lower half minus upper half: the signed sum of q phi and the
+                // sum of q |phi| (q >= 0), turned into the + and - parts below
+                acc[1] = fma(qy, dy, acc[1]);
+                acc[2] = fma(q, fabs(dy), acc[2]);
+                acc[3] = fma(q, dx, acc[3]);
+                acc[4] = fma(q, fabs(dx), acc[4]);
+                acc[5] = fma(qy, dg, acc[5]);
+                acc[6] = fma(q, fabs(dg), acc[6]);
                 if (WORK) {
                     T cFF, cFS, cSF, cSS;
                     child_chords_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w), cFF, cFS, cSF, cSS);
@@ -753,8 +766,23 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 }
             } else {
                 const T ch = block_chord_ab(a, b, hx * dd.z, hy * fabs(dd.w));
-                acc[0] += q * scale * ch;
+                acc[0] = fma(q, ch, acc[0]);
                 if (WORK) evals += ch > T(0);
+            }
+        }
+    }
+    if (MODE != kBpQuad) {
+        // the block scale 2^-level (a power of two: the products above are
+        // scaled exactly); (signed sum s, absolute sum a) -> + part (s + a) / 2
+        // and - part (s - a) / 2, clamped to their signs against rounding
+        const T scale = T(1) / T(bsz);
+        acc[0] *= scale;
+        if (MODE == kBpSplit) {
+#pragma unroll
+            for (int k = 1; k < 7; k += 2) {
+                const T sg = acc[k] * scale, ab = acc[k + 1] * scale;
+                acc[k] = fmax(T(0.5) * (sg + ab), T(0));
+                acc[k + 1] = fmin(T(0.5) * (sg - ab), T(0));
             }
         }
     }
