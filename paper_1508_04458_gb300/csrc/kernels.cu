@@ -213,8 +213,10 @@ __device__ __forceinline__ void forward_body(const Geom<T>& g, const T* __restri
     forward_cost_partial(term, cost_part, slot);
 }
 
+// Sixteen CTAs per SM (at most 32 registers): a full SM of warps to cover
+// the image-row loads that miss L1.
 template <typename T, bool PIX, bool WORK>
-__global__ void __launch_bounds__(kFwdTPB)
+__global__ void __launch_bounds__(kFwdTPB, 16)
 k_forward(Geom<T> g, const T* __restrict__ mu, const T* __restrict__ pad, const uint8_t* __restrict__ leaf,
           const float* __restrict__ d, const typename CostTerm<T>::type* __restrict__ dterm,
           const float* __restrict__ I0, T* __restrict__ qhat, T* __restrict__ p_out,
@@ -645,10 +647,10 @@ __device__ __forceinline__ double flip2(double x, double s1, double s2)
     return (signbit(s1) != signbit(s2)) ? -x : x;
 }
 
-// dirtab[v][b] = (s/dx, -c/dy, 1/dx, 1/dy) of ray (v, b), c, s = cos, sin of
-// the view, the ray oriented so that dx >= 0: with delta the ray's offset
-// from a block centre along u, the centre-line crossings are a = delta s/dx
-// and b = -delta c/dy.
+// dirtab[v][b] = (s/dx, -c/dy, 1/dx, ry/dy) of ray (v, b), c, s = cos, sin of
+// the view, ry = vy / vx, the ray oriented so that dx >= 0: with delta the
+// ray's offset from a block centre along u, the centre-line crossings are
+// a = delta s/dx and b = -delta c/dy.
 // Item kinds of a back-projection segment.
 enum { kBpBlock = 0, kBpSplit = 1, kBpQuad = 2 };
 
@@ -666,7 +668,11 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
     const int bsz = 1 << S.level;
     const T hx = T(0.5) * T(bsz) * g.vx, hy = T(0.5) * T(bsz) * g.vy;
     const T cx = g.X0 + (T(2 * bx + 1)) * hx, cy = g.Y0 + (T(2 * by + 1)) * hy;
-    // the block scale 2^-level is applied once after the loops (exact)
+    // The ray parameters are measured in units of hx: the block spans
+    // [a - 1/dx, a + 1/dx] along x and [b - ry/|dy|, b + ry/|dy|] along y
+    // (ry = vy / vx, folded into the table's fourth entry), so no per-bin
+    // scaling; the sums are multiplied by hx once after the loops.
+    const T ihx = T(1) / hx, ry = g.vy * g.ivx;
     const int v0 = chunk * S.vpc;
     const int v1 = min(g.V, v0 + S.vpc);
     const bool fan = g.kind != 0;
@@ -700,9 +706,9 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
         // covers the fast division's rounding (~1e-4 bin at the detector edge)
         const int blo = max(0, (int)ceil(fma(umin, ku, g.ucen - T(1e-3))));
         const int bhi = min(g.B - 1, (int)floor(fma(umax, ku, g.ucen + T(1e-3))));
-        const T kappa = fan ? (g.sod - ac) * isdd : T(1);
-        // ray offset from the block centre along u, linear in the bin
-        T delta = (T(blo) * g.pitch + u0) * kappa - wc;
+        const T kappa = (fan ? (g.sod - ac) * isdd : T(1)) * ihx;
+        // ray offset from the block centre along u (in units of hx), linear in the bin
+        T delta = fma(T(blo) * g.pitch + u0, kappa, -wc * ihx);
         const T dstep = g.pitch * kappa;
         const T* row = sino + (size_t)v * g.B;
         const typename Vec4<T>::type* drow = TABLE ? dirtab + (size_t)v * g.B : nullptr;
@@ -725,10 +731,11 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                     dx = -dx;
                     dy = -dy;
                 }
+                const T iy = safe_rcp(dy);
                 dd.z = safe_rcp(dx);
-                dd.w = safe_rcp(dy);
+                dd.w = iy * ry;
                 dd.x = s * dd.z;
-                dd.y = -c * dd.w;
+                dd.y = -c * iy;
             }
             const T a = delta * dd.x, b = delta * dd.y;
             const T q = __ldg(row + bb);
@@ -736,7 +743,7 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 // pixel basis: the four pixels' chords in physical order, select-free:
                 // pixel (ylo,xlo), (ylo,xhi), (yhi,xlo), (yhi,xhi) sums
                 T cll, chl, clh, chh;
-                child_chords_phys_xpos(a, b, T(0.5) * hx, T(0.5) * hy, dd.z, dd.w, cll, chl, clh, chh);
+                child_chords_phys_xpos(a, b, T(0.5), T(0.5), dd.z, dd.w, cll, chl, clh, chh);
                 acc[0] += q * cll;
                 acc[1] += q * chl;
                 acc[2] += q * clh;
@@ -748,7 +755,7 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 // The travel has dx >= 0, so its first x half is the lower one;
                 // along y the first half is the lower one when 1/dy > 0
                 T A, dx, dy, dg;
-                haar_split(a, b, hx * dd.z, hy * fabs(dd.w), A, dx, dy, dg);
+                haar_split(a, b, dd.z, fabs(dd.w), A, dx, dy, dg);
                 const T qy = flip(q, dd.w);        // q with the sign that orders the y halves
                 acc[0] = fma(q, A, acc[0]);
                 // lower half minus upper half: the signed sum of q phi and the
@@ -761,21 +768,24 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
                 acc[6] = fma(q, fabs(dg), acc[6]);
                 if (WORK) {
                     T cFF, cFS, cSF, cSS;
-                    child_chords_ab(a, b, hx * fabs(dd.z), hy * fabs(dd.w), cFF, cFS, cSF, cSS);
+                    child_chords_ab(a, b, dd.z, fabs(dd.w), cFF, cFS, cSF, cSS);
                     evals += (cFF > T(0)) + (cFS > T(0)) + (cSF > T(0)) + (cSS > T(0));
                 }
             } else {
-                const T ch = block_chord_ab(a, b, hx * dd.z, hy * fabs(dd.w));
+                const T ch = block_chord_ab(a, b, dd.z, fabs(dd.w));
                 acc[0] = fma(q, ch, acc[0]);
                 if (WORK) evals += ch > T(0);
             }
         }
     }
-    if (MODE != kBpQuad) {
-        // the block scale 2^-level (a power of two: the products above are
-        // scaled exactly); (signed sum s, absolute sum a) -> + part (s + a) / 2
-        // and - part (s - a) / 2, clamped to their signs against rounding
-        const T scale = T(1) / T(bsz);
+    if (MODE == kBpQuad) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] *= hx;
+    } else {
+        // hx times the block scale 2^-level; (signed sum s, absolute sum a)
+        // -> + part (s + a) / 2 and - part (s - a) / 2, clamped to their
+        // signs against rounding
+        const T scale = hx / T(bsz);
         acc[0] *= scale;
         if (MODE == kBpSplit) {
 #pragma unroll
@@ -875,8 +885,10 @@ __device__ __forceinline__ void bp_body(const Geom<T>& g, const SegTable& tab, i
     }
 }
 
+// Six CTAs per SM (at most 40 registers): the extra warps hide more of the
+// gathers' latency than the tighter allocation costs.
 template <typename T>
-__global__ void __launch_bounds__(kBackTPB)
+__global__ void __launch_bounds__(kBackTPB, 6)
 k_backproject(Geom<T> g, SegTable tab, const T* __restrict__ sino,
               const typename Vec4<T>::type* __restrict__ dirtab, T* __restrict__ part,
               unsigned long long* __restrict__ work)

@@ -411,8 +411,10 @@ wam_status plan_segments(wam_ctx* c, const std::vector<ListInfo>& lists, SegTabl
     return ensure_t(c, B_PART, (size_t)std::max<long long>(part, 1), part_out);
 }
 
-// Per ray (s/dx, -c/dy, 1/dx, 1/dy): the reciprocal unit direction and its
-// products with the view's sin and -cos, computed in FP64 on the host once
+// Per ray (s/dx, -c/dy, 1/dx, ry/dy), ry = vy / vx: the reciprocal unit
+// direction (its y part times the pixel's aspect ratio, the back-projector
+// measuring lengths in units of a block's half-width) and its products with
+// the view's sin and -cos, computed in FP64 on the host once
 // per context and precision.  Every ray is taken in the orientation with
 // dx >= 0 (a line's two orientations cross the same voxels), so the
 // back-projector's first x half along the travel is always the lower one.
@@ -433,6 +435,7 @@ wam_status dir_table(wam_ctx* c, const void** out, const std::vector<int>* order
         a = a < tiny ? tiny : a;
         return std::signbit(d) ? -1.0 / a : 1.0 / a;
     };
+    const double ry = w.vy / w.vx;                    // the pixel's aspect ratio
     for (int k = 0; k < w.n_views; ++k) {
         const int view = order ? (*order)[k] : k;     // row k of the table holds this view
         const double th = w.angle0 + view * (w.angle_span / w.n_views);
@@ -454,7 +457,7 @@ wam_status dir_table(wam_ctx* c, const void** out, const std::vector<int>* order
             e[0] = (T)(sn * ix);
             e[1] = (T)(-cs * iy);
             e[2] = (T)ix;
-            e[3] = (T)iy;
+            e[3] = (T)(ry * iy);
         }
     }
     T* d = nullptr;
