@@ -684,21 +684,51 @@ def sub_cone256(args, quick: bool = False):
             "roofline": res["multires_3d_haar"]["roofline"], **res}
 
 
-def profile_case(full: bool, n: int = 256):
+def profile_case(case: str, n: int = 256):
     """A case of the same kernels for kernel profiling: an n x n bag with
     n * 1.40625 views x 2n bins (256: 360 x 512; 512: 720 x 1024, the
-    benchmark's own scan)."""
+    benchmark's own scan).  multires / full: two reconstructions of the
+    benchmark's schedule (multiresolution AM / plain AM).  fulltree: one
+    8-iteration multiresolution run whose expansions after iterations 1-4
+    take every leaf, so launches 6 to 8 of the back-projector run the full
+    4-level tree (the same items whatever the data); it prints the library's
+    work count (child chords) and CUDA-event time per launch of that phase.
+    forward: three pixel-basis forward projections of a constant image
+    (the strip walk alone)."""
+    import json
     import torch
     from paper_1508_04458_gb300 import inputs as I
     from paper_1508_04458_gb300 import wam
     p = I.problem_fan(256, 360, 512, 1e5, seed=I.SEED_BASE + 3) if n == 256 else I.problem_fan512()
     ctx = wam.Context(p.geom)
     ctx.set_data(p.d.astype(np.float32), p.I0)
-    for _ in range(2):
-        if full:
-            ctx.reconstruct(0, N_ITERS, precision=32, full_am=True, device_out=True)
-        else:
-            ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32, device_out=True)
+    if case == "fulltree":
+        ea, tau = (1, 2, 3, 4), (-1.0, -1.0, -1.0, -1.0)
+        ctx.reconstruct(4, 8, ea, tau, precision=32, device_out=True)
+        torch.cuda.synchronize()
+        per = {}
+        for mode, key in ((wam.WAM_PROFILE_WORK, "work"), (wam.WAM_PROFILE_TIME, "ms")):
+            for iters in (8, 6):
+                ctx.profile(mode=mode)
+                ctx.reconstruct(4, iters, ea, tau, precision=32, device_out=True)
+                per[(key, iters)] = ctx.stats()["backproject"][key]
+                ctx.profile(False)
+        print(json.dumps({"case": "fulltree fan%d" % n,
+                          "backproject_work_per_launch": (per[("work", 8)] - per[("work", 6)]) / 2,
+                          "backproject_ms_per_launch": (per[("ms", 8)] - per[("ms", 6)]) / 2}))
+    elif case == "forward":
+        g = p.geom
+        mu = torch.full((g.nx * g.ny,), 0.02, dtype=torch.float32, device="cuda")
+        q = torch.empty(g.n_views * g.n_bins, dtype=torch.float32, device="cuda")
+        cost = torch.empty(1, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.check(wam.wam_forward(ctx.h, 0, None, wam.ptr(mu), wam.ptr(q), wam.ptr(cost), wam.current_stream()))
+    else:
+        for _ in range(2):
+            if case == "full":
+                ctx.reconstruct(0, N_ITERS, precision=32, full_am=True, device_out=True)
+            else:
+                ctx.reconstruct(L_LEVELS, N_ITERS, EXPAND_AT, TAU, precision=32, device_out=True)
     torch.cuda.synchronize()
     ctx.close()
 
@@ -719,14 +749,15 @@ def main():
                     help="fan512 (default): the benchmark line; batch32 / cone256 / autograd: secondary "
                          "measurements of the batched, 3-D cone-beam and differentiation paths "
                          "(one JSON line each)")
-    ap.add_argument("--profile-case", choices=("multires", "full"), default=None,
-                    help="run two reconstructions (multires or plain AM) of a 256x256 fan-beam bag "
-                         "(360 views x 512 bins) for kernel profiling, print nothing")
+    ap.add_argument("--profile-case", choices=("multires", "full", "fulltree", "forward"), default=None,
+                    help="kernel profiling cases on a fan-beam bag (--profile-n): two reconstructions "
+                         "(multires or plain AM, print nothing); fulltree: the full 4-level tree, prints the "
+                         "back-projector's work and time per launch; forward: three pixel-basis projections")
     ap.add_argument("--profile-n", type=int, choices=(256, 512), default=256,
                     help="image side of --profile-case (512: the benchmark's own bag and scan)")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case == "full", args.profile_n)
+        profile_case(args.profile_case, args.profile_n)
         return
     subs = {"batch32": sub_batch32, "cone256": sub_cone256, "autograd": sub_autograd}
     if args.workload in subs:
