@@ -483,12 +483,12 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                 const float dw = fmaf(fk, dstep, dw0);
                 const float4 T = __ldg(drow + bb);
                 const float a = dw * T.x, b = dw * T.y;
-                const float q = __ldg(row + bb) * __ldg(dl + bb) * scale;
+                const float q = __ldg(row + bb) * __ldg(dl + bb);
                 if (MODE == kBp3Block) {
                     const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
                     const float ch = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh) -
                                            fmaxf(fmaxf(a - Ax, b - Ay), zsl), 0.0f);
-                    acc[0] += q * ch;
+                    acc[0] = fmaf(q, ch, acc[0]);
                     if (WORK) evals += ch > 0.0f;
                 } else if (MODE == kBp3Quad) {
                     // the split of the block within the slice's z slab from the
@@ -510,14 +510,15 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                             for (int i = 0; i < 2; ++i)
                                 evals += fminf(fminf(xh[i], yh[j]), zsh) - fmaxf(fmaxf(xl[i], yl[j]), zsl) > 0.0f;
                     }
-                    acc[0] += q * (hi - lo);
-                    // + on the lower halves: t = 1 x, 2 y, 3 xy
+                    acc[0] = fmaf(q, hi - lo, acc[0]);
+                    // + on the lower halves: t = 1 x, 2 y, 3 xy; the signed sum of
+                    // q phi and the sum of q |phi| (q >= 0), split after the loops
                     const float W[3] = {flipf(fmaf(2.0f, ca, -sm), T.z), flipf(fmaf(2.0f, cb, -sm), T.w),
                                         flipf(flipf(fmaf(-2.0f, fabsf(ca - cb), hi - lo), T.z), T.w)};
 #pragma unroll
                     for (int t = 0; t < 3; ++t) {
-                        const float ph = q * W[t];
-                        if (ph > 0.0f) acc[1 + 2 * t] += ph; else acc[2 + 2 * t] += ph;
+                        acc[1 + 2 * t] = fmaf(q, W[t], acc[1 + 2 * t]);
+                        acc[2 + 2 * t] = fmaf(q, fabsf(W[t]), acc[2 + 2 * t]);
                     }
                 } else if (MODE == kBp3Octet) {
                     // voxel basis: chords of the 8 voxels in physical order (index
@@ -572,17 +573,32 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                                 w[i] = u0 + u1;
                                 w[i + h] = u0 - u1;
                             }
-                    acc[0] += q * w[0];
+                    acc[0] = fmaf(q, w[0], acc[0]);
 #pragma unroll
                     for (int t = 1; t < 8; ++t) {
                         float wt = w[t];
                         if (t & 1) wt = flipf(wt, T.z);
                         if (t & 2) wt = flipf(wt, T.w);
                         if (t & 4) wt = flipf(wt, ri);
-                        const float ph = q * wt;
-                        if (ph > 0.0f) acc[2 * t - 1] += ph; else acc[2 * t] += ph;
+                        // signed and absolute sums (q >= 0), split after the loops
+                        acc[2 * t - 1] = fmaf(q, wt, acc[2 * t - 1]);
+                        acc[2 * t] = fmaf(q, fabsf(wt), acc[2 * t]);
                     }
                 }
+            }
+        }
+    }
+    if (MODE != kBp3Octet) {
+        // the basis scale, and (signed sum s, absolute sum a) -> + part
+        // (s + a) / 2 and - part (s - a) / 2, clamped to their signs
+        acc[0] *= scale;
+        if (MODE == kBp3Oct || MODE == kBp3Quad) {
+            constexpr int nd = MODE == kBp3Oct ? 7 : 3;
+#pragma unroll
+            for (int t = 1; t <= nd; ++t) {
+                const float sg = acc[2 * t - 1] * scale, ab = acc[2 * t] * scale;
+                acc[2 * t - 1] = fmaxf(0.5f * (sg + ab), 0.0f);
+                acc[2 * t] = fminf(0.5f * (sg - ab), 0.0f);
             }
         }
     }
