@@ -407,12 +407,13 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
 
     float acc = 0.0f;
     unsigned steps = 0;
-    // walk state: the padded column colp of the next strip's first cell, the
-    // next oriented minor grid line fbo
+    // walk state: the padded column colp of the next strip's first cell, and
+    // E = u - (the next oriented minor grid line) after the last strip walked
+    // (traverse_strips' running form: the same values, the same sums)
     int colp = c0 + 1;
-    float fbo = up ? 1.0f : 0.0f;
-    auto strip = [&](const float* base, int rs, int& p, float chord, float u) {
-        const float e = u - fbo;
+    const float fbo0 = up ? 1.0f : 0.0f;
+    float E = 0.0f;
+    auto strip = [&](const float* base, int rs, int& p, float chord, float e) {
         const bool cross = e >= 0.0f;
         const float cb = cross ? fminf(e * vk, chord) : 0.0f;
         const int pb = cross ? p + dlin : p;
@@ -420,25 +421,22 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
         acc += ca * base[p];
         acc += cb * base[pb];
         if (WORK) steps += (ca > 0.0f) + (cb > 0.0f);
-        fbo = cross ? fbo + 1.0f : fbo;
+        E = cross ? e - 1.0f : e;
         p = pb + rs;
     };
     // interior strips ja..jb (full chords) from base (row stride rs), p the
     // index of strip ja's first cell; returns the index one row past jb
     auto interior = [&](const float* base, int rs, int p, int ja, int jb) {
-        float fj = (float)ja;
 #pragma unroll 4
-        for (int jj = ja; jj <= jb; ++jj) {
-            fj += 1.0f;
-            strip(base, rs, p, full, fmaf(fj, D, A));
-        }
+        for (int jj = ja; jj <= jb; ++jj) strip(base, rs, p, full, E + D);
         return p;
     };
     // the partial first strip (the whole walk when it is one strip), from global memory
     if (hit) {
         int p = (j0 + 1) * sM + colp;
-        if (j0 == j1) strip(img, sM, p, (s_hi - s_lo) * sec, fmaf(s_hi, G, U0));
-        else strip(img, sM, p, fmaxf(fmaf((float)(j0 + 1), vm, M0) - s_lo, 0.0f) * sec, fmaf((float)(j0 + 1), D, A));
+        if (j0 == j1) strip(img, sM, p, (s_hi - s_lo) * sec, fmaf(s_hi, G, U0) - fbo0);
+        else strip(img, sM, p, fmaxf(fmaf((float)(j0 + 1), vm, M0) - s_lo, 0.0f) * sec,
+                   fmaf((float)(j0 + 1), D, A) - fbo0);
         colp = p - (j0 + 2) * sM;
     }
     const int i0 = j0 + 1, i1 = j1 - 1;          // the interior strips
@@ -458,7 +456,9 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
             if (hit && ja <= jb && !timed_out) {
                 // the columns this ray reaches in the stage: its column now and
                 // after the crossings up to strip jb (at most one per strip)
-                const int ncross = max(0, (int)floorf(fmaf((float)(jb + 1), D, A)) - (int)fbo + 1);
+                // (E + (jb + 1 - ja) D rounded down, plus one, up to one off by
+                // rounding: inside the window's two-cell margin)
+                const int ncross = max(0, (int)floorf(fmaf((float)(jb + 1 - ja), D, E)) + 1);
                 const int cend = colp + dlin * ncross;
                 const int x0 = s_x0[st];
                 if (min(colp, cend) - 2 >= x0 && max(colp, cend) + 2 < x0 + kStageCols) {
@@ -490,7 +490,8 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
     // the partial last strip, from global memory
     if (hit && j1 > j0) {
         int p = (j1 + 1) * sM + colp;
-        strip(img, sM, p, fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec, fmaf(s_hi, G, U0));
+        strip(img, sM, p, fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec,
+              E + (fmaf(s_hi, G, U0) - fmaf((float)j1, D, A)));
     }
     CostAcc<float> term = 0;
     if (b < g.B) term = forward_ray_out(g, v, b, inside ? acc : 0.0f, d, dterm, I0, qhat, p_out, resid);

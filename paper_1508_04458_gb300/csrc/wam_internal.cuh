@@ -218,11 +218,13 @@ __device__ __forceinline__ void traverse_pixels(const Geom<T>& g, const Ray<T>& 
 //
 // The minor coordinate is tracked in pixel units oriented along the ray's
 // minor travel and counted from the edge of the entry pixel c0
-// (u = +-(n - N0 - c0 v_minor) / v_minor), so the next grid line is the
-// integer fbo ahead and a crossing is u - fbo >= 0; the piece beyond it is
-// (u - fbo) v_minor / |d_minor| (no division in the loop).  Counting from c0
-// keeps u small for rays near an axis, whose crossing points are the most
-// sensitive to rounding in u.  The two partial end strips are peeled;
+// (u = +-(n - N0 - c0 v_minor) / v_minor), so the next grid line is an
+// integer ahead; the walk carries e = u - (that line) at the end of each
+// strip, which grows by the constant D per full strip and drops by one at a
+// crossing (e >= 0); the piece beyond a crossing is e v_minor / |d_minor| (no
+// division in the loop).  Counting from c0 keeps u small for rays near an
+// axis, whose crossing points are the most sensitive to rounding in u.  The
+// two partial end strips are peeled (e from the entry and exit points);
 // interior strips have the constant chord v_major / |d_major|.
 //
 // Pixels are addressed in an image with a one-pixel zero apron on every side,
@@ -267,31 +269,30 @@ __device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& 
     const T G = fabs(slope) * ivn;                     // oriented minor units per unit major
     const T U0 = (up ? n0 - Nc : Nc - n0) * ivn;       // u at major 0
     const int sM = pad_row(nn), dlin = up ? 1 : -1;
-    T fbo = up ? T(1) : T(0);                          // next minor grid line, oriented
+    const T fbo0 = up ? T(1) : T(0);                   // the first minor grid line ahead, oriented
     int lin = (j0 + 1) * sM + c0 + 1;
-    auto strip = [&](T chord, T u) {
-        const T e = u - fbo;
+    // One strip: e = u - (the next oriented minor grid line) at the strip's
+    // end; a crossing (e >= 0) puts the last e * vk of the chord in the next
+    // cell.  Returns e for the next line (one line further on a crossing).
+    auto strip = [&](T chord, T e) {
         const bool cross = e >= T(0);
         const T cb = cross ? fmin(e * vk, chord) : T(0);
         const int lb = cross ? lin + dlin : lin;
         visit(lin, chord - cb, lb, cb);
-        fbo = cross ? fbo + T(1) : fbo;
         lin = lb + sM;
+        return cross ? e - T(1) : e;
     };
     if (j1 == j0) {
-        strip((s_hi - s_lo) * sec, fma(s_hi, G, U0));
+        strip((s_hi - s_lo) * sec, fma(s_hi, G, U0) - fbo0);
         return;
     }
     const T A = fma(G, M0, U0), D = G * vm;            // u at the end of strip j: A + (j + 1) D
-    T fj = T(j0 + 1);
-    strip(fmax(fma(fj, vm, M0) - s_lo, T(0)) * sec, fma(fj, D, A));
+    T E = strip(fmax(fma(T(j0 + 1), vm, M0) - s_lo, T(0)) * sec, fma(T(j0 + 1), D, A) - fbo0);
     const T full = vm * sec;
 #pragma unroll 4
-    for (int k = j1 - j0 - 1; k > 0; --k) {
-        fj += T(1);
-        strip(full, fma(fj, D, A));
-    }
-    strip(fmax(s_hi - fma(T(j1), vm, M0), T(0)) * sec, fma(s_hi, G, U0));
+    for (int k = j1 - j0 - 1; k > 0; --k) E = strip(full, E + D);
+    // the last strip ends at the exit point, u - A - j1 D past the end of strip j1 - 1
+    strip(fmax(s_hi - fma(T(j1), vm, M0), T(0)) * sec, E + (fma(s_hi, G, U0) - fma(T(j1), D, A)));
 }
 
 // ---------------------------------------------------------------------------
