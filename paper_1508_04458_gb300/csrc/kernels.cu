@@ -413,9 +413,9 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
     int colp = c0 + 1;
     const float fbo0 = up ? 1.0f : 0.0f;
     float E = 0.0f;
-    auto strip = [&](const float* base, int rs, int& p, float chord, float e) {
+    auto strip = [&](const float* base, int rs, int& p, float chord, float e, auto clamp) {
         const bool cross = e >= 0.0f;
-        const float cb = cross ? fminf(e * vk, chord) : 0.0f;
+        const float cb = cross ? (decltype(clamp)::value ? fminf(e * vk, chord) : e * vk) : 0.0f;
         const int pb = cross ? p + dlin : p;
         const float ca = chord - cb;
         acc += ca * base[p];
@@ -428,15 +428,15 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
     // index of strip ja's first cell; returns the index one row past jb
     auto interior = [&](const float* base, int rs, int p, int ja, int jb) {
 #pragma unroll 4
-        for (int jj = ja; jj <= jb; ++jj) strip(base, rs, p, full, E + D);
+        for (int jj = ja; jj <= jb; ++jj) strip(base, rs, p, full, E + D, std::false_type());
         return p;
     };
     // the partial first strip (the whole walk when it is one strip), from global memory
     if (hit) {
         int p = (j0 + 1) * sM + colp;
-        if (j0 == j1) strip(img, sM, p, (s_hi - s_lo) * sec, fmaf(s_hi, G, U0) - fbo0);
+        if (j0 == j1) strip(img, sM, p, (s_hi - s_lo) * sec, fmaf(s_hi, G, U0) - fbo0, std::true_type());
         else strip(img, sM, p, fmaxf(fmaf((float)(j0 + 1), vm, M0) - s_lo, 0.0f) * sec,
-                   fmaf((float)(j0 + 1), D, A) - fbo0);
+                   fmaf((float)(j0 + 1), D, A) - fbo0, std::true_type());
         colp = p - (j0 + 2) * sM;
     }
     const int i0 = j0 + 1, i1 = j1 - 1;          // the interior strips
@@ -491,7 +491,7 @@ k_forward_staged(Geom<float> g, const float* __restrict__ pad, const __grid_cons
     if (hit && j1 > j0) {
         int p = (j1 + 1) * sM + colp;
         strip(img, sM, p, fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec,
-              E + (fmaf(s_hi, G, U0) - fmaf((float)j1, D, A)));
+              E + (fmaf(s_hi, G, U0) - fmaf((float)j1, D, A)), std::true_type());
     }
     CostAcc<float> term = 0;
     if (b < g.B) term = forward_ray_out(g, v, b, inside ? acc : 0.0f, d, dterm, I0, qhat, p_out, resid);

@@ -9,6 +9,7 @@
 // Both evaluate h(y|x) = length of ray y inside voxel x (Sec. II) and its
 // block sums, which by Eq. 1.2 give phi(y|z) = sum_x h(y|x) omega(x|z).
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -274,25 +275,29 @@ __device__ __forceinline__ void traverse_strips(const Geom<T>& g, const Ray<T>& 
     // One strip: e = u - (the next oriented minor grid line) at the strip's
     // end; a crossing (e >= 0) puts the last e * vk of the chord in the next
     // cell.  Returns e for the next line (one line further on a crossing).
-    auto strip = [&](T chord, T e) {
+    // (In a full strip the piece past a crossing, e vk with 0 <= e < D, is
+    // below the chord D vk, so only the partial end strips clamp it.)
+    auto strip = [&](T chord, T e, auto clamp) {
         const bool cross = e >= T(0);
-        const T cb = cross ? fmin(e * vk, chord) : T(0);
+        const T cb = cross ? (decltype(clamp)::value ? fmin(e * vk, chord) : e * vk) : T(0);
         const int lb = cross ? lin + dlin : lin;
         visit(lin, chord - cb, lb, cb);
         lin = lb + sM;
         return cross ? e - T(1) : e;
     };
+    using Clamp = std::true_type;
+    using NoClamp = std::false_type;
     if (j1 == j0) {
-        strip((s_hi - s_lo) * sec, fma(s_hi, G, U0) - fbo0);
+        strip((s_hi - s_lo) * sec, fma(s_hi, G, U0) - fbo0, Clamp());
         return;
     }
     const T A = fma(G, M0, U0), D = G * vm;            // u at the end of strip j: A + (j + 1) D
-    T E = strip(fmax(fma(T(j0 + 1), vm, M0) - s_lo, T(0)) * sec, fma(T(j0 + 1), D, A) - fbo0);
+    T E = strip(fmax(fma(T(j0 + 1), vm, M0) - s_lo, T(0)) * sec, fma(T(j0 + 1), D, A) - fbo0, Clamp());
     const T full = vm * sec;
 #pragma unroll 4
-    for (int k = j1 - j0 - 1; k > 0; --k) E = strip(full, E + D);
+    for (int k = j1 - j0 - 1; k > 0; --k) E = strip(full, E + D, NoClamp());
     // the last strip ends at the exit point, u - A - j1 D past the end of strip j1 - 1
-    strip(fmax(s_hi - fma(T(j1), vm, M0), T(0)) * sec, E + (fma(s_hi, G, U0) - fma(T(j1), D, A)));
+    strip(fmax(s_hi - fma(T(j1), vm, M0), T(0)) * sec, E + (fma(s_hi, G, U0) - fma(T(j1), D, A)), Clamp());
 }
 
 // ---------------------------------------------------------------------------
