@@ -694,7 +694,8 @@ def profile_case(case: str, n: int = 256):
     4-level tree (the same items whatever the data); it prints the library's
     work count (child chords) and CUDA-event time per launch of that phase.
     forward: three pixel-basis forward projections of a constant image
-    (the strip walk alone)."""
+    with the global-memory strip walk, then three with the walk staged in
+    shared memory 24 strips at a time."""
     import json
     import torch
     from paper_1508_04458_gb300 import inputs as I
@@ -721,8 +722,11 @@ def profile_case(case: str, n: int = 256):
         mu = torch.full((g.nx * g.ny,), 0.02, dtype=torch.float32, device="cuda")
         q = torch.empty(g.n_views * g.n_bins, dtype=torch.float32, device="cuda")
         cost = torch.empty(1, dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            ctx.check(wam.wam_forward(ctx.h, 0, None, wam.ptr(mu), wam.ptr(q), wam.ptr(cost), wam.current_stream()))
+        for rows in (0, 24):
+            ctx.check(wam.wam_set_tuning(ctx.h, wam.WAM_TUNE_FWD_STAGE_ROWS, float(rows)))
+            for _ in range(3):
+                ctx.check(wam.wam_forward(ctx.h, 0, None, wam.ptr(mu), wam.ptr(q), wam.ptr(cost),
+                                          wam.current_stream()))
     else:
         for _ in range(2):
             if case == "full":
@@ -752,7 +756,8 @@ def main():
     ap.add_argument("--profile-case", choices=("multires", "full", "fulltree", "forward"), default=None,
                     help="kernel profiling cases on a fan-beam bag (--profile-n): two reconstructions "
                          "(multires or plain AM, print nothing); fulltree: the full 4-level tree, prints the "
-                         "back-projector's work and time per launch; forward: three pixel-basis projections")
+                         "back-projector's work and time per launch; forward: pixel-basis projections, "
+                         "unstaged then staged")
     ap.add_argument("--profile-n", type=int, choices=(256, 512), default=256,
                     help="image side of --profile-case (512: the benchmark's own bag and scan)")
     args = ap.parse_args()
