@@ -4,6 +4,7 @@
 // (octree blocks, seven details) or the 2-D Haar transform of each z-slice
 // under one shared tree (the paper's own 3-D setting).  All sums run in a
 // fixed order.
+#include <type_traits>
 #include "cone3d.cuh"
 
 #include <cmath>
@@ -204,35 +205,42 @@ __device__ __forceinline__ void traverse_strips3(const Geom3& g, const Ray3& r, 
     const float Un = (upn ? n0 - Nc : Nc - n0) * ivn, Uz = (upz ? z0 - Zc : Zc - z0) * g.ivz;
     const int sM = nn + 2, sZ = (nm + 2) * (nn + 2);
     const int dln = upn ? 1 : -1, dlz = upz ? sZ : -sZ;
-    float fn = upn ? 1.0f : 0.0f, fz = upz ? 1.0f : 0.0f;   // next grid lines, oriented
+    const float fn0 = upn ? 1.0f : 0.0f, fz0 = upz ? 1.0f : 0.0f;   // the first grid lines ahead, oriented
     int lin = ((k0 + 1) * (nm + 2) + (j0 + 1)) * sM + c0 + 1;
-    auto strip = [&](float chord, float un, float uz) {
-        const float en = un - fn, ez = uz - fz;
+    // One strip: en, ez = the minor and z positions at the strip's end minus
+    // the next oriented grid lines; a crossing (e >= 0) puts the last e vk of
+    // the chord beyond that line.  En, Ez carry them to the next strip (one
+    // line further on a crossing).  In a full strip a piece past a crossing
+    // (0 <= e < D) is below the chord D vk, so only the end strips clamp it.
+    float En = 0.0f, Ez = 0.0f;
+    auto strip = [&](float chord, float en, float ez, auto clamp) {
         const bool cn = en >= 0.0f, cz = ez >= 0.0f;
-        const float ln = cn ? fminf(en * vkn, chord) : 0.0f;    // piece beyond the minor line
-        const float lz = cz ? fminf(ez * vkz, chord) : 0.0f;    // piece beyond the z plane
+        const float pn = en * vkn, pz = ez * vkz;
+        const float ln = cn ? (decltype(clamp)::value ? fminf(pn, chord) : pn) : 0.0f;   // piece beyond the minor line
+        const float lz = cz ? (decltype(clamp)::value ? fminf(pz, chord) : pz) : 0.0f;   // piece beyond the z plane
         const float hi = fmaxf(ln, lz), lo = fminf(ln, lz);
         const int lb = ln > lz ? lin + dln : (cz ? lin + dlz : lin);
         const int lc = lin + (cn ? dln : 0) + (cz ? dlz : 0);
         visit(lin, chord - hi, lb, hi - lo, lc, lo);
-        fn = cn ? fn + 1.0f : fn;
-        fz = cz ? fz + 1.0f : fz;
+        En = cn ? en - 1.0f : en;
+        Ez = cz ? ez - 1.0f : ez;
         lin = lc + sM;
     };
     if (j1 == j0) {
-        strip((s_hi - s_lo) * sec, fmaf(s_hi, Gn, Un), fmaf(s_hi, Gz, Uz));
+        strip((s_hi - s_lo) * sec, fmaf(s_hi, Gn, Un) - fn0, fmaf(s_hi, Gz, Uz) - fz0, std::true_type());
         return;
     }
     const float An = fmaf(Gn, M0, Un), Dn = Gn * vm, Az = fmaf(Gz, M0, Uz), Dz = Gz * vm;
-    float fj = (float)(j0 + 1);
-    strip(fmaxf(fmaf(fj, vm, M0) - s_lo, 0.0f) * sec, fmaf(fj, Dn, An), fmaf(fj, Dz, Az));
+    const float fj = (float)(j0 + 1);
+    strip(fmaxf(fmaf(fj, vm, M0) - s_lo, 0.0f) * sec, fmaf(fj, Dn, An) - fn0, fmaf(fj, Dz, Az) - fz0,
+          std::true_type());
     const float full = vm * sec;
 #pragma unroll 4
-    for (int k = j1 - j0 - 1; k > 0; --k) {
-        fj += 1.0f;
-        strip(full, fmaf(fj, Dn, An), fmaf(fj, Dz, Az));
-    }
-    strip(fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec, fmaf(s_hi, Gn, Un), fmaf(s_hi, Gz, Uz));
+    for (int k = j1 - j0 - 1; k > 0; --k) strip(full, En + Dn, Ez + Dz, std::false_type());
+    // the last strip ends at the exit point, past the end of strip j1 - 1 by
+    // u - A - j1 D on each minor axis
+    strip(fmaxf(s_hi - fmaf((float)j1, vm, M0), 0.0f) * sec, En + (fmaf(s_hi, Gn, Un) - fmaf((float)j1, Dn, An)),
+          Ez + (fmaf(s_hi, Gz, Uz) - fmaf((float)j1, Dz, Az)), std::true_type());
 }
 
 }  // namespace
