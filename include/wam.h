@@ -201,6 +201,11 @@ wam_status wam_reconstruct(wam_ctx* ctx, const wam_schedule* sched, void* mu_out
  *     plan) from a global counter, the bags in decreasing order of work, then
  *     every bag's cost sum and update.  Epochs in which some bag walks its
  *     tree leaf by leaf, or lambda > 0, run as use_graph = 1.
+ * Modes 0 and 1 run every bag's forward with the global-memory walk,
+ * whatever staged tile height the context is tuned to (WAM_TUNE_FWD_STAGE_ROWS
+ * is chosen for a bag running alone; with the bags' kernels running at the
+ * same time the staged tiles' shared memory makes them slower), which changes
+ * no result: the two walks agree bit for bit.
  * Results of modes 0 and 1 equal n calls of wam_reconstruct bit for bit;
  * mode 2 runs the same kernel bodies and sums in the same order inside other
  * kernels, where the compiler may contract multiply-adds differently: it

@@ -39,14 +39,19 @@ def _device_name() -> str:
     return torch.cuda.get_device_name(0).replace(" ", "_")
 
 
-def _timed(ctx: "wam.Context", kernel: str, levels: int, n_iters: int, expand_at, tau) -> float:
-    """ms per launch of one kernel class in a profiled reconstruction."""
+def _timed(ctx: "wam.Context", kernel: str, levels: int, n_iters: int, expand_at, tau, reps: int = 3) -> float:
+    """ms per launch of one kernel class: the fastest of `reps` profiled
+    reconstructions after a warm-up (close candidates differ by a few
+    percent, about the spread of a single run)."""
     ctx.reconstruct(levels, n_iters, expand_at, tau, device_out=True)      # warm-up
-    ctx.profile(mode=wam.WAM_PROFILE_TIME)
-    ctx.reconstruct(levels, n_iters, expand_at, tau, device_out=True)
-    st = ctx.stats()[kernel]
-    ctx.profile(False)
-    return st["ms"] / max(1, st["launches"])
+    best = float("inf")
+    for _ in range(reps):
+        ctx.profile(mode=wam.WAM_PROFILE_TIME)
+        ctx.reconstruct(levels, n_iters, expand_at, tau, device_out=True)
+        st = ctx.stats()[kernel]
+        ctx.profile(False)
+        best = min(best, st["ms"] / max(1, st["launches"]))
+    return best
 
 
 def measure(ctx: "wam.Context", value: float, levels: int, n_iters: int, expand_at, tau) -> float:

@@ -2201,6 +2201,15 @@ wam_status wam_reconstruct_batch(wam_ctx* const* ctxs, int n, const wam_schedule
             wam_status s = runs[i].setup(ctxs[i], sc, st);
             if (s != WAM_OK) { cleanup(); return s; }
         }
+        // the bags' branches (modes 0 and 1) run concurrently: a staged forward
+        // tile, chosen for a bag run alone, slows the shared GPU down there, so
+        // the branches take the global-memory walk
+        if (use_graph != 2)
+            for (auto& r : runs) {
+                r.g.stage_rows = 0;
+                r.gperm.stage_rows = 0;
+                for (auto& gs : r.gsub) gs.stage_rows = 0;
+            }
         bool ok = true;
         for (int i = 0; i < n && ok; ++i)
             ok = cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking) == cudaSuccess &&
