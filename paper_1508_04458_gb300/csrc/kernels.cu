@@ -1765,7 +1765,9 @@ static void launch_strip_walk(const Geom<T>& gc, T* pad, const float* d, const t
     if constexpr (std::is_same<T, float>::value) {
         CUtensorMap my, mx;
         int* err = stage_error_word();
-        const int R = gc.stage_rows;
+        // staged tiles pay off from 128-cell grids up (coarser grids' bands are
+        // a few cells wide and their walks a few stages long)
+        const int R = std::min(gc.nx, gc.ny) >= 128 ? gc.stage_rows : 0;
         if ((R == 16 || R == 24 || R == 32) && err && pad_map(&my, pad, gc.nx + 2, gc.ny + 2, R) &&
             pad_map(&mx, pad + (size_t)pad_row(gc.nx) * (gc.ny + 2), gc.ny + 2, gc.nx + 2, R)) {
             COUNT_LAUNCH();
