@@ -460,9 +460,10 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
             const float ri = __ldg(g.rowinv + rr);
             // z intervals (in tau) of the first / second z half and of the whole
             // block; for voxel octets the lower / upper half in physical order
-            float z0l, z0h, z1l, z1h, zsl, zsh;
+            float z0l, z0h, z1l, z1h, zsl, zsh, zc;
             if (vr != 0.0f) {
                 const float cc = -(vr * kappa - cz) * ri;      // z centre-plane crossing
+                zc = cc;
                 if (oct) {
                     const float Hz = 0.5f * hz, uz = fabsf(ri) + ri, wz = fabsf(ri) - ri;
                     z0l = fmaf(-Hz, uz, cc); z0h = fmaf(Hz, wz, cc);      // lower z half
@@ -482,6 +483,7 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                 z0l = lo ? -B : B; z0h = lo ? B : -B;
                 z1l = hi ? -B : B; z1h = hi ? B : -B;
                 zsl = in ? -B : B; zsh = in ? B : -B;
+                zc = lo ? B : -B;      // the ray lies wholly in the first (lower) or second z half
             }
             const float* row = sino + ((size_t)v * g.R + rr) * g.B;
             const float* dl = g.dlen + (size_t)rr * g.B;
@@ -553,34 +555,45 @@ __device__ __forceinline__ void bp3_item(const Geom3& g, const Segment3& S, int 
                             }
                         }
                 } else {
+                    // The 3-D Haar split without the eight octant chords: with [lo, hi]
+                    // the ray's interval in the block and ca, cb, cc its x, y and z
+                    // centre-plane crossings clamped to it, the ray is in the first
+                    // half along an axis before that axis' crossing, so the products
+                    // of the half signs (+1 first, -1 second) integrate to
+                    // 2 c - (lo + hi) for one axis, (hi - lo) - 2 |ci - cj| for two
+                    // (the stretch between the crossings has mixed signs), and for
+                    // all three, whose product flips at each of the sorted crossings
+                    // p1 <= p2 <= p3: 2 (p1 - p2 + p3) - (lo + hi), with
+                    // p2 = ca + cb + cc - p1 - p3.  w[t]: bit 1 x, 2 y, 4 z.
                     const float Ax = hx * fabsf(T.z), Ay = hy * fabsf(T.w);
-                    const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
-                    const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
-                    const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
-                    float w[8];   // index i + 2 j + 4 k
-#pragma unroll
-                    for (int j = 0; j < 2; ++j)
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const float lo = fmaxf(xl[i], yl[j]), hi = fminf(xh[i], yh[j]);
-#pragma unroll
-                            for (int k = 0; k < 2; ++k)
-                                w[i + 2 * j + 4 * k] = fmaxf(fminf(hi, zh[k]) - fmaxf(lo, zl[k]), 0.0f);
-                        }
+                    const float lo = fmaxf(fmaxf(a - Ax, b - Ay), zsl);
+                    const float hi = fmaxf(fminf(fminf(a + Ax, b + Ay), zsh), lo);
+                    const float ca = fminf(fmaxf(a, lo), hi), cb = fminf(fmaxf(b, lo), hi);
+                    const float cc = fminf(fmaxf(zc, lo), hi);
+                    const float A = hi - lo, sm = lo + hi;
+                    const float p1 = fminf(fminf(ca, cb), cc), p3 = fmaxf(fmaxf(ca, cb), cc);
+                    float w[8];
+                    w[0] = A;
+                    w[1] = fmaf(2.0f, ca, -sm);
+                    w[2] = fmaf(2.0f, cb, -sm);
+                    w[4] = fmaf(2.0f, cc, -sm);
+                    w[3] = fmaf(-2.0f, fabsf(ca - cb), A);
+                    w[5] = fmaf(-2.0f, fabsf(ca - cc), A);
+                    w[6] = fmaf(-2.0f, fabsf(cb - cc), A);
+                    w[7] = fmaf(4.0f, p1 + p3, -fmaf(2.0f, ca + cb + cc, sm));
                     if (WORK) {
+                        const float xl[2] = {a - Ax, a}, xh[2] = {a, a + Ax};
+                        const float yl[2] = {b - Ay, b}, yh[2] = {b, b + Ay};
+                        const float zl[2] = {z0l, z1l}, zh[2] = {z0h, z1h};
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) evals += w[i] > 0.0f;
-                    }
-                    // in-place Walsh-Hadamard transform over (x, y, z)
+                        for (int j = 0; j < 2; ++j)
 #pragma unroll
-                    for (int h = 1; h < 8; h <<= 1)
+                            for (int i = 0; i < 2; ++i) {
+                                const float l2 = fmaxf(xl[i], yl[j]), h2 = fminf(xh[i], yh[j]);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (!(i & h)) {
-                                const float u0 = w[i], u1 = w[i + h];
-                                w[i] = u0 + u1;
-                                w[i + h] = u0 - u1;
+                                for (int k = 0; k < 2; ++k) evals += fminf(h2, zh[k]) - fmaxf(l2, zl[k]) > 0.0f;
                             }
+                    }
                     acc[0] = fmaf(q, w[0], acc[0]);
 #pragma unroll
                     for (int t = 1; t < 8; ++t) {
