@@ -393,9 +393,12 @@ cudaError_t launch_forward3(const Geom3& g, const float* mu, float* pad, const u
 //   x halves [a - Ax, a], [a, a + Ax], y halves [b - Ay, b], [b, b + Ay],
 //   z halves [c - Az, c], [c, c + Az]  (first / second along the ray).
 // Modes: octet (voxel basis, 2x2x2 voxels: the 8 voxel chords in physical
-// order, sums of non-negative terms), 3-D Haar (8 octants: approximation + 7
-// details split by sign), per-slice 2-D Haar (4 quadrants clipped to the
-// slice: approximation + 3 details), or a single block chord.
+// order, sums of non-negative terms), 3-D Haar (approximation + 7 details,
+// from the centre-plane crossings clamped to the ray's interval in the block,
+// no octant chords), per-slice 2-D Haar (the same in the slice's z slab:
+// approximation + 3 details), or a single block chord.  Details accumulate
+// the signed sum and the absolute sum of qhat * phi, turned into the + and -
+// parts after the view loop.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void decode3(const Segment3& S, int item, int& bx, int& by, int& bz)
 {

@@ -602,13 +602,16 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
 // CTA = 32 consecutive items (blocks of one level, Morton order) x 8 warps;
 // lane i of every warp holds item i, warp w takes views v0 + w, v0 + w + 8,
 // ... of the CTA's view range.  For each view the block's shadow on the
-// detector is found from its corners; for each ray in it the chords through
-// the four children give phi for the approximation (all +) and the three
-// details (Haar signs), and qhat*phi goes to the + or - accumulator by the
-// sign of phi.  The 8 warps' sums are added in a fixed order in shared memory
-// and one partial per (item, view range) is written; partials are summed in a
-// fixed order by the consumer.  dirtab (optional) holds the reciprocal unit
-// direction (1/dx, 1/dy) of every ray.
+// detector is found from its corners; for each ray in it the Haar split
+// (haar_split: the block chord and the three half differences, from the
+// centre-line crossings clamped to the ray's interval in the block) gives phi
+// for the approximation (all +) and the three details, and the signed sum of
+// qhat*phi and the sum of qhat*|phi| are accumulated; after the view loop they
+// become the + and - parts of Eq. 1.10.  The 8 warps' sums are added in a fixed
+// order in shared memory and one partial per (item, view range) is written;
+// partials are summed in a fixed order by the consumer.  dirtab (optional)
+// holds per ray the reciprocal unit direction (1/dx, ry/dy) and its products
+// with the view's sin and -cos.
 // ---------------------------------------------------------------------------
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
