@@ -677,26 +677,30 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
     // (ry = vy / vx, folded into the table's fourth entry), so no per-bin
     // scaling; the sums are multiplied by hx once after the loops.
     const T ihx = T(1) / hx, ry = g.vy * g.ivx;
+    // the block's centre and the source distance in the same units (the
+    // shadow's corners are ratios, the same in any unit)
+    const T cxn = cx * ihx, cyn = cy * ihx, sodn = g.sod * ihx;
     const int v0 = chunk * S.vpc;
     const int v1 = min(g.V, v0 + S.vpc);
     const bool fan = g.kind != 0;
     const T isdd = T(1) / g.sdd, ipitch = T(1) / g.pitch;
     const T u0 = -g.ucen * g.pitch;
-    // detector coordinate -> bin: u * ku + ucen (fan: u = sdd w / (sod - a))
-    const T ku = fan ? g.sdd * ipitch : ipitch;
+    // detector coordinate -> bin: u * ku + ucen (fan: u = sdd w / (sod - a),
+    // a ratio; parallel: u = w, here in units of hx)
+    const T ku = fan ? g.sdd * ipitch : hx * ipitch;
     for (int v = v0 + wv; v < v1; v += kViewLanes) {
         const auto csv = ld2(g.cs + 2 * v);
         const T c = csv.x, s = csv.y;
-        const T ac = cx * c + cy * s;        // block centre along e
-        const T wc = -cx * s + cy * c;       // ... along u
-        // shadow of the block from its four corners (+-hx, +-hy): along u the
-        // corners sit at wc +- (hy c - hx s) and wc +- (hx s + hy c), along e
-        // at ac +- (hx c + hy s) and ac +- (hx c - hy s) respectively
-        const T w1 = hy * c - hx * s, e1 = hx * c + hy * s;
-        const T w2 = hx * s + hy * c, e2 = hx * c - hy * s;
+        const T ac = cxn * c + cyn * s;      // block centre along e (units of hx)
+        const T wc = -cxn * s + cyn * c;     // ... along u
+        // shadow of the block from its four corners (+-1, +-ry): along u the
+        // corners sit at wc +- (ry c - s) and wc +- (s + ry c), along e at
+        // ac +- (c + ry s) and ac +- (c - ry s) respectively
+        const T w1 = fma(ry, c, -s), e1 = fma(ry, s, c);
+        const T w2 = fma(ry, c, s), e2 = fma(-ry, s, c);
         T umin, umax;
+        const T D = sodn - ac;
         if (fan) {
-            const T D = g.sod - ac;
             const T r0 = fast_div(wc - w1, D + e1), r1 = fast_div(wc + w1, D - e1);
             const T r2 = fast_div(wc - w2, D - e2), r3 = fast_div(wc + w2, D + e2);
             umin = fmin(fmin(r0, r1), fmin(r2, r3));
@@ -710,9 +714,10 @@ __device__ __forceinline__ void bp_item(const Geom<T>& g, const Segment& S, int 
         // covers the fast division's rounding (~1e-4 bin at the detector edge)
         const int blo = max(0, (int)ceil(fma(umin, ku, g.ucen - T(1e-3))));
         const int bhi = min(g.B - 1, (int)floor(fma(umax, ku, g.ucen + T(1e-3))));
-        const T kappa = (fan ? (g.sod - ac) * isdd : T(1)) * ihx;
+        // kappa: detector length per unit of hx at the block's depth
+        const T kappa = fan ? D * isdd : ihx;
         // ray offset from the block centre along u (in units of hx), linear in the bin
-        T delta = fma(T(blo) * g.pitch + u0, kappa, -wc * ihx);
+        T delta = fma(T(blo) * g.pitch + u0, kappa, -wc);
         const T dstep = g.pitch * kappa;
         const T* row = sino + (size_t)v * g.B;
         const typename Vec4<T>::type* drow = TABLE ? dirtab + (size_t)v * g.B : nullptr;
