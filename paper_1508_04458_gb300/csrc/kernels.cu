@@ -535,12 +535,19 @@ __global__ void k_max_final(const double* __restrict__ part, int n, double* __re
     if (threadIdx.x == 0) *out = s;
 }
 
+// c negated where bit li of `bits` is set (a sign-bit flip in FP32).
+__device__ __forceinline__ float flip_bit(float c, int bits, int li)
+{
+    return __int_as_float(__float_as_int(c) ^ ((bits << (31 - li)) & 0x80000000));
+}
+__device__ __forceinline__ double flip_bit(double c, int bits, int li) { return ((bits >> li) & 1) ? -c : c; }
+
 // ---------------------------------------------------------------------------
 // a5, Eq. 1.61: per ray sum over active z of |phi(y|z)|, then max over rays.
-// The ray walks the leaves; each leaf's chord is added to the accumulator of
-// the child (quadrant) it lies in, for every expanded ancestor block.  A
-// convex block is crossed in one contiguous run of leaves, so an ancestor's
-// |phi| terms are final when the next ancestor of that level appears.
+// The ray walks the leaves; each leaf's chord is added, with the Haar signs of
+// the quadrant it lies in, to the three detail sums of every expanded ancestor
+// block.  A convex block is crossed in one contiguous run of leaves, so a
+// block's |phi| terms are final when the ray's pixel leaves it.
 // ---------------------------------------------------------------------------
 template <typename T, int LM>
 __global__ void __launch_bounds__(kFwdTPB)
@@ -554,36 +561,39 @@ k_z0(Geom<T> g, Layout lay, const uint8_t* __restrict__ leaf, double* __restrict
     if (b < g.B) {
         Ray<T> r;
         if (make_ray(g, v, b, r)) {
-            // per expanded ancestor level, the ray's three Haar detail sums of the
-            // current block (lower minus upper half, left minus right, diagonal)
+            // per level, the ray's three Haar detail sums of its current block
+            // (lower minus upper half, left minus right, diagonal); they stay
+            // zero in blocks that are not expanded
             T hs[LM > 0 ? LM : 1], vs[LM > 0 ? LM : 1], ds[LM > 0 ? LM : 1];
-            int cur[LM > 0 ? LM : 1];
 #pragma unroll
-            for (int l = 0; l < LM; ++l) {
-                cur[l] = -1;
-                hs[l] = vs[l] = ds[l] = T(0);
-            }
+            for (int l = 0; l < LM; ++l) hs[l] = vs[l] = ds[l] = T(0);
             T total = T(0), rs = T(0);
             const int L = LM;
             auto flush = [&](int li) {
-                if (cur[li] >= 0) {
-                    const T s = T(1) / T(1 << (li + 1));
-                    rs += s * (fabs(hs[li]) + fabs(vs[li]) + fabs(ds[li]));
-                }
+                const T s = T(1) / T(1 << (li + 1));
+                rs += s * (fabs(hs[li]) + fabs(vs[li]) + fabs(ds[li]));
                 hs[li] = vs[li] = ds[li] = T(0);
             };
-            traverse(g, leaf, r, [&](int ix, int iy, int lam, int bx0, int by0, T c) {
+            // the previous leaf's pixel: the level-l block changes between two
+            // leaves exactly when bit l or a higher one of x or y changes, i.e.
+            // for every l up to the highest changed bit (the start flushes the
+            // zero sums of every level)
+            int pix = -1, piy = -1;
+            traverse(g, leaf, r, [&](int ix, int iy, int lam, int, int, T c) {
                 total += c;
+                const int hb = 31 - __clz((ix ^ pix) | (iy ^ piy));
+                pix = ix;
+                piy = iy;
 #pragma unroll
                 for (int li = 0; li < LM; ++li) {
                     const int l = li + 1;
+                    if (l <= hb) flush(li);
                     if (l > lam) {
-                        const int id = ((iy >> l) << 16) | (ix >> l);
-                        if (id != cur[li]) { flush(li); cur[li] = id; }
-                        const bool yb = (by0 >> li) & 1, xb = (bx0 >> li) & 1;
-                        hs[li] += yb ? -c : c;
-                        vs[li] += xb ? -c : c;
-                        ds[li] += (yb != xb) ? -c : c;
+                        // the leaf's quadrant in its level-l ancestor: bit l - 1 of
+                        // the pixel (the leaf is aligned to 2^lam, lam < l)
+                        hs[li] += flip_bit(c, iy, li);
+                        vs[li] += flip_bit(c, ix, li);
+                        ds[li] += flip_bit(c, ix ^ iy, li);
                     }
                 }
             });
