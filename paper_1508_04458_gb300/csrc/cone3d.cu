@@ -1078,7 +1078,7 @@ cudaError_t launch_expand3(const Layout3& lay, const float* mu, double tau, cons
 // Block lists in Morton order: list 0 level-L blocks not expanded, list 1
 // level-L expanded, list 1 + k expanded blocks of level L - k.  Entries
 // (bx | by << 10 | bz << 20); in the slices mode the lists hold 2-D blocks
-// (bz = 0) and the driver repeats them over the slices.
+// (bz = 0) and the host code repeats them over the slices.
 __device__ __forceinline__ uint32_t part1by2(uint32_t x, int sh)
 {
     uint32_t r = 0;

@@ -1718,7 +1718,7 @@ cudaError_t launch_batch_iteration(const BagDev* bags, const BatchPrefix* pre_de
 // ---- the staged forward's host side -----------------------------------------
 
 // Raised by a staged forward whose tensor copy did not complete in time; one
-// word per device, read and cleared by the driver after a reconstruction.
+// word per device, read and cleared by the host code after a reconstruction.
 __device__ int g_stage_err;
 
 int* stage_error_word()

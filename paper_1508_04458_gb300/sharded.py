@@ -13,7 +13,7 @@ every rank keeps an identical copy of beta and of the tree without further
 exchange.
 
 The arithmetic of each step runs in a backend with the interface of
-WamSteps (libwam's step-level calls on the rank's GPU); the driver only
+WamSteps (libwam's step-level calls on the rank's GPU); this module only
 orders the steps and the exchanges.  Results equal the single-GPU
 reconstruction up to the order of the FP32 partial sums.
 """
