@@ -314,7 +314,9 @@ wam_status wam_forward_f64(wam_ctx* ctx, int levels, const unsigned char* masks,
 
 /* a4, Eq. 1.10: bhat+(z) = sum over rays with phi(y|z) > 0 of qhat(y) phi(y|z)
  * and bhat-(z) over phi < 0, for every active z, phi = H Omega computed per
- * (ray, block) from exact chords through the block's four children.
+ * (ray, block) from exact chords through the block's four children.  qhat
+ * must be >= 0 (as wam_forward makes it): the two parts come from the sums of
+ * qhat phi and qhat |phi|, each clamped to its sign.
  * Inactive entries are set to 0.  bplus, bminus [nx*ny] FP64 in coefficient
  * layout.  levels = 0 gives H^T qhat in bplus (pixel basis). */
 wam_status wam_split_backproject(wam_ctx* ctx, int levels, const unsigned char* masks,
