@@ -841,9 +841,14 @@ cudaError_t launch_reduce_voxels3(const SegTable3& tab, const Layout3& lay, cons
 // ---------------------------------------------------------------------------
 constexpr int kMaxL3 = 5;
 
-// Z3: the 3-D tree (octant sums, a Walsh-Hadamard transform at each
-// block's end); else the per-slice 2-D tree (three signed detail sums per
-// level, as in 2-D)
+// c negated where bit li of `bits` is set (a sign-bit flip).
+__device__ __forceinline__ float flip_bit3(float c, int bits, int li)
+{
+    return __int_as_float(__float_as_int(c) ^ ((bits << (31 - li)) & 0x80000000));
+}
+
+// Z3: the 3-D tree (seven signed detail sums per level); else the per-slice
+// 2-D tree (three, as in 2-D)
 template <bool Z3>
 __global__ void __launch_bounds__(kFwdTPB)
 k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict__ part)
@@ -855,70 +860,58 @@ k_z03(Geom3 g, Layout3 lay, const uint8_t* __restrict__ leaf, double* __restrict
         Ray3 ray;
         if (make_ray3(g, v, r, b, ray)) {
             const int L = lay.L, z3 = Z3 ? 1 : 0;
-            float acc[kMaxL3][Z3 ? 8 : 3];
-            long long cur[kMaxL3];
+            // per level, the ray's signed detail sums of its current block: the
+            // 3-D tree's seven (x, y, xy, z, xz, yz, xyz half-sign products) or
+            // the slice's three (x, y, xy); they stay zero in blocks that are
+            // not expanded
+            constexpr int ND = Z3 ? 7 : 3;
+            float acc[kMaxL3][ND];
 #pragma unroll
-            for (int l = 0; l < kMaxL3; ++l) {
-                cur[l] = -1;
+            for (int l = 0; l < kMaxL3; ++l)
 #pragma unroll
-                for (int k = 0; k < (Z3 ? 8 : 3); ++k) acc[l][k] = 0.0f;
-            }
+                for (int k = 0; k < ND; ++k) acc[l][k] = 0.0f;
             float total = 0.0f, rs = 0.0f;
             auto flush = [&](int li) {
-                if (cur[li] >= 0) {
-                    float sa = 0.0f;
-                    if (Z3) {
-                        float w[8];
+                float sa = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) w[k] = acc[li][k];
+                for (int t = 0; t < ND; ++t) sa += fabsf(acc[li][t]);
+                rs += (float)basis_scale(z3, li + 1) * sa;
 #pragma unroll
-                        for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                if (!(i & h)) {
-                                    const float u0 = w[i], u1 = w[i + h];
-                                    w[i] = u0 + u1;
-                                    w[i + h] = u0 - u1;
-                                }
-#pragma unroll
-                        for (int t = 1; t < 8; ++t) sa += fabsf(w[t]);
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) sa += fabsf(acc[li][t]);
-                    }
-                    rs += (float)basis_scale(z3, li + 1) * sa;
-                }
-#pragma unroll
-                for (int k = 0; k < (Z3 ? 8 : 3); ++k) acc[li][k] = 0.0f;
+                for (int k = 0; k < ND; ++k) acc[li][k] = 0.0f;
             };
-            walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int lam, int bx0, int by0, int bz0, float c) {
+            // the previous leaf's voxel: the level-l block changes exactly when bit
+            // l or a higher one of x or y (3-D tree: or z) changes, and in the
+            // slices mode with any change of slice (the start flushes zero sums)
+            int pix = -1, piy = -1, piz = -1;
+            walk3(g, leaf, z3, ray, [&](int ix, int iy, int iz, int lam, int, int, int, float c) {
                 total += c;
+                const int mz = Z3 ? (iz ^ piz) : (iz != piz ? -1 : 0);
+                const int hb = 31 - __clz((ix ^ pix) | (iy ^ piy) | mz);
+                pix = ix;
+                piy = iy;
+                piz = iz;
 #pragma unroll
                 for (int li = 0; li < kMaxL3; ++li) {
                     const int l = li + 1;
+                    if (l <= hb && l <= L) flush(li);
                     if (l > lam && l <= L) {
-                        const long long id = z3 ? (((long long)(iz >> l) * 1024 + (iy >> l)) * 1024 + (ix >> l))
-                                                : (((long long)iz * 1024 + (iy >> l)) * 1024 + (ix >> l));
-                        if (id != cur[li]) {
-                            flush(li);
-                            cur[li] = id;
-                        }
+                        // the leaf's half along each axis in its level-l ancestor:
+                        // bit l - 1 of the voxel (the leaf is aligned to 2^lam)
+                        acc[li][0] += flip_bit3(c, ix, li);
+                        acc[li][1] += flip_bit3(c, iy, li);
+                        acc[li][2] += flip_bit3(c, ix ^ iy, li);
                         if (Z3) {
-                            const int q = ((bx0 >> li) & 1) + 2 * ((by0 >> li) & 1) + 4 * ((bz0 >> li) & 1);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) acc[li][k] += (q == k) ? c : 0.0f;
-                        } else {
-                            // Walsh-Hadamard rows 1..3 of the quadrant: x, y, x^y signs
-                            const bool xb = (bx0 >> li) & 1, yb = (by0 >> li) & 1;
-                            acc[li][0] += xb ? -c : c;
-                            acc[li][1] += yb ? -c : c;
-                            acc[li][2] += (xb != yb) ? -c : c;
+                            acc[li][3 % ND] += flip_bit3(c, iz, li);
+                            acc[li][4 % ND] += flip_bit3(c, ix ^ iz, li);
+                            acc[li][5 % ND] += flip_bit3(c, iy ^ iz, li);
+                            acc[li][6 % ND] += flip_bit3(c, ix ^ iy ^ iz, li);
                         }
                     }
                 }
             });
 #pragma unroll
-            for (int li = 0; li < kMaxL3; ++li) flush(li);
+            for (int li = 0; li < kMaxL3; ++li)
+                if (li + 1 <= L) flush(li);
             rowsum = (double)rs + (double)total * basis_scale(z3, L);
         }
     }
